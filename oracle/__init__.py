@@ -1,0 +1,210 @@
+"""CPU oracle for rule-based blocking — TEST INFRASTRUCTURE ONLY.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  The GPU library and its Python binding
+never import it, and it imports nothing from them.
+
+Contents:
+  * hb_oracle.cpp   - the blocking definition of Section 2 ("Semantics",
+                      "Blocking") as a literal nested loop, a grouped variant,
+                      per-pair checks and the single predicates;
+  * plan.py         - the execution-plan generator of Section 4.2 (ordering by
+                      cost-effectiveness, execution tree, witness probability,
+                      edge scores, DFS order) and its flattening into the
+                      sequential execution path of Section 5.1;
+  * mlp.py          - fp64 forward / backward / Adam for the cost-model MLP.
+
+This module marshals numpy tables (see ``synth``) into the C oracle.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SO = os.path.join(_HERE, "liboracle.so")
+
+KINDS = {"eq": 0, "eq_prefix": 1, "ed": 2, "jaccard": 3, "absdiff": 4}
+
+
+class OrCol(ctypes.Structure):
+    _fields_ = [("type", ctypes.c_int32), ("pad", ctypes.c_int32), ("data", ctypes.c_void_p),
+                ("off", ctypes.c_void_p), ("valid", ctypes.c_void_p)]
+
+
+class OrPred(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("col_t", ctypes.c_int32), ("col_s", ctypes.c_int32),
+                ("k", ctypes.c_int32), ("q", ctypes.c_int32), ("num", ctypes.c_uint32), ("den", ctypes.c_uint32),
+                ("delta", ctypes.c_float)]
+
+
+def build(force: bool = False) -> str:
+    """Compile liboracle.so (plain C++17, -O2, no fast-math, no contraction)."""
+    src = os.path.join(_HERE, "hb_oracle.cpp")
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(src):
+        tmp = _SO + f".tmp{os.getpid()}"
+        subprocess.check_call(["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fno-fast-math", "-shared",
+                               "-fPIC", "-pthread", "-o", tmp, src])
+        os.replace(tmp, _SO)
+    return _SO
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(_SO)
+        P = ctypes.c_void_p
+        i64, i32 = ctypes.c_int64, ctypes.c_int32
+        L.or_edit_distance.restype = i64
+        L.or_edit_distance.argtypes = [P, i64, P, i64]
+        L.or_qgram_sets.restype = None
+        L.or_qgram_sets.argtypes = [P, i64, P, i64, i32, P, P, P]
+        L.or_jaccard_ge.restype = i32
+        L.or_jaccard_ge.argtypes = [P, i64, P, i64, i32, ctypes.c_uint32, ctypes.c_uint32]
+        L.or_absdiff_le.restype = i32
+        L.or_absdiff_le.argtypes = [ctypes.c_float, ctypes.c_float, ctypes.c_float]
+        L.or_block_literal.restype = i64
+        L.or_block_literal.argtypes = [i64, i32, P, i64, i32, P, i32, P, P, P, i64]
+        L.or_block_hash.restype = i64
+        L.or_block_hash.argtypes = [i64, i32, P, i64, i32, P, i32, P, P, i32, P, i64, P, i32]
+        L.or_check_pairs.restype = None
+        L.or_check_pairs.argtypes = [i64, i32, P, i64, i32, P, i32, P, P, P, i64, P]
+        L.or_pred_verdicts.restype = None
+        L.or_pred_verdicts.argtypes = [i64, i32, P, i64, i32, P, P, P, i64, P]
+        _lib = L
+    return _lib
+
+
+def _buf(b: bytes | bytearray | str):
+    if isinstance(b, str):
+        b = b.encode()
+    a = np.frombuffer(bytes(b), np.uint8) if len(b) else np.zeros(1, np.uint8)
+    return a, len(b)
+
+
+def edit_distance(a, b) -> int:
+    A, la = _buf(a)
+    B, lb = _buf(b)
+    return int(lib().or_edit_distance(A.ctypes.data, la, B.ctypes.data, lb))
+
+
+def qgram_sets(a, b, q=3):
+    A, la = _buf(a)
+    B, lb = _buf(b)
+    out = np.zeros(3, np.int64)
+    lib().or_qgram_sets(A.ctypes.data, la, B.ctypes.data, lb, q, out.ctypes.data, out[1:].ctypes.data,
+                        out[2:].ctypes.data)
+    return int(out[0]), int(out[1]), int(out[2])
+
+
+def jaccard_ge(a, b, num, den, q=3) -> bool:
+    A, la = _buf(a)
+    B, lb = _buf(b)
+    return bool(lib().or_jaccard_ge(A.ctypes.data, la, B.ctypes.data, lb, q, num, den))
+
+
+def absdiff_le(a: float, b: float, delta: float) -> bool:
+    return bool(lib().or_absdiff_le(a, b, delta))
+
+
+class _Marshal:
+    """Keeps numpy buffers alive while the C oracle reads them."""
+
+    def __init__(self, table):
+        self.keep = []
+        n = len(table.columns)
+        self.arr = (OrCol * max(n, 1))()
+        for i, c in enumerate(table.columns):
+            col = OrCol()
+            col.type = {"string": 0, "int32": 1, "fp32": 2}[c.type]
+            data = c.data if len(c.data) else np.zeros(1, c.data.dtype)
+            self.keep.append(data)
+            col.data = data.ctypes.data
+            if c.offsets is not None:
+                off = np.ascontiguousarray(c.offsets, np.uint32)
+                self.keep.append(off)
+                col.off = off.ctypes.data
+            if c.valid is not None:
+                v = np.ascontiguousarray(c.valid, np.uint8)
+                self.keep.append(v)
+                col.valid = v.ctypes.data
+            self.arr[i] = col
+        self.n = table.n_rows
+        self.ncols = n
+
+
+def _rules(mds):
+    starts = np.zeros(len(mds) + 1, np.int32)
+    flat = []
+    for m, preds in enumerate(mds):
+        flat.extend(preds)
+        starts[m + 1] = len(flat)
+    arr = (OrPred * max(len(flat), 1))()
+    for i, p in enumerate(flat):
+        kind, ct, cs, k, q, num, den, delta = p
+        arr[i] = OrPred(KINDS[kind], ct, cs, k, q, num, den, delta)
+    return starts, arr
+
+
+def _args(R, S):
+    r = _Marshal(R)
+    s = _Marshal(S) if S is not None else None
+    return r, s, (r.n, r.ncols, r.arr, s.n if s else 0, s.ncols if s else 0, s.arr if s else None)
+
+
+def _unpack(buf, n):
+    v = buf[:n]
+    return np.stack([(v >> 32).astype(np.int64), (v & 0xFFFFFFFF).astype(np.int64)], axis=1) if n else \
+        np.zeros((0, 2), np.int64)
+
+
+def block_literal(R, mds, S=None) -> np.ndarray:
+    """Pairs (i, j) of the naive nested loop, ascending; shape [n, 2]."""
+    r, s, a = _args(R, S)
+    starts, preds = _rules(mds)
+    n = lib().or_block_literal(*a, len(mds), starts.ctypes.data, preds, None, 0)
+    buf = np.zeros(max(n, 1), np.uint64)
+    lib().or_block_literal(*a, len(mds), starts.ctypes.data, preds, buf.ctypes.data, n)
+    return _unpack(buf, n)
+
+
+def block_hash(R, mds, S=None, threads=None, count_candidates=True):
+    """(pairs [n,2] ascending, candidate count) of the grouped evaluation."""
+    r, s, a = _args(R, S)
+    starts, preds = _rules(mds)
+    threads = threads or os.cpu_count() or 1
+    cand = np.zeros(1, np.int64)
+    n = lib().or_block_hash(*a, len(mds), starts.ctypes.data, preds, threads, None, 0, cand.ctypes.data,
+                            1 if count_candidates else 0)
+    buf = np.zeros(max(n, 1), np.uint64)
+    lib().or_block_hash(*a, len(mds), starts.ctypes.data, preds, threads, buf.ctypes.data, n, None, 0)
+    return _unpack(buf, n), int(cand[0])
+
+
+def check_pairs(R, mds, pairs, S=None) -> np.ndarray:
+    """Verdict (0/1) of the disjunction for each given pair (i, j)."""
+    r, s, a = _args(R, S)
+    starts, preds = _rules(mds)
+    pairs = np.asarray(pairs, np.int64).reshape(-1, 2)
+    packed = ((pairs[:, 0].astype(np.uint64) << np.uint64(32)) | pairs[:, 1].astype(np.uint64)).copy()
+    out = np.zeros(max(len(packed), 1), np.uint8)
+    lib().or_check_pairs(*a, len(mds), starts.ctypes.data, preds, packed.ctypes.data, len(packed), out.ctypes.data)
+    return out[:len(packed)]
+
+
+def pred_verdicts(R, pred, pairs, S=None) -> np.ndarray:
+    """Verdict (0/1) of one predicate for each given pair (i, j)."""
+    r, s, a = _args(R, S)
+    _, preds = _rules([[pred]])
+    pairs = np.asarray(pairs, np.int64).reshape(-1, 2)
+    packed = ((pairs[:, 0].astype(np.uint64) << np.uint64(32)) | pairs[:, 1].astype(np.uint64)).copy()
+    out = np.zeros(max(len(packed), 1), np.uint8)
+    lib().or_pred_verdicts(*a, preds, packed.ctypes.data, len(packed), out.ctypes.data)
+    return out[:len(packed)]

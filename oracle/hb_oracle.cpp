@@ -1,0 +1,343 @@
+/*
+ * CPU oracle for rule-based blocking — TEST INFRASTRUCTURE ONLY.
+ *
+ * Only the tests, the package's smoke check and the benchmark's CPU-baseline
+ * leg load this library.  The GPU library never links or calls it, and it
+ * shares no code, header or table with the GPU library.
+ *
+ * What it computes is the plain definition of blocking with matching
+ * dependencies (Section 2, "Rules", "Semantics" and "Blocking"):
+ *
+ *   Ca = { (t1, t2) : some MD phi = X -> t.eid = s.eid in Delta has
+ *                     h(t1, t2) |= p for every predicate p in X }
+ *
+ * for a self-join (pairs i < j of one relation) or for two relations R x S
+ * (all pairs (i in R, j in S)).  The naive evaluation of Section 4 ("a naive
+ * approach ... evaluate each MD in Delta for all pairs") is or_block_literal;
+ * or_block_hash only restricts which pairs are looked at, using the fact that
+ * a pair can satisfy a precondition only if it agrees on all of its equality
+ * predicates, and then evaluates the whole disjunction for each such pair.
+ *
+ * Predicate semantics (readings where the paper is silent):
+ *   - a missing operand makes every predicate false (Example 3: (t2, t3) fails
+ *     price equality because t2.price is missing);
+ *   - eq        : byte equality of strings, value equality of int32;
+ *   - eq_prefix : equality of the first min(k, len) bytes of two strings;
+ *   - ed        : unit-cost Levenshtein distance over bytes <= k
+ *                 (edit distance of Example 2), by the Wagner-Fischer DP;
+ *   - jaccard   : set of all contiguous q-byte substrings (no padding, strings
+ *                 shorter than q give the empty set); |A^B| * den >= num * |AuB|
+ *                 in integers (Jaccard measure of Example 2);
+ *   - absdiff   : fabsf(a - b) <= delta in IEEE binary32, round to nearest even,
+ *                 no contraction (compile with -ffp-contract=off).
+ *
+ * Parity status: ed, jaccard, absdiff, eq and eq_prefix are pinned by the
+ * tests (textbook DP properties, brute force, hand-computed cases and the
+ * paper's Table 1 / Examples 3 and "(t1, t5)").
+ */
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <mutex>
+#include <set>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+namespace {
+
+struct or_col {
+    int32_t type;            /* 0 string, 1 int32, 2 fp32 */
+    int32_t pad;
+    const void *data;        /* string bytes, int32 values or float values */
+    const uint32_t *off;     /* strings: n+1 byte offsets */
+    const uint8_t *valid;    /* one byte per row, nonzero = present; NULL = all present */
+};
+
+struct or_pred {
+    int32_t kind;            /* 0 eq, 1 eq_prefix, 2 ed, 3 jaccard, 4 absdiff */
+    int32_t col_t, col_s;    /* column of the left tuple (R) and of the right tuple (S) */
+    int32_t k;               /* ed: max distance; eq_prefix: prefix length */
+    int32_t q;               /* jaccard: gram length */
+    uint32_t num, den;       /* jaccard: threshold num/den */
+    float delta;             /* absdiff */
+};
+
+struct Rel {
+    int64_t n;
+    int ncols;
+    const or_col *cols;
+};
+
+bool present(const or_col &c, int64_t i) { return c.valid == nullptr || c.valid[i] != 0; }
+
+std::string bytes_of(const or_col &c, int64_t i) {
+    const uint8_t *p = static_cast<const uint8_t *>(c.data);
+    return std::string(reinterpret_cast<const char *>(p + c.off[i]), c.off[i + 1] - c.off[i]);
+}
+
+/* Wagner-Fischer dynamic programme for the Levenshtein distance. */
+int64_t levenshtein(const std::string &a, const std::string &b) {
+    const size_t m = a.size(), n = b.size();
+    std::vector<int64_t> prev(n + 1), cur(n + 1);
+    for (size_t j = 0; j <= n; j++) prev[j] = (int64_t)j;
+    for (size_t i = 1; i <= m; i++) {
+        cur[0] = (int64_t)i;
+        for (size_t j = 1; j <= n; j++) {
+            int64_t sub = prev[j - 1] + (a[i - 1] == b[j - 1] ? 0 : 1);
+            int64_t del = prev[j] + 1;
+            int64_t ins = cur[j - 1] + 1;
+            cur[j] = std::min(sub, std::min(del, ins));
+        }
+        std::swap(prev, cur);
+    }
+    return prev[n];
+}
+
+std::set<std::string> qgrams(const std::string &s, int q) {
+    std::set<std::string> g;
+    if (q <= 0) return g;
+    for (size_t i = 0; i + (size_t)q <= s.size(); i++) g.insert(s.substr(i, (size_t)q));
+    return g;
+}
+
+bool jaccard_ge(const std::string &a, const std::string &b, int q, uint32_t num, uint32_t den) {
+    std::set<std::string> A = qgrams(a, q), B = qgrams(b, q);
+    std::vector<std::string> inter;
+    std::set_intersection(A.begin(), A.end(), B.begin(), B.end(), std::back_inserter(inter));
+    uint64_t I = inter.size();
+    uint64_t U = A.size() + B.size() - I;
+    return I * (uint64_t)den >= (uint64_t)num * U;
+}
+
+bool holds(const or_pred &p, const Rel &R, int64_t i, const Rel &S, int64_t j) {
+    const or_col &a = R.cols[p.col_t];
+    const or_col &b = S.cols[p.col_s];
+    if (!present(a, i) || !present(b, j)) return false;
+    switch (p.kind) {
+    case 0:
+        if (a.type == 0 && b.type == 0) return bytes_of(a, i) == bytes_of(b, j);
+        if (a.type == 1 && b.type == 1)
+            return static_cast<const int32_t *>(a.data)[i] == static_cast<const int32_t *>(b.data)[j];
+        return false;
+    case 1: {
+        std::string x = bytes_of(a, i), y = bytes_of(b, j);
+        size_t k = (size_t)std::max(p.k, 0);
+        return x.substr(0, std::min(k, x.size())) == y.substr(0, std::min(k, y.size()));
+    }
+    case 2:
+        return levenshtein(bytes_of(a, i), bytes_of(b, j)) <= (int64_t)p.k;
+    case 3:
+        return jaccard_ge(bytes_of(a, i), bytes_of(b, j), p.q, p.num, p.den);
+    case 4: {
+        float x = static_cast<const float *>(a.data)[i];
+        float y = static_cast<const float *>(b.data)[j];
+        volatile float d = x - y;
+        return std::fabs((float)d) <= p.delta;
+    }
+    }
+    return false;
+}
+
+/* the precondition of one MD: every predicate holds (short-circuit AND) */
+bool md_holds(const or_pred *preds, int32_t lo, int32_t hi, const Rel &R, int64_t i, const Rel &S, int64_t j) {
+    for (int32_t k = lo; k < hi; k++)
+        if (!holds(preds[k], R, i, S, j)) return false;
+    return true;
+}
+
+/* the disjunction over all MDs: some MD is a witness (short-circuit OR) */
+bool dnf_holds(int n_md, const int32_t *md_start, const or_pred *preds, const Rel &R, int64_t i, const Rel &S,
+               int64_t j) {
+    for (int m = 0; m < n_md; m++)
+        if (md_holds(preds, md_start[m], md_start[m + 1], R, i, S, j)) return true;
+    return false;
+}
+
+bool is_equality(const or_pred &p) { return p.kind == 0 || p.kind == 1; }
+
+/* the grouping key of tuple i for the equality predicates of one MD; false if a value is missing */
+bool group_key(const or_pred *preds, int32_t lo, int32_t hi, const Rel &T, int64_t i, bool left, std::string &key) {
+    key.clear();
+    for (int32_t k = lo; k < hi; k++) {
+        const or_pred &p = preds[k];
+        if (!is_equality(p)) continue;
+        const or_col &c = T.cols[left ? p.col_t : p.col_s];
+        if (!present(c, i)) return false;
+        std::string part;
+        if (c.type == 1) {
+            int32_t v = static_cast<const int32_t *>(c.data)[i];
+            part.assign(reinterpret_cast<const char *>(&v), 4);
+        } else {
+            part = bytes_of(c, i);
+            if (p.kind == 1) part = part.substr(0, std::min((size_t)std::max(p.k, 0), part.size()));
+        }
+        uint64_t len = part.size();
+        key.append(reinterpret_cast<const char *>(&len), 8);
+        key.append(part);
+    }
+    return true;
+}
+
+int64_t emit(const std::vector<uint64_t> &v, uint64_t *out, int64_t cap) {
+    int64_t n = (int64_t)v.size();
+    if (out) std::memcpy(out, v.data(), sizeof(uint64_t) * (size_t)std::min(n, cap));
+    return n;
+}
+
+}  // namespace
+
+extern "C" {
+
+int64_t or_edit_distance(const uint8_t *a, int64_t la, const uint8_t *b, int64_t lb) {
+    return levenshtein(std::string(reinterpret_cast<const char *>(a), (size_t)la),
+                       std::string(reinterpret_cast<const char *>(b), (size_t)lb));
+}
+
+/* sizes of the q-gram sets and of their intersection */
+void or_qgram_sets(const uint8_t *a, int64_t la, const uint8_t *b, int64_t lb, int32_t q, int64_t *na, int64_t *nb,
+                   int64_t *ni) {
+    std::set<std::string> A = qgrams(std::string(reinterpret_cast<const char *>(a), (size_t)la), q);
+    std::set<std::string> B = qgrams(std::string(reinterpret_cast<const char *>(b), (size_t)lb), q);
+    std::vector<std::string> inter;
+    std::set_intersection(A.begin(), A.end(), B.begin(), B.end(), std::back_inserter(inter));
+    *na = (int64_t)A.size();
+    *nb = (int64_t)B.size();
+    *ni = (int64_t)inter.size();
+}
+
+int32_t or_jaccard_ge(const uint8_t *a, int64_t la, const uint8_t *b, int64_t lb, int32_t q, uint32_t num,
+                      uint32_t den) {
+    return jaccard_ge(std::string(reinterpret_cast<const char *>(a), (size_t)la),
+                      std::string(reinterpret_cast<const char *>(b), (size_t)lb), q, num, den) ? 1 : 0;
+}
+
+int32_t or_absdiff_le(float a, float b, float delta) {
+    volatile float d = a - b;
+    return std::fabs((float)d) <= delta ? 1 : 0;
+}
+
+/*
+ * Naive nested loop (Section 4, first paragraph).  S == NULL means self-join
+ * (pairs i < j of R).  Pairs are packed as (i << 32) | j, ascending.
+ * Returns the number of pairs; writes at most cap of them.
+ */
+int64_t or_block_literal(int64_t nR, int32_t ncR, const or_col *R, int64_t nS, int32_t ncS, const or_col *S,
+                         int32_t n_md, const int32_t *md_start, const or_pred *preds, uint64_t *out, int64_t cap) {
+    Rel r{nR, ncR, R};
+    Rel s = S ? Rel{nS, ncS, S} : r;
+    std::vector<uint64_t> res;
+    for (int64_t i = 0; i < r.n; i++)
+        for (int64_t j = S ? 0 : i + 1; j < s.n; j++)
+            if (dnf_holds(n_md, md_start, preds, r, i, s, j)) res.push_back(((uint64_t)i << 32) | (uint64_t)j);
+    return emit(res, out, cap);
+}
+
+/*
+ * Same result as or_block_literal, looking only at pairs that agree on all
+ * equality predicates of some MD (MDs without one contribute every pair).
+ * Also returns, in *n_candidates, the number of distinct such pairs.
+ */
+int64_t or_block_hash(int64_t nR, int32_t ncR, const or_col *R, int64_t nS, int32_t ncS, const or_col *S,
+                      int32_t n_md, const int32_t *md_start, const or_pred *preds, int32_t n_threads, uint64_t *out,
+                      int64_t cap, int64_t *n_candidates, int32_t count_candidates) {
+    Rel r{nR, ncR, R};
+    Rel s = S ? Rel{nS, ncS, S} : r;
+    const bool self = (S == nullptr);
+    struct Group { std::vector<int64_t> left, right; };
+    std::vector<Group> groups;
+    for (int m = 0; m < n_md; m++) {
+        std::unordered_map<std::string, size_t> index;
+        std::string key;
+        size_t first = groups.size();
+        for (int64_t i = 0; i < r.n; i++) {
+            if (!group_key(preds, md_start[m], md_start[m + 1], r, i, true, key)) continue;
+            auto it = index.find(key);
+            if (it == index.end()) { it = index.emplace(key, groups.size()).first; groups.emplace_back(); }
+            groups[it->second].left.push_back(i);
+        }
+        if (!self) {
+            for (int64_t j = 0; j < s.n; j++) {
+                if (!group_key(preds, md_start[m], md_start[m + 1], s, j, false, key)) continue;
+                auto it = index.find(key);
+                if (it == index.end()) continue;
+                groups[it->second].right.push_back(j);
+            }
+        }
+        (void)first;
+    }
+    std::atomic<size_t> next{0};
+    std::vector<std::vector<uint64_t>> res((size_t)std::max(n_threads, 1)), cand((size_t)std::max(n_threads, 1));
+    auto work = [&](int t) {
+        for (;;) {
+            size_t g = next.fetch_add(1);
+            if (g >= groups.size()) break;
+            const Group &G = groups[g];
+            if (self) {
+                for (size_t a = 0; a < G.left.size(); a++)
+                    for (size_t b = a + 1; b < G.left.size(); b++) {
+                        int64_t i = G.left[a], j = G.left[b];
+                        uint64_t key = ((uint64_t)i << 32) | (uint64_t)j;
+                        if (count_candidates) cand[t].push_back(key);
+                        if (dnf_holds(n_md, md_start, preds, r, i, s, j)) res[t].push_back(key);
+                    }
+            } else {
+                for (int64_t i : G.left)
+                    for (int64_t j : G.right) {
+                        uint64_t key = ((uint64_t)i << 32) | (uint64_t)j;
+                        if (count_candidates) cand[t].push_back(key);
+                        if (dnf_holds(n_md, md_start, preds, r, i, s, j)) res[t].push_back(key);
+                    }
+            }
+        }
+    };
+    std::vector<std::thread> th;
+    int nt = std::max(n_threads, 1);
+    for (int t = 1; t < nt; t++) th.emplace_back(work, t);
+    work(0);
+    for (auto &x : th) x.join();
+    std::vector<uint64_t> all;
+    for (auto &v : res) { all.insert(all.end(), v.begin(), v.end()); std::vector<uint64_t>().swap(v); }
+    std::sort(all.begin(), all.end());
+    all.erase(std::unique(all.begin(), all.end()), all.end());
+    if (n_candidates) {
+        if (count_candidates) {
+            std::vector<uint64_t> c;
+            for (auto &v : cand) { c.insert(c.end(), v.begin(), v.end()); std::vector<uint64_t>().swap(v); }
+            std::sort(c.begin(), c.end());
+            c.erase(std::unique(c.begin(), c.end()), c.end());
+            *n_candidates = (int64_t)c.size();
+        } else {
+            *n_candidates = -1;
+        }
+    }
+    return emit(all, out, cap);
+}
+
+/* Disjunction verdict for given pairs (i << 32 | j); used for sampled checks at full size. */
+void or_check_pairs(int64_t nR, int32_t ncR, const or_col *R, int64_t nS, int32_t ncS, const or_col *S,
+                    int32_t n_md, const int32_t *md_start, const or_pred *preds, const uint64_t *pairs, int64_t n,
+                    uint8_t *verdict) {
+    Rel r{nR, ncR, R};
+    Rel s = S ? Rel{nS, ncS, S} : r;
+    for (int64_t k = 0; k < n; k++) {
+        int64_t i = (int64_t)(pairs[k] >> 32), j = (int64_t)(pairs[k] & 0xffffffffu);
+        verdict[k] = dnf_holds(n_md, md_start, preds, r, i, s, j) ? 1 : 0;
+    }
+}
+
+/* Single-predicate verdicts (for the per-predicate logs and unit pins). */
+void or_pred_verdicts(int64_t nR, int32_t ncR, const or_col *R, int64_t nS, int32_t ncS, const or_col *S,
+                      const or_pred *pred, const uint64_t *pairs, int64_t n, uint8_t *verdict) {
+    Rel r{nR, ncR, R};
+    Rel s = S ? Rel{nS, ncS, S} : r;
+    for (int64_t k = 0; k < n; k++) {
+        int64_t i = (int64_t)(pairs[k] >> 32), j = (int64_t)(pairs[k] & 0xffffffffu);
+        verdict[k] = holds(*pred, r, i, s, j) ? 1 : 0;
+    }
+}
+
+}  // extern "C"
