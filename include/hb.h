@@ -1,0 +1,287 @@
+/*
+ * libhb — rule-based blocking for entity resolution on one GB300 GPU.
+ *
+ * The library computes, for a set Delta of matching dependencies (MDs), the
+ * candidate pairs Ca of Section 2 ("Blocking"): a tuple pair is a candidate
+ * iff some MD phi = X -> t.eid = s.eid in Delta is a witness at it, i.e. the
+ * pair satisfies every predicate of the precondition X ("Semantics").
+ *
+ *   self-join : Ca = { (i, j) : 0 <= i < j < n,  some phi satisfied by (t_i, t_j) }
+ *   R x S     : Ca = { (i, j) : i in R, j in S,  some phi satisfied by (r_i, s_j) }
+ *
+ * Predicates (Section 2, "Predicates": t.A = s.B and t.A ~ s.B with a
+ * similarity measure and a threshold):
+ *   HB_P_EQ          t.A = s.B          strings by bytes, int32 by value
+ *   HB_P_EQ_PREFIX   first k bytes equal (strings; a shorter string is its own prefix)
+ *   HB_P_ED_LE       Levenshtein distance over bytes <= k          (edit distance, Example 2)
+ *   HB_P_JACCARD_GE  q-gram set Jaccard >= num/den, compared as    (Jaccard measure, Example 2)
+ *                    |A n B| * den >= num * |A u B| (q = 1..4, contiguous q-byte
+ *                    substrings, no padding; a string shorter than q has no grams)
+ *   HB_P_ABSDIFF_LE  fabsf(a - b) <= delta in binary32 (fp32 columns)
+ * A missing operand (valid[i] == 0) makes every predicate false (Example 3:
+ * (t2, t3) is not a witness because t2.price is missing).
+ *
+ * All similarity predicates provided are symmetric, so a self-join emits each
+ * unordered pair once as (i, j) with i < j (Section 5.1, last paragraph of
+ * "Reusing computation").  The result is exact: no sampling, no approximation.
+ *
+ * Errors: every call returns an hb_status; nothing throws across this
+ * boundary.  On a non-OK status hb_last_error() describes it.  Calls on one
+ * context must not run concurrently.  Inputs are copied: the caller may free
+ * its buffers as soon as a call returns.
+ */
+#ifndef HB_H
+#define HB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define HB_API __attribute__((visibility("default")))
+#else
+#define HB_API
+#endif
+
+typedef struct hb_ctx hb_ctx;
+
+typedef enum {
+    HB_OK = 0,
+    HB_ERR_ARG = -1,            /* invalid argument (message names it) */
+    HB_ERR_OOM = -2,            /* host or device allocation failed */
+    HB_ERR_CUDA = -3,           /* a CUDA call failed (message has the CUDA error) */
+    HB_ERR_STATE = -4,          /* call out of order (e.g. hb_block before hb_load_table) */
+    HB_ERR_OVERFLOW = -5,       /* a fixed-capacity output could not hold the result */
+    HB_ERR_DEVICE_TIMEOUT = -6, /* a bounded device-side wait gave up */
+    HB_ERR_INTERNAL = -7
+} hb_status;
+
+typedef enum { HB_COL_STRING = 0, HB_COL_INT32 = 1, HB_COL_FP32 = 2 } hb_coltype;
+
+/* One column of a relation (Section 2, "Relations": schema R = (eid, A1..An)). */
+typedef struct {
+    int32_t type;             /* hb_coltype */
+    int32_t reserved;         /* 0 */
+    const void *data;         /* STRING: bytes; INT32: int32_t[n]; FP32: float[n] */
+    const uint32_t *offsets;  /* STRING: n+1 nondecreasing byte offsets, offsets[0] = 0; else NULL */
+    const uint8_t *valid;     /* n bytes, nonzero = present; NULL = every row present */
+    uint64_t data_bytes;      /* STRING: offsets[n]; ignored otherwise */
+} hb_column;
+
+typedef enum {
+    HB_P_EQ = 0,
+    HB_P_EQ_PREFIX = 1,
+    HB_P_ED_LE = 2,
+    HB_P_JACCARD_GE = 3,
+    HB_P_ABSDIFF_LE = 4
+} hb_pkind;
+
+/* One predicate of an MD precondition (Section 2, "Predicates"). */
+typedef struct {
+    int32_t kind;             /* hb_pkind */
+    int32_t col_t;            /* column of the left tuple (relation R) */
+    int32_t col_s;            /* column of the right tuple (S; = col_t for a self-join) */
+    int32_t k;                /* ED_LE: max distance (>= 0); EQ_PREFIX: prefix length (>= 1) */
+    int32_t q;                /* JACCARD_GE: gram length, 1..4 */
+    uint32_t num, den;        /* JACCARD_GE: threshold num/den, 0 <= num <= den, den >= 1 */
+    float delta;              /* ABSDIFF_LE: threshold (>= 0) */
+} hb_predicate;
+
+typedef struct { uint32_t tid1, tid2; } hb_pair;
+
+typedef struct {
+    int32_t device;           /* CUDA device ordinal */
+    int32_t tile;             /* tuples per tile side: 0 = autotuned, else 32 or 64 */
+    uint64_t chunk_bytes;     /* pinned staging chunk for host uploads; 0 = 256 MiB */
+    uint64_t seed;            /* seed of the planner's samples */
+    void *stream;             /* cudaStream_t to run on; NULL = a stream owned by the context */
+    int64_t out_capacity;     /* initial capacity (pairs) of the result slab; 0 = automatic */
+    int32_t flags;            /* reserved, 0 */
+    int32_t reserved;
+} hb_options;
+
+/* Planner modes.  Every mode yields the same pair set; they differ in speed. */
+typedef enum {
+    HB_PLAN_RULE_DATA = 0,    /* Section 4.2: order by (1 - sp) / cost, tree, wp, edge scores, DFS */
+    HB_PLAN_LEARNED = 1,      /* same, with sp and cost predicted by the trained cost model;
+                                 falls back to HB_PLAN_RULE_DATA when no usable model is loaded */
+    HB_PLAN_GIVEN_ORDER = 2,  /* MDs and predicates exactly as added */
+    HB_PLAN_RANDOM = 3,       /* a seeded random order */
+    HB_PLAN_COST_FIRST = 4,   /* cheapest predicate first (cost only) */
+    HB_PLAN_SEL_FIRST = 5     /* most selective predicate first (sp only) */
+} hb_plan_mode;
+
+#define HB_MAX_MDS 64
+#define HB_MAX_PREDS 128
+
+typedef struct {
+    int32_t mode;                     /* the mode that was applied */
+    int32_t n_preds;                  /* distinct predicates over all MDs */
+    int32_t n_ops;                    /* non-equality predicates in the evaluation program */
+    int32_t n_eq;                     /* distinct equality keys (blocking keys) */
+    int32_t op_pred[HB_MAX_PREDS];    /* program order: distinct predicate ids */
+    int32_t md_order[HB_MAX_MDS];     /* DFS order of the MDs */
+    double sp[HB_MAX_PREDS];          /* sp(p, D) used for ordering */
+    double cost[HB_MAX_PREDS];        /* cost(p, D) used for ordering */
+    int32_t pred_md[HB_MAX_PREDS];    /* first MD that holds each distinct predicate */
+    int32_t tile;                     /* tile side chosen for evaluation */
+    int32_t n_mds;
+} hb_plan_info;
+
+typedef struct {
+    int64_t n_rows_r, n_rows_s;
+    int64_t candidate_pairs;   /* pairs that agree on every equality predicate of some MD, each once */
+    int64_t emitted_pairs;     /* |Ca| of the last call */
+    int64_t tiles;             /* evaluation work items of the last call */
+    int64_t blocks;            /* non-trivial blocks over all MDs */
+    double ms_h2d, ms_encode, ms_plan, ms_block_build, ms_eval, ms_sort, ms_d2h, ms_total;
+    int64_t device_bytes;      /* device memory held by the context */
+    int32_t tile;              /* tile side used */
+    int32_t n_mds;
+} hb_stats;
+
+/* ---- context ---- */
+HB_API hb_status hb_create(hb_ctx **out, const hb_options *opt);   /* opt may be NULL (defaults) */
+HB_API void hb_destroy(hb_ctx *ctx);
+HB_API const char *hb_last_error(void);                            /* thread-local; "" when none */
+HB_API const char *hb_version(void);
+
+/*
+ * Load relation `side` (0 = R, 1 = S; a self-join loads only R) of n_rows rows
+ * and n_cols columns.  on_device = 0: pointers are host memory, copied through
+ * pinned staging chunks of chunk_bytes; on_device = 1: pointers are device
+ * memory of this context's device, copied device to device.  Replaces any
+ * previous table of that side.
+ */
+HB_API hb_status hb_load_table(hb_ctx *ctx, int32_t side, int64_t n_rows, int32_t n_cols, const hb_column *cols,
+                        int32_t on_device);
+
+/* Add one MD with 1..10 predicates; *md_id_out (optional) receives its id (0, 1, ...). */
+HB_API hb_status hb_add_md(hb_ctx *ctx, int32_t n_pred, const hb_predicate *preds, int32_t *md_id_out);
+HB_API hb_status hb_clear_mds(hb_ctx *ctx);
+
+/*
+ * Build the execution plan (Section 4.2) for the loaded tables and MDs:
+ * samples the data on the GPU for sp and cost, orders predicates, builds the
+ * execution tree and flattens it into the sequential program of Section 5.1.
+ * Must follow the last hb_add_md / hb_load_table.  info_out is optional.
+ */
+HB_API hb_status hb_plan(hb_ctx *ctx, int32_t mode, hb_plan_info *info_out);
+
+/*
+ * Compute Ca for the loaded tables (self-join when only R is loaded).
+ * *pairs_out receives a library-allocated host array of *n_out pairs sorted
+ * ascending by (tid1, tid2), unique; free it with hb_free_pairs.  Plans with
+ * HB_PLAN_RULE_DATA first if hb_plan was not called.
+ */
+HB_API hb_status hb_block(hb_ctx *ctx, hb_pair **pairs_out, int64_t *n_out);
+
+/*
+ * As hb_block, but the sorted pairs stay in device memory owned by the
+ * context (valid until the next call on it); *dev_pairs_out is a device pointer.
+ */
+HB_API hb_status hb_block_device(hb_ctx *ctx, hb_pair **dev_pairs_out, int64_t *n_out);
+
+/*
+ * R x S with S streamed from host memory: R must be loaded (side 0); S's
+ * columns (host pointers, same column order as used by the MDs' col_s) are
+ * copied in chunks of chunk_bytes through pinned buffers, and every chunk is
+ * encoded, blocked and evaluated while the next one is in flight.  Output as
+ * hb_block (tid2 indexes S as given).
+ */
+HB_API hb_status hb_block_stream(hb_ctx *ctx, int64_t n_rows_s, int32_t n_cols, const hb_column *cols_s,
+                          hb_pair **pairs_out, int64_t *n_out);
+
+/*
+ * Batched form: the loaded R holds n_jobs independent relations stacked by
+ * rows; job j is rows [job_rows[j], job_rows[j+1]).  Every job is blocked
+ * with the context's MDs in one persistent work-queue launch sequence (replayed
+ * from a CUDA graph when the shapes repeat).  Pairs use job-local row ids;
+ * job j's pairs are (*pairs_out)[job_pairs_out[j] .. job_pairs_out[j+1]),
+ * each range sorted.  job_pairs_out has n_jobs + 1 entries (caller-owned).
+ */
+HB_API hb_status hb_block_batch(hb_ctx *ctx, int32_t n_jobs, const int64_t *job_rows, hb_pair **pairs_out,
+                         int64_t *job_pairs_out);
+
+HB_API void hb_free_pairs(hb_pair *pairs);
+HB_API hb_status hb_get_stats(const hb_ctx *ctx, hb_stats *out);
+
+/*
+ * Order predicates and MDs from given sp / cost values only (no data, no GPU):
+ * the pure host part of hb_plan.  mds are given as predicate ids:
+ * md_pred[md_start[m] .. md_start[m+1]).  Writes the flattened program
+ * (program_out, n_prog_out, skipping ids with skip[p] != 0), the per-MD
+ * checkpoint index (cp_out[m], -1 when none) and the DFS MD order.
+ */
+HB_API hb_status hb_plan_order(int32_t n_preds, const double *sp, const double *cost, int32_t n_mds,
+                        const int32_t *md_start, const int32_t *md_pred, const uint8_t *skip,
+                        int32_t *program_out, int32_t *n_prog_out, int32_t *cp_out, int32_t *md_order_out);
+
+/* ---------------- learned cost model (small MLP, 32 -> 64 -> 64 -> 1, ReLU) ----------------
+ * Section 4.2 ("Shallow NNs", "Estimated cost") estimates predicate cost with
+ * a shallow network trained on historical logs.  Here two such networks
+ * predict, per predicate, its log cost per evaluated pair and the logit of its
+ * pass rate from HB_FEATURES features of sampled column statistics.
+ */
+#define HB_FEATURES 32
+#define HB_MLP_PARAMS (32 * 64 + 64 + 64 * 64 + 64 + 64 + 1)   /* W1 b1 W2 b2 W3 b3, row-major */
+
+/* One logged predicate evaluation record of the blocker. */
+typedef struct {
+    float features[HB_FEATURES];
+    float log_cost;          /* log(mean device cycles per evaluation) */
+    float logit_pass;        /* logit(pass rate), clamped to [-12, 12] */
+    int64_t evaluated;       /* evaluations counted */
+    int64_t passed;
+    int32_t pred;            /* distinct predicate id in the context */
+    int32_t kind;
+} hb_pred_log;
+
+/*
+ * Run the current plan once with per-predicate instrumentation (evaluations,
+ * passes and clock cycles per predicate) and append one record per
+ * non-equality predicate to out (capacity cap).  *n_out receives the count.
+ */
+HB_API hb_status hb_log_predicates(hb_ctx *ctx, hb_pred_log *out, int32_t cap, int32_t *n_out);
+
+/* Features the cost model sees for each distinct predicate of the current plan. */
+HB_API hb_status hb_predicate_features(hb_ctx *ctx, float *features_out, int32_t cap_preds, int32_t *n_out);
+
+/*
+ * Train the two networks on the GPU with the library's own forward, backward
+ * and Adam kernels (FP32, mean squared error): rows are n records of
+ * HB_FEATURES floats (host), targets y_cost[n], y_sel[n] (host).  The trained
+ * weights become the context's model (used by HB_PLAN_LEARNED).  Returns the
+ * final training losses in loss_out[2] (optional).
+ */
+HB_API hb_status hb_train_cost_model(hb_ctx *ctx, int32_t n, const float *X, const float *y_cost, const float *y_sel,
+                              int32_t epochs, float lr, uint64_t seed, float *loss_out);
+
+/* Copy the model weights out (2 x HB_MLP_PARAMS floats) or in. */
+HB_API hb_status hb_get_cost_model(hb_ctx *ctx, float *params_out);
+HB_API hb_status hb_set_cost_model(hb_ctx *ctx, const float *params);
+
+/*
+ * MLP kernels on device buffers (all pointers device memory, row-major):
+ * X [n, 32] fp32, params [HB_MLP_PARAMS] fp32, y [n] fp32.
+ * hb_mlp_forward_bf16 rounds X, weights and hidden activations to bfloat16
+ * and accumulates in fp32.  hb_mlp_backward computes the gradient of
+ * mean((y - t)^2) into grad [HB_MLP_PARAMS] (overwritten).  hb_adam_step
+ * applies Adam (Kingma & Ba) step number `step` (1-based) in place.
+ * `stream` is a cudaStream_t (NULL = default stream).
+ */
+HB_API hb_status hb_mlp_forward(const float *X, int32_t n, const float *params, float *y, void *stream);
+HB_API hb_status hb_mlp_forward_bf16(const float *X, int32_t n, const float *params, float *y, void *stream);
+HB_API hb_status hb_mlp_backward(const float *X, const float *t, int32_t n, const float *params, float *grad,
+                          void *stream);
+HB_API hb_status hb_adam_step(float *params, const float *grad, float *m, float *v, int32_t n_params, int32_t step,
+                       float lr, float beta1, float beta2, float eps, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HB_H */

@@ -1,0 +1,1043 @@
+// libhb C-ABI: context, table loading, rules, planning and the blocking
+// pipelines (self-join, R x S, streamed R x S, batched jobs).
+//
+// Pipeline of one blocking call (Section 3 overview, GB300 form):
+//   encode    : exact dictionary codes of the equality keys, per-string
+//               features for edit distance / q-gram Jaccard, packed records;
+//   plan      : Section 4.2 ordering + execution tree -> sequential program;
+//   blocks    : per MD, tuples grouped by all of its equality keys;
+//   evaluate  : tiles of every block's pair space, persistent work queue;
+//   output    : radix sort of the packed pairs, copy to the caller.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <numeric>
+#include <random>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "hb_ctx.h"
+
+namespace hb {
+
+static thread_local std::string g_err;
+
+hb_status fail(hb_status st, const std::string &msg) {
+    g_err = msg;
+    return st;
+}
+
+}  // namespace hb
+
+using namespace hb;
+
+namespace hb {
+
+hb_status grow(hb_ctx *c, Buf &b, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    if (b.bytes >= bytes) return HB_OK;
+    if (b.p) cudaFreeAsync(b.p, c->stream);
+    b.p = nullptr;
+    b.bytes = 0;
+    size_t want = bytes + bytes / 8;
+    cudaError_t e = cudaMallocAsync(&b.p, want, c->stream);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        b.p = nullptr;
+        return fail(HB_ERR_OOM, "device allocation of " + std::to_string(want) + " bytes failed");
+    }
+    b.bytes = want;
+    return HB_OK;
+}
+
+
+void free_buf(hb_ctx *c, Buf &b) {
+    if (b.p) cudaFreeAsync(b.p, c->stream);
+    b.p = nullptr;
+    b.bytes = 0;
+}
+
+static void free_side_encoding(hb_ctx *c, SideData &s) {
+    if (s.rec) cudaFreeAsync(s.rec, c->stream);
+    s.rec = nullptr;
+    for (auto g : s.grams)
+        if (g) cudaFreeAsync(g, c->stream);
+    s.grams.clear();
+    s.encoded = false;
+}
+
+static void free_side(hb_ctx *c, SideData &s) {
+    free_side_encoding(c, s);
+    for (void *p : s.allocs) cudaFreeAsync(p, c->stream);
+    s.allocs.clear();
+    s.cols.clear();
+    s.n = 0;
+}
+
+static void free_dicts(hb_ctx *c) {
+    for (auto d : c->dict)
+        if (d) cudaFreeAsync(d, c->stream);
+    c->dict.clear();
+    c->dict_cap.clear();
+}
+
+static void invalidate_encoding(hb_ctx *c) {
+    free_side_encoding(c, c->side[0]);
+    free_side_encoding(c, c->side[1]);
+    free_dicts(c);
+}
+
+hb_status dmalloc(hb_ctx *c, void **p, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMallocAsync(p, bytes, c->stream);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return fail(HB_ERR_OOM, "device allocation of " + std::to_string(bytes) + " bytes failed");
+    }
+    return HB_OK;
+}
+
+static hb_status ensure_pinned(hb_ctx *c) {
+    size_t want = c->opt.chunk_bytes ? c->opt.chunk_bytes : (256ull << 20);
+    if (c->pin_bytes == want) return HB_OK;
+    for (int b = 0; b < 2; b++) {
+        if (c->pin[b]) {
+            cudaEventSynchronize(c->pin_ev[b]);
+            cudaFreeHost(c->pin[b]);
+        }
+        c->pin[b] = nullptr;
+    }
+    for (int b = 0; b < 2; b++) {
+        HB_CUDA(cudaMallocHost(&c->pin[b], want));
+        if (!c->pin_ev[b]) HB_CUDA(cudaEventCreateWithFlags(&c->pin_ev[b], cudaEventDisableTiming));
+    }
+    c->pin_bytes = want;
+    return HB_OK;
+}
+
+// host -> device through the two pinned chunks: the copy of chunk i into
+// pinned memory overlaps the DMA of chunk i-1.
+hb_status upload(hb_ctx *c, void *dst, const void *src, size_t bytes) {
+    if (bytes == 0) return HB_OK;
+    HB_TRY(ensure_pinned(c));
+    size_t off = 0;
+    int i = 0;
+    while (off < bytes) {
+        const int b = i & 1;
+        const size_t len = std::min(c->pin_bytes, bytes - off);
+        HB_CUDA(cudaEventSynchronize(c->pin_ev[b]));
+        memcpy(c->pin[b], static_cast<const char *>(src) + off, len);
+        HB_CUDA(cudaMemcpyAsync(static_cast<char *>(dst) + off, c->pin[b], len, cudaMemcpyHostToDevice, c->stream));
+        HB_CUDA(cudaEventRecord(c->pin_ev[b], c->stream));
+        off += len;
+        i++;
+    }
+    return HB_OK;
+}
+
+static hb_status copy_in(hb_ctx *c, void *dst, const void *src, size_t bytes, bool on_device) {
+    if (bytes == 0) return HB_OK;
+    if (on_device) {
+        HB_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, c->stream));
+        return HB_OK;
+    }
+    return upload(c, dst, src, bytes);
+}
+
+}  // namespace hb
+
+// ===================================================================== context
+extern "C" const char *hb_last_error(void) { return g_err.c_str(); }
+extern "C" const char *hb_version(void) { return "libhb 0.1 (sm_103a)"; }
+
+extern "C" hb_status hb_create(hb_ctx **out, const hb_options *opt) {
+    if (!out) return fail(HB_ERR_ARG, "hb_create: out is NULL");
+    *out = nullptr;
+    hb_ctx *c = new (std::nothrow) hb_ctx();
+    if (!c) return fail(HB_ERR_OOM, "hb_create: host allocation failed");
+    if (opt) c->opt = *opt;
+    if (c->opt.tile != 0 && c->opt.tile != 32 && c->opt.tile != 64) {
+        delete c;
+        return fail(HB_ERR_ARG, "hb_create: tile must be 0, 32 or 64");
+    }
+    c->device = c->opt.device;
+    cudaError_t e = cudaSetDevice(c->device);
+    if (e != cudaSuccess) {
+        delete c;
+        return fail(HB_ERR_CUDA, std::string("hb_create: cudaSetDevice: ") + cudaGetErrorString(e));
+    }
+    cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, c->device);
+    if (c->opt.stream) {
+        c->stream = static_cast<cudaStream_t>(c->opt.stream);
+    } else {
+        e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            delete c;
+            return fail(HB_ERR_CUDA, std::string("hb_create: stream: ") + cudaGetErrorString(e));
+        }
+        c->own_stream = true;
+    }
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, c->device) == cudaSuccess) {
+        uint64_t thr = UINT64_MAX;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    c->stats.tile = 32;
+    *out = c;
+    return HB_OK;
+}
+
+extern "C" void hb_destroy(hb_ctx *c) {
+    if (!c) return;
+    cudaSetDevice(c->device);
+    cudaStreamSynchronize(c->stream);
+    free_side(c, c->side[0]);
+    free_side(c, c->side[1]);
+    free_dicts(c);
+    Buf *bufs[] = {&c->w_table, &c->w_slot_r, &c->w_slot_s, &c->w_count_r, &c->w_count_s, &c->w_start_r,
+                   &c->w_start_s, &c->w_cursor, &c->w_members_r, &c->w_members_s, &c->w_blocks, &c->w_tiles,
+                   &c->w_prefix, &c->w_scan, &c->w_out, &c->w_alt, &c->w_sort, &c->w_pairs, &c->w_counters,
+                   &c->w_lut, &c->w_log, &c->w_jac};
+    for (Buf *b : bufs) free_buf(c, *b);
+    cudaStreamSynchronize(c->stream);
+    for (int b = 0; b < 2; b++) {
+        if (c->pin[b]) cudaFreeHost(c->pin[b]);
+        if (c->pin_ev[b]) cudaEventDestroy(c->pin_ev[b]);
+    }
+    if (c->own_stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+// ===================================================================== tables
+extern "C" hb_status hb_load_table(hb_ctx *c, int32_t side, int64_t n_rows, int32_t n_cols, const hb_column *cols,
+                                   int32_t on_device) {
+    if (!c) return fail(HB_ERR_ARG, "hb_load_table: ctx is NULL");
+    if (side != 0 && side != 1) return fail(HB_ERR_ARG, "hb_load_table: side must be 0 (R) or 1 (S)");
+    if (n_rows < 0 || n_rows >= (1ll << 30)) return fail(HB_ERR_ARG, "hb_load_table: n_rows must be in [0, 2^30)");
+    if (n_cols < 0 || n_cols > 1024 || (n_cols > 0 && !cols)) return fail(HB_ERR_ARG, "hb_load_table: bad columns");
+    cudaSetDevice(c->device);
+    for (int k = 0; k < n_cols; k++) {
+        const hb_column &col = cols[k];
+        if (col.type < 0 || col.type > 2) return fail(HB_ERR_ARG, "hb_load_table: column " + std::to_string(k) + " has an unknown type");
+        if (n_rows > 0 && !col.data && !(col.type == HB_COL_STRING && col.data_bytes == 0))
+            return fail(HB_ERR_ARG, "hb_load_table: column " + std::to_string(k) + " has no data");
+        if (col.type == HB_COL_STRING) {
+            if (!col.offsets) return fail(HB_ERR_ARG, "hb_load_table: string column " + std::to_string(k) + " has no offsets");
+            if (!on_device) {
+                if (col.offsets[0] != 0) return fail(HB_ERR_ARG, "hb_load_table: offsets[0] must be 0");
+                for (int64_t i = 0; i < n_rows; i++)
+                    if (col.offsets[i + 1] < col.offsets[i])
+                        return fail(HB_ERR_ARG, "hb_load_table: offsets of column " + std::to_string(k) + " decrease at row " + std::to_string(i));
+                if ((uint64_t)col.offsets[n_rows] != col.data_bytes)
+                    return fail(HB_ERR_ARG, "hb_load_table: data_bytes != offsets[n] in column " + std::to_string(k));
+            }
+        }
+    }
+    SideData &S = c->side[side];
+    free_side(c, S);
+    invalidate_encoding(c);
+    c->planned = false;
+    S.n = n_rows;
+    S.cols.resize(n_cols);
+    for (int k = 0; k < n_cols; k++) {
+        const hb_column &col = cols[k];
+        DevCol &d = S.cols[k];
+        d.type = col.type;
+        d.n = n_rows;
+        void *p = nullptr;
+        if (col.type == HB_COL_STRING) {
+            d.nbytes = col.data_bytes;
+            HB_TRY(dmalloc(c, &p, col.data_bytes + 16));
+            S.allocs.push_back(p);
+            d.bytes = static_cast<uint8_t *>(p);
+            HB_TRY(copy_in(c, d.bytes, col.data, col.data_bytes, on_device));
+            HB_TRY(dmalloc(c, &p, sizeof(uint32_t) * (n_rows + 1)));
+            S.allocs.push_back(p);
+            d.off = static_cast<uint32_t *>(p);
+            HB_TRY(copy_in(c, d.off, col.offsets, sizeof(uint32_t) * (n_rows + 1), on_device));
+        } else {
+            HB_TRY(dmalloc(c, &p, 4 * (size_t)n_rows + 16));
+            S.allocs.push_back(p);
+            d.vals = p;
+            HB_TRY(copy_in(c, d.vals, col.data, 4 * (size_t)n_rows, on_device));
+        }
+        if (col.valid) {
+            HB_TRY(dmalloc(c, &p, (size_t)n_rows + 16));
+            S.allocs.push_back(p);
+            d.valid = static_cast<uint8_t *>(p);
+            HB_TRY(copy_in(c, d.valid, col.valid, (size_t)n_rows, on_device));
+        }
+    }
+    if (side == 0) c->stats.n_rows_r = n_rows;
+    else c->stats.n_rows_s = n_rows;
+    return HB_OK;
+}
+
+// ===================================================================== rules
+static bool same_pred(const hb_predicate &a, const hb_predicate &b) {
+    return a.kind == b.kind && a.col_t == b.col_t && a.col_s == b.col_s && a.k == b.k && a.q == b.q &&
+           a.num == b.num && a.den == b.den && a.delta == b.delta;
+}
+
+static hb_predicate normalize(hb_predicate p) {
+    hb_predicate r{};
+    r.kind = p.kind;
+    r.col_t = p.col_t;
+    r.col_s = p.col_s;
+    switch (p.kind) {
+    case HB_P_EQ_PREFIX: r.k = p.k; break;
+    case HB_P_ED_LE: r.k = p.k; break;
+    case HB_P_JACCARD_GE: {
+        r.q = p.q;
+        uint32_t g = std::gcd(p.num, p.den);
+        if (g == 0) g = 1;
+        r.num = p.num / g;
+        r.den = p.den / g;
+        break;
+    }
+    case HB_P_ABSDIFF_LE: r.delta = p.delta; break;
+    default: break;
+    }
+    return r;
+}
+
+extern "C" hb_status hb_add_md(hb_ctx *c, int32_t n_pred, const hb_predicate *preds, int32_t *md_id_out) {
+    if (!c) return fail(HB_ERR_ARG, "hb_add_md: ctx is NULL");
+    if (n_pred < 1 || n_pred > 10 || !preds) return fail(HB_ERR_ARG, "hb_add_md: an MD holds 1..10 predicates");
+    if ((int)c->md_raw.size() >= HB_MAX_MDS) return fail(HB_ERR_ARG, "hb_add_md: at most 64 MDs");
+    std::vector<hb_predicate> v;
+    for (int i = 0; i < n_pred; i++) {
+        const hb_predicate &p = preds[i];
+        if (p.kind < 0 || p.kind > 4) return fail(HB_ERR_ARG, "hb_add_md: unknown predicate kind");
+        if (p.col_t < 0 || p.col_s < 0) return fail(HB_ERR_ARG, "hb_add_md: negative column index");
+        if (p.kind == HB_P_EQ_PREFIX && p.k < 1) return fail(HB_ERR_ARG, "hb_add_md: prefix length must be >= 1");
+        if (p.kind == HB_P_ED_LE && (p.k < 0 || p.k > 31))
+            return fail(HB_ERR_ARG, "hb_add_md: edit-distance threshold must be in [0, 31]");
+        if (p.kind == HB_P_JACCARD_GE && (p.q < 1 || p.q > 4 || p.den < 1 || p.num > p.den))
+            return fail(HB_ERR_ARG, "hb_add_md: Jaccard needs q in 1..4 and 0 <= num <= den, den >= 1");
+        if (p.kind == HB_P_ABSDIFF_LE && !(p.delta >= 0.f))
+            return fail(HB_ERR_ARG, "hb_add_md: |a-b| threshold must be >= 0");
+        v.push_back(normalize(p));
+    }
+    c->md_raw.push_back(v);
+    c->planned = false;
+    invalidate_encoding(c);
+    if (md_id_out) *md_id_out = (int32_t)c->md_raw.size() - 1;
+    return HB_OK;
+}
+
+extern "C" hb_status hb_clear_mds(hb_ctx *c) {
+    if (!c) return fail(HB_ERR_ARG, "hb_clear_mds: ctx is NULL");
+    c->md_raw.clear();
+    c->planned = false;
+    invalidate_encoding(c);
+    return HB_OK;
+}
+
+// ===================================================================== plan
+namespace hb {
+
+bool is_self(hb_ctx *c) { return c->side[1].cols.empty() && c->side[1].n == 0; }
+
+static hb_status check_column(hb_ctx *c, int side, int col, int want_type, const char *what) {
+    const SideData &S = c->side[side];
+    if (col >= (int)S.cols.size())
+        return fail(HB_ERR_ARG, std::string(what) + ": column " + std::to_string(col) + " does not exist in " +
+                                    (side ? "S" : "R"));
+    if (want_type >= 0 && S.cols[col].type != want_type)
+        return fail(HB_ERR_ARG, std::string(what) + ": column " + std::to_string(col) + " has the wrong type");
+    return HB_OK;
+}
+
+// distinct predicates, equality keys, feature groups and the record layout
+static hb_status build_layout(hb_ctx *c, bool job_key) {
+    const bool self = is_self(c);
+    const int rs = self ? 0 : 1;
+    c->preds.clear();
+    c->md_preds.clear();
+    c->eqkeys.clear();
+    c->groups.clear();
+    for (auto &md : c->md_raw) {
+        std::vector<int> ids;
+        for (auto &p : md) {
+            if (self && p.col_t != p.col_s)
+                return fail(HB_ERR_ARG, "self-join predicates must compare the same column (col_t == col_s)");
+            const char *what = "predicate";
+            switch (p.kind) {
+            case HB_P_EQ: {
+                HB_TRY(check_column(c, 0, p.col_t, -1, what));
+                HB_TRY(check_column(c, rs, p.col_s, -1, what));
+                int tt = c->side[0].cols[p.col_t].type, ts = c->side[rs].cols[p.col_s].type;
+                if (tt != ts || tt == HB_COL_FP32)
+                    return fail(HB_ERR_ARG, "equality compares two string or two int32 columns");
+                break;
+            }
+            case HB_P_EQ_PREFIX:
+            case HB_P_ED_LE:
+            case HB_P_JACCARD_GE:
+                HB_TRY(check_column(c, 0, p.col_t, HB_COL_STRING, what));
+                HB_TRY(check_column(c, rs, p.col_s, HB_COL_STRING, what));
+                break;
+            case HB_P_ABSDIFF_LE:
+                HB_TRY(check_column(c, 0, p.col_t, HB_COL_FP32, what));
+                HB_TRY(check_column(c, rs, p.col_s, HB_COL_FP32, what));
+                break;
+            }
+            int id = -1;
+            for (size_t k = 0; k < c->preds.size(); k++)
+                if (same_pred(c->preds[k].p, p)) id = (int)k;
+            if (id < 0) {
+                if ((int)c->preds.size() >= HB_MAX_PREDS) return fail(HB_ERR_ARG, "too many distinct predicates");
+                PredInfo pi;
+                pi.p = p;
+                id = (int)c->preds.size();
+                c->preds.push_back(pi);
+            }
+            ids.push_back(id);
+        }
+        c->md_preds.push_back(ids);
+    }
+    // equality keys
+    for (auto &pi : c->preds) {
+        if (pi.p.kind != HB_P_EQ && pi.p.kind != HB_P_EQ_PREFIX) continue;
+        EqKey k{pi.p.col_t, pi.p.col_s, pi.p.kind == HB_P_EQ_PREFIX ? pi.p.k : -1};
+        int e = -1;
+        for (size_t j = 0; j < c->eqkeys.size(); j++)
+            if (c->eqkeys[j].col_t == k.col_t && c->eqkeys[j].col_s == k.col_s && c->eqkeys[j].prefix == k.prefix)
+                e = (int)j;
+        if (e < 0) {
+            e = (int)c->eqkeys.size();
+            c->eqkeys.push_back(k);
+        }
+        pi.eq_index = e;
+    }
+    c->n_eq_total = (int)c->eqkeys.size() + (job_key ? 1 : 0);
+    if (c->n_eq_total > MAX_EQ) return fail(HB_ERR_ARG, "at most 16 distinct equality keys");
+    int word = c->n_eq_total;
+    for (auto &pi : c->preds) {
+        if (pi.eq_index >= 0) continue;
+        int kind = pi.p.kind == HB_P_ED_LE ? OP_ED : pi.p.kind == HB_P_JACCARD_GE ? OP_JAC : OP_ABS;
+        int q = kind == OP_JAC ? pi.p.q : 0;
+        int g = -1;
+        for (size_t j = 0; j < c->groups.size(); j++) {
+            const FeatGroup &G = c->groups[j];
+            if (G.kind == kind && G.col_t == pi.p.col_t && G.col_s == pi.p.col_s && G.q == q) g = (int)j;
+        }
+        if (g < 0) {
+            FeatGroup G{kind, pi.p.col_t, pi.p.col_s, q, word};
+            word += kind == OP_ED ? FEAT_ED_WORDS : kind == OP_JAC ? FEAT_JAC_WORDS : FEAT_ABS_WORDS;
+            g = (int)c->groups.size();
+            c->groups.push_back(G);
+        }
+        pi.group = g;
+    }
+    c->W = (word + 3) & ~3;
+    if (c->W > 252) return fail(HB_ERR_ARG, "record too wide: too many distinct predicate columns");
+    // equality sets and the MDs that can own pairs
+    const int n_md = (int)c->md_preds.size();
+    c->eqset.assign(n_md, 0);
+    c->eqonly = 0;
+    for (int m = 0; m < n_md; m++) {
+        uint16_t s = job_key ? (uint16_t)(1u << c->eqkeys.size()) : 0;
+        bool has_other = false;
+        for (int id : c->md_preds[m]) {
+            if (c->preds[id].eq_index >= 0) s |= (uint16_t)(1u << c->preds[id].eq_index);
+            else has_other = true;
+        }
+        c->eqset[m] = s;
+        if (!has_other) c->eqonly |= 1ull << m;
+    }
+    c->active.clear();
+    for (int m = 0; m < n_md; m++) {
+        bool dominated = false;
+        for (int j = 0; j < m; j++)
+            if ((c->eqset[j] & c->eqset[m]) == c->eqset[j]) dominated = true;   // eqset_j subset of eqset_m
+        if (!dominated) c->active.push_back(m);
+    }
+    c->lut.clear();
+    if (c->n_eq_total <= LUT_MAX_EQ) {
+        c->lut.assign((size_t)1 << c->n_eq_total, 0);
+        for (uint32_t E = 0; E < c->lut.size(); E++)
+            for (int m = 0; m < n_md; m++)
+                if ((E & c->eqset[m]) == c->eqset[m]) c->lut[E] |= 1ull << m;
+    }
+    c->batch_layout = job_key;
+    return HB_OK;
+}
+
+// Section 4.2 statistics: sp from LSH bucket counts on a sample, cost from an
+// operation-count model over sampled string lengths.
+static hb_status plan_stats(hb_ctx *c, std::vector<double> &sp, std::vector<double> &cost) {
+    const int P = (int)c->preds.size();
+    sp.assign(P, 1.0);
+    cost.assign(P, 1.0);
+    const SideData &R = c->side[0];
+    if (P == 0 || R.n == 0) return HB_OK;
+    const int K = 1024;
+    const int n_samples = (int)std::min<int64_t>(R.n, 65536);
+    const int n_keep = std::min(n_samples, 4096);
+    std::vector<SampleSpec> specs(P);
+    for (int p = 0; p < P; p++) {
+        const hb_predicate &q = c->preds[p].p;
+        const DevCol &col = R.cols[q.col_t];
+        SampleSpec s{};
+        s.kind = q.kind;
+        s.type = col.type;
+        s.bytes = col.bytes;
+        s.off = col.off;
+        s.vals = col.vals;
+        s.valid = col.valid;
+        s.prefix = q.kind == HB_P_EQ_PREFIX ? q.k : -1;
+        s.q = q.kind == HB_P_JACCARD_GE ? q.q : 3;
+        s.delta = q.delta;
+        specs[p] = s;
+    }
+    Buf tmp;
+    size_t bytes = sizeof(SampleSpec) * P + sizeof(uint32_t) * ((size_t)P * K + P + 2 * (size_t)P * n_keep) + 1024;
+    HB_TRY(grow(c, tmp, bytes));
+    char *base = static_cast<char *>(tmp.p);
+    SampleSpec *d_specs = reinterpret_cast<SampleSpec *>(base);
+    uint32_t *hist = reinterpret_cast<uint32_t *>(base + ((sizeof(SampleSpec) * P + 255) & ~size_t(255)));
+    uint32_t *present = hist + (size_t)P * K;
+    uint32_t *lens = present + P;
+    uint32_t *grams = lens + (size_t)P * n_keep;
+    HB_CUDA(cudaMemcpyAsync(d_specs, specs.data(), sizeof(SampleSpec) * P, cudaMemcpyHostToDevice, c->stream));
+    HB_CUDA(cudaMemsetAsync(hist, 0, sizeof(uint32_t) * ((size_t)P * K + P), c->stream));
+    lsh_hist(d_specs, P, R.n, n_samples, K, hist, present, lens, grams, n_keep, c->stream);
+    std::vector<uint32_t> h((size_t)P * K + P + 2 * (size_t)P * n_keep);
+    HB_CUDA(cudaMemcpyAsync(h.data(), hist, sizeof(uint32_t) * h.size(), cudaMemcpyDeviceToHost, c->stream));
+    HB_CUDA(cudaStreamSynchronize(c->stream));
+    free_buf(c, tmp);
+    std::vector<double> sd(P, 0.0);
+    for (int p = 0; p < P; p++) {
+        const double n = h[(size_t)P * K + p];
+        double acc = 0;
+        for (int b = 0; b < K; b++) {
+            double d = h[(size_t)p * K + b] - n / K;
+            acc += d * d;
+        }
+        sd[p] = std::sqrt(acc / K);
+        // operation-count cost model (speed only)
+        const hb_predicate &q = c->preds[p].p;
+        double mlen = 0, mg = 0;
+        int cnt = 0;
+        for (int s = 0; s < n_keep; s++) {
+            uint32_t L = h[(size_t)P * K + P + (size_t)p * n_keep + s];
+            uint32_t G = h[(size_t)P * K + P + (size_t)P * n_keep + (size_t)p * n_keep + s];
+            if (L == NULL_LEN) continue;
+            mlen += L;
+            mg += G;
+            cnt++;
+        }
+        if (cnt) {
+            mlen /= cnt;
+            mg /= cnt;
+        }
+        switch (q.kind) {
+        case HB_P_EQ:
+        case HB_P_EQ_PREFIX: cost[p] = 1.0; break;
+        case HB_P_ABSDIFF_LE: cost[p] = 2.0; break;
+        case HB_P_ED_LE: cost[p] = 4.0 + 0.5 * mlen * (2.0 * q.k + 1.0); break;
+        case HB_P_JACCARD_GE: cost[p] = 6.0 + 2.0 * mg; break;
+        }
+    }
+    double mx = 0, mc = 0;
+    for (int p = 0; p < P; p++) {
+        mx = std::max(mx, sd[p]);
+        mc = std::max(mc, cost[p]);
+    }
+    for (int p = 0; p < P; p++) {
+        sp[p] = mx > 0 ? std::max(sd[p] / mx, 1e-6) : 1e-6;
+        cost[p] = mc > 0 ? std::max(cost[p] / mc, 1e-6) : 1e-6;
+    }
+    return HB_OK;
+}
+
+static hb_status finish_plan(hb_ctx *c, int mode, const std::vector<double> &sp, const std::vector<double> &cost) {
+    const int P = (int)c->preds.size();
+    const int n_md = (int)c->md_preds.size();
+    std::vector<uint8_t> skip(P, 0);
+    for (int p = 0; p < P; p++) skip[p] = c->preds[p].eq_index >= 0 ? 1 : 0;
+    std::vector<int> program;
+    std::vector<int> cp(n_md, -1);
+    std::vector<int> md_order;
+    if (mode == HB_PLAN_GIVEN_ORDER || mode == HB_PLAN_RANDOM) {
+        std::vector<int> mds(n_md);
+        std::iota(mds.begin(), mds.end(), 0);
+        std::vector<std::vector<int>> order(n_md);
+        for (int m = 0; m < n_md; m++) order[m] = c->md_preds[m];
+        if (mode == HB_PLAN_RANDOM) {
+            std::mt19937_64 rng(c->opt.seed ^ 0x5DEECE66Dull);
+            std::shuffle(mds.begin(), mds.end(), rng);
+            for (auto &o : order) std::shuffle(o.begin(), o.end(), rng);
+        }
+        std::vector<int> pos(P, -1);
+        for (int m : mds) {
+            md_order.push_back(m);
+            for (int p : order[m])
+                if (!skip[p] && pos[p] < 0) {
+                    pos[p] = (int)program.size();
+                    program.push_back(p);
+                }
+        }
+        for (int m = 0; m < n_md; m++)
+            for (int p : c->md_preds[m])
+                if (pos[p] > cp[m]) cp[m] = pos[p];
+    } else {
+        PlanResult R = make_plan(P, sp.data(), cost.data(), c->md_preds, skip);
+        program = R.program;
+        cp = R.cp;
+        md_order = R.md_order;
+    }
+    if ((int)program.size() > MAX_OPS) return fail(HB_ERR_ARG, "too many distinct non-equality predicates");
+    c->program = program;
+    c->ops.clear();
+    for (size_t k = 0; k < program.size(); k++) {
+        const PredInfo &pi = c->preds[program[k]];
+        const FeatGroup &G = c->groups[pi.group];
+        Op op{};
+        op.kind = (uint8_t)G.kind;
+        op.feat = (uint8_t)G.word;
+        op.k = (uint8_t)(pi.p.kind == HB_P_ED_LE ? pi.p.k : 0);
+        op.num = pi.p.num;
+        op.den = pi.p.den;
+        op.delta = pi.p.delta;
+        for (int m = 0; m < n_md; m++) {
+            for (int p : c->md_preds[m])
+                if (p == program[k]) op.need |= 1ull << m;
+            if (cp[m] == (int)k) op.cp |= 1ull << m;
+        }
+        c->ops.push_back(op);
+    }
+    hb_plan_info &I = c->info;
+    memset(&I, 0, sizeof(I));
+    I.mode = mode;
+    I.n_preds = P;
+    I.n_ops = (int)program.size();
+    I.n_eq = (int)c->eqkeys.size();
+    I.n_mds = n_md;
+    for (size_t k = 0; k < program.size(); k++) I.op_pred[k] = program[k];
+    for (size_t k = 0; k < md_order.size() && k < HB_MAX_MDS; k++) I.md_order[k] = md_order[k];
+    for (int p = 0; p < P; p++) {
+        I.sp[p] = sp.empty() ? 0 : sp[p];
+        I.cost[p] = cost.empty() ? 0 : cost[p];
+        I.pred_md[p] = -1;
+        for (int m = 0; m < n_md && I.pred_md[p] < 0; m++)
+            for (int q : c->md_preds[m])
+                if (q == p) I.pred_md[p] = m;
+    }
+    int tile = c->opt.tile ? c->opt.tile : 32;
+    c->tile = tile;
+    I.tile = tile;
+    c->planned = true;
+    return HB_OK;
+}
+
+
+hb_status do_plan(hb_ctx *c, int mode, bool job_key) {
+    if (c->md_raw.empty()) return fail(HB_ERR_STATE, "hb_plan: no MD added");
+    if (c->side[0].cols.empty() && c->side[0].n == 0) return fail(HB_ERR_STATE, "hb_plan: relation R not loaded");
+    if (mode < 0 || mode > 5) return fail(HB_ERR_ARG, "hb_plan: unknown mode");
+    cudaSetDevice(c->device);
+    auto t0 = std::chrono::steady_clock::now();
+    bool relayout = !c->planned || c->batch_layout != job_key || c->preds.empty();
+    if (relayout) {
+        invalidate_encoding(c);
+        HB_TRY(build_layout(c, job_key));
+    }
+    std::vector<double> sp, cost;
+    HB_TRY(plan_stats(c, sp, cost));
+    int applied = mode;
+    if (mode == HB_PLAN_LEARNED) {
+        bool ok = false;
+        std::vector<double> lsp = sp, lcost = cost;
+        HB_TRY(learned_stats(c, lsp, lcost, ok));
+        if (ok) {
+            sp = lsp;
+            cost = lcost;
+        } else {
+            applied = HB_PLAN_RULE_DATA;
+        }
+    } else if (mode == HB_PLAN_COST_FIRST) {
+        for (auto &x : sp) x = 0.5;
+    } else if (mode == HB_PLAN_SEL_FIRST) {
+        for (auto &x : cost) x = 1.0;
+    }
+    HB_TRY(finish_plan(c, applied, sp, cost));
+    c->info.mode = applied;
+    auto t1 = std::chrono::steady_clock::now();
+    c->stats.ms_plan = std::chrono::duration<double, std::milli>(t1 - t0).count();
+    return HB_OK;
+}
+
+}  // namespace hb
+
+extern "C" hb_status hb_plan(hb_ctx *c, int32_t mode, hb_plan_info *info_out) {
+    if (!c) return fail(HB_ERR_ARG, "hb_plan: ctx is NULL");
+    HB_TRY(do_plan(c, mode, false));
+    if (info_out) *info_out = c->info;
+    return HB_OK;
+}
+
+// ===================================================================== encode
+namespace hb {
+
+__global__ void k_job_codes(const int64_t *job_rows, int n_jobs, int64_t n, uint32_t *rec, int W, int word) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int lo = 0, hi = n_jobs;   // job_rows[lo] <= i < job_rows[hi]
+    while (hi - lo > 1) {
+        int mid = (lo + hi) >> 1;
+        if (job_rows[mid] <= i) lo = mid;
+        else hi = mid;
+    }
+    rec[i * W + word] = (uint32_t)lo;
+}
+
+hb_status encode_side(hb_ctx *c, int side) {
+    SideData &S = c->side[side];
+    if (S.encoded) return HB_OK;
+    const int64_t n = S.n;
+    const int W = c->W;
+    void *p = nullptr;
+    HB_TRY(dmalloc(c, &p, sizeof(uint32_t) * (size_t)W * (size_t)(n > 0 ? n : 1) + 64));
+    S.rec = static_cast<uint32_t *>(p);
+    HB_CUDA(cudaMemsetAsync(S.rec, 0, sizeof(uint32_t) * (size_t)W * (size_t)(n > 0 ? n : 1), c->stream));
+    // equality codes
+    Buf codes;
+    HB_TRY(grow(c, codes, sizeof(uint32_t) * (size_t)(n + 1)));
+    if (side == 0) {
+        free_dicts(c);
+        c->dict.assign(c->eqkeys.size(), nullptr);
+        c->dict_cap.assign(c->eqkeys.size(), 0);
+    }
+    for (size_t e = 0; e < c->eqkeys.size(); e++) {
+        const EqKey &k = c->eqkeys[e];
+        if (side == 0) {
+            uint64_t cap = pow2_at_least(std::max<uint64_t>(2 * (uint64_t)n, 1024));
+            HB_TRY(dmalloc(c, &p, sizeof(uint64_t) * cap));
+            c->dict[e] = static_cast<uint64_t *>(p);
+            c->dict_cap[e] = cap;
+            dict_build(S.cols[k.col_t], k.prefix, c->dict[e], cap, as<uint32_t>(codes), c->stream);
+        } else {
+            dict_probe(S.cols[k.col_s], k.prefix, c->side[0].cols[k.col_t], k.prefix, c->dict[e], c->dict_cap[e],
+                       as<uint32_t>(codes), c->stream);
+        }
+        code_feature(as<uint32_t>(codes), n, S.rec, W, (int)e, c->stream);
+    }
+    free_buf(c, codes);
+    // feature groups
+    S.grams.assign(c->groups.size(), nullptr);
+    Buf flag;
+    HB_TRY(grow(c, flag, 16));
+    HB_CUDA(cudaMemsetAsync(flag.p, 0, 16, c->stream));
+    for (size_t g = 0; g < c->groups.size(); g++) {
+        const FeatGroup &G = c->groups[g];
+        const DevCol &col = S.cols[side == 0 ? G.col_t : G.col_s];
+        if (G.kind == OP_ED) {
+            ed_features(col, S.rec, W, G.word, c->stream);
+        } else if (G.kind == OP_ABS) {
+            abs_feature(col, S.rec, W, G.word, c->stream);
+        } else {
+            HB_TRY(dmalloc(c, &p, sizeof(uint32_t) * (col.nbytes + 4)));
+            S.grams[g] = static_cast<uint32_t *>(p);
+            HB_TRY(grow(c, c->w_jac, jac_scratch_bytes(n)));
+            jac_features_impl(col, G.q, S.rec, W, G.word, S.grams[g], c->w_jac.p, as<unsigned int>(flag), c->n_sm,
+                              c->stream);
+        }
+    }
+    unsigned int too_long = 0;
+    HB_CUDA(cudaMemcpyAsync(&too_long, flag.p, sizeof(unsigned int), cudaMemcpyDeviceToHost, c->stream));
+    HB_CUDA(cudaStreamSynchronize(c->stream));
+    free_buf(c, flag);
+    HB_CUDA(cudaGetLastError());
+    if (too_long) return fail(HB_ERR_ARG, "a string compared by q-gram Jaccard has more than 8192 grams");
+    S.encoded = true;
+    return HB_OK;
+}
+
+}  // namespace hb
+
+// ===================================================================== blocking
+namespace hb {
+
+
+// counters layout (u64 words): 0 tile_counter, 1 out_count, 2 cand_count, 3 n_blocks (u32), 4 overflow (u32)
+static hb_status build_blocks(hb_ctx *c, const uint32_t *rec_r, int64_t n_r, const uint32_t *rec_s, int64_t n_s,
+                              bool self, unsigned long long *ctr, uint32_t &block_cap) {
+    const int W = c->W;
+    const uint64_t H = pow2_at_least(std::max<uint64_t>(2 * (uint64_t)std::max<int64_t>(n_r, 1), 1024));
+    const int na = (int)c->active.size();
+    const uint64_t per_md = self ? (uint64_t)(n_r / 2 + 1) : (uint64_t)std::min<int64_t>(n_r, n_s) + 1;
+    const uint64_t bc = std::min<uint64_t>(per_md * (uint64_t)std::max(na, 1), 0xFFFFFFF0ull);
+    block_cap = (uint32_t)bc;
+    HB_TRY(grow(c, c->w_table, sizeof(uint64_t) * H));
+    HB_TRY(grow(c, c->w_slot_r, sizeof(uint32_t) * (size_t)(n_r + 1)));
+    HB_TRY(grow(c, c->w_count_r, sizeof(uint32_t) * (H + 1)));
+    HB_TRY(grow(c, c->w_start_r, sizeof(uint32_t) * (H + 1)));
+    HB_TRY(grow(c, c->w_cursor, sizeof(uint32_t) * (H + 1)));
+    HB_TRY(grow(c, c->w_members_r, sizeof(uint32_t) * (size_t)std::max<int64_t>(n_r, 1) * std::max(na, 1)));
+    if (!self) {
+        HB_TRY(grow(c, c->w_slot_s, sizeof(uint32_t) * (size_t)(n_s + 1)));
+        HB_TRY(grow(c, c->w_count_s, sizeof(uint32_t) * (H + 1)));
+        HB_TRY(grow(c, c->w_start_s, sizeof(uint32_t) * (H + 1)));
+        HB_TRY(grow(c, c->w_members_s, sizeof(uint32_t) * (size_t)std::max<int64_t>(n_s, 1) * std::max(na, 1)));
+    }
+    HB_TRY(grow(c, c->w_blocks, sizeof(BlockDesc) * (size_t)bc));
+    HB_TRY(grow(c, c->w_tiles, sizeof(uint64_t) * ((size_t)bc + 1)));
+    HB_TRY(grow(c, c->w_prefix, sizeof(uint64_t) * ((size_t)bc + 1)));
+    HB_TRY(grow(c, c->w_scan, std::max(scan_tmp_bytes((int64_t)H + 1), scan_tmp_bytes((int64_t)bc + 1))));
+    uint32_t *n_blocks = reinterpret_cast<uint32_t *>(ctr + 3);
+    unsigned int *overflow = reinterpret_cast<unsigned int *>(ctr + 4);
+    for (int a = 0; a < na; a++) {
+        const int m = c->active[a];
+        int32_t words[MAX_EQ];
+        int nk = 0;
+        for (int e = 0; e < c->n_eq_total; e++)
+            if (c->eqset[m] & (1u << e)) words[nk++] = e;
+        group_build(rec_r, W, n_r, words, nk, as<uint64_t>(c->w_table), H, as<uint32_t>(c->w_slot_r), c->stream);
+        HB_CUDA(cudaMemsetAsync(c->w_count_r.p, 0, sizeof(uint32_t) * (H + 1), c->stream));
+        count_slots(as<uint32_t>(c->w_slot_r), n_r, as<uint32_t>(c->w_count_r), c->stream);
+        scan_exclusive_u32(as<uint32_t>(c->w_count_r), as<uint32_t>(c->w_start_r), (int64_t)H, nullptr, c->w_scan.p,
+                           c->w_scan.bytes, c->stream);
+        HB_CUDA(cudaMemsetAsync(c->w_cursor.p, 0, sizeof(uint32_t) * (H + 1), c->stream));
+        uint32_t *mem_r = as<uint32_t>(c->w_members_r) + (size_t)a * (size_t)std::max<int64_t>(n_r, 1);
+        scatter_slots(as<uint32_t>(c->w_slot_r), n_r, as<uint32_t>(c->w_start_r), as<uint32_t>(c->w_cursor), mem_r,
+                      c->stream);
+        if (self) {
+            emit_blocks(as<uint32_t>(c->w_count_r), as<uint32_t>(c->w_start_r), nullptr, nullptr, H, (uint32_t)m, 1,
+                        (uint32_t)((size_t)a * (size_t)std::max<int64_t>(n_r, 1)), 0, c->tile,
+                        as<BlockDesc>(c->w_blocks), as<uint64_t>(c->w_tiles), n_blocks, block_cap, overflow,
+                        c->stream);
+        } else {
+            group_probe(rec_s, n_s, rec_r, W, words, nk, as<uint64_t>(c->w_table), H, as<uint32_t>(c->w_slot_s),
+                        c->stream);
+            HB_CUDA(cudaMemsetAsync(c->w_count_s.p, 0, sizeof(uint32_t) * (H + 1), c->stream));
+            count_slots(as<uint32_t>(c->w_slot_s), n_s, as<uint32_t>(c->w_count_s), c->stream);
+            scan_exclusive_u32(as<uint32_t>(c->w_count_s), as<uint32_t>(c->w_start_s), (int64_t)H, nullptr,
+                               c->w_scan.p, c->w_scan.bytes, c->stream);
+            HB_CUDA(cudaMemsetAsync(c->w_cursor.p, 0, sizeof(uint32_t) * (H + 1), c->stream));
+            uint32_t *mem_s = as<uint32_t>(c->w_members_s) + (size_t)a * (size_t)std::max<int64_t>(n_s, 1);
+            scatter_slots(as<uint32_t>(c->w_slot_s), n_s, as<uint32_t>(c->w_start_s), as<uint32_t>(c->w_cursor),
+                          mem_s, c->stream);
+            emit_blocks(as<uint32_t>(c->w_count_r), as<uint32_t>(c->w_start_r), as<uint32_t>(c->w_count_s),
+                        as<uint32_t>(c->w_start_s), H, (uint32_t)m, 0,
+                        (uint32_t)((size_t)a * (size_t)std::max<int64_t>(n_r, 1)),
+                        (uint32_t)((size_t)a * (size_t)std::max<int64_t>(n_s, 1)), c->tile, as<BlockDesc>(c->w_blocks),
+                        as<uint64_t>(c->w_tiles), n_blocks, block_cap, overflow, c->stream);
+        }
+    }
+    clamp_blocks(n_blocks, block_cap, c->stream);
+    scan_exclusive_u64(as<uint64_t>(c->w_tiles), as<uint64_t>(c->w_prefix), (int64_t)bc, n_blocks, c->w_scan.p,
+                       c->w_scan.bytes, c->stream);
+    HB_CUDA(cudaGetLastError());
+    return HB_OK;
+}
+
+static EvalParams make_params(hb_ctx *c, const uint32_t *rec_r, const uint32_t *rec_s, int side_s, bool self,
+                              unsigned long long *ctr, int key_bits_s) {
+    EvalParams P;
+    memset(&P, 0, sizeof(P));
+    P.n_ops = (int)c->ops.size();
+    P.n_eq = c->n_eq_total;
+    P.W = c->W;
+    P.self_join = self ? 1 : 0;
+    P.n_md = (int)c->md_preds.size();
+    P.use_lut = c->lut.empty() ? 0 : 1;
+    P.tile = c->tile;
+    P.key_bits_s = key_bits_s;
+    P.eqonly = c->eqonly;
+    for (int m = 0; m < P.n_md; m++) P.eqset[m] = c->eqset[m];
+    for (size_t k = 0; k < c->ops.size(); k++) {
+        P.ops[k] = c->ops[k];
+        const PredInfo &pi = c->preds[c->program[k]];
+        const FeatGroup &G = c->groups[pi.group];
+        if (G.kind == OP_ED) {
+            P.ptr_r[k] = c->side[0].cols[G.col_t].bytes;
+            P.ptr_s[k] = self ? c->side[0].cols[G.col_t].bytes : c->side[side_s].cols[G.col_s].bytes;
+        } else if (G.kind == OP_JAC) {
+            P.ptr_r[k] = c->side[0].grams[pi.group];
+            P.ptr_s[k] = self ? c->side[0].grams[pi.group] : c->side[side_s].grams[pi.group];
+        }
+    }
+    P.rec_r = rec_r;
+    P.rec_s = rec_s;
+    P.lut = P.use_lut ? as<uint64_t>(c->w_lut) : nullptr;
+    P.members_r = as<uint32_t>(c->w_members_r);
+    P.members_s = self ? as<uint32_t>(c->w_members_r) : as<uint32_t>(c->w_members_s);
+    P.blocks = as<BlockDesc>(c->w_blocks);
+    P.n_blocks = reinterpret_cast<const uint32_t *>(ctr + 3);
+    P.tile_prefix = as<uint64_t>(c->w_prefix);
+    P.tile_counter = ctr + 0;
+    P.out = as<uint64_t>(c->w_out);
+    P.out_count = ctr + 1;
+    P.out_cap = (uint64_t)c->out_cap;
+    P.cand_count = ctr + 2;
+    P.claim = 2;
+    P.log = as<unsigned long long>(c->w_log);
+    return P;
+}
+
+hb_status ensure_ready(hb_ctx *c, bool job_key) {
+    if (!c->planned || c->batch_layout != job_key) HB_TRY(do_plan(c, HB_PLAN_RULE_DATA, job_key));
+    HB_TRY(encode_side(c, 0));
+    if (!is_self(c)) HB_TRY(encode_side(c, 1));
+    HB_TRY(grow(c, c->w_counters, 64 * sizeof(unsigned long long)));
+    if (!c->lut.empty()) {
+        HB_TRY(grow(c, c->w_lut, sizeof(uint64_t) * c->lut.size()));
+        HB_CUDA(cudaMemcpyAsync(c->w_lut.p, c->lut.data(), sizeof(uint64_t) * c->lut.size(), cudaMemcpyHostToDevice,
+                                c->stream));
+    }
+    HB_TRY(grow(c, c->w_log, sizeof(unsigned long long) * MAX_OPS * 8));
+    return HB_OK;
+}
+
+
+// blocks -> evaluation -> sorted packed keys; result keys in *sorted, count in res
+hb_status block_eval_sort(hb_ctx *c, const uint32_t *rec_r, int64_t n_r, const uint32_t *rec_s,
+                                 int64_t n_s, bool self, int side_s, int key_bits, int key_bits_s, int logging,
+                                 RunResult &res, uint64_t **sorted, Timer *tm) {
+    unsigned long long *ctr = as<unsigned long long>(c->w_counters);
+    HB_CUDA(cudaMemsetAsync(ctr, 0, 64 * sizeof(unsigned long long), c->stream));
+    if (logging) HB_CUDA(cudaMemsetAsync(c->w_log.p, 0, sizeof(unsigned long long) * MAX_OPS * 8, c->stream));
+    uint32_t block_cap = 0;
+    HB_TRY(build_blocks(c, rec_r, n_r, rec_s, n_s, self, ctr, block_cap));
+    if (tm) tm->mark();
+    if (c->out_cap == 0) c->out_cap = c->opt.out_capacity > 0 ? c->opt.out_capacity : std::max<int64_t>(1 << 20, n_r);
+    HB_TRY(grow(c, c->w_out, sizeof(uint64_t) * (size_t)c->out_cap));
+    const size_t smem = eval_smem_bytes(c->W, c->n_eq_total, c->lut.empty() ? 0 : 1, c->tile);
+    int bps = eval_blocks_per_sm(c->tile, logging, smem);
+    if (bps < 1) return fail(HB_ERR_ARG, "record too wide for the evaluation kernel's shared memory");
+    const int grid = bps * c->n_sm;
+    for (int attempt = 0; attempt < 2; attempt++) {
+        EvalParams P = make_params(c, rec_r, rec_s, side_s, self, ctr, key_bits_s);
+        HB_CUDA(launch_eval(P, grid, smem, logging, c->stream));
+        if (tm && attempt == 0) tm->mark();
+        unsigned long long h[5];
+        HB_CUDA(cudaMemcpyAsync(h, ctr, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+        HB_CUDA(cudaStreamSynchronize(c->stream));
+        if (h[4]) return fail(HB_ERR_INTERNAL, "block list overflow");
+        res.n_out = (int64_t)h[1];
+        res.cand = (int64_t)h[2];
+        res.blocks = (int64_t)(uint32_t)h[3];
+        if (res.n_out <= c->out_cap) break;
+        // the slab was too small: grow it to the exact count and evaluate again
+        c->out_cap = res.n_out + res.n_out / 8 + 1024;
+        HB_TRY(grow(c, c->w_out, sizeof(uint64_t) * (size_t)c->out_cap));
+        HB_CUDA(cudaMemsetAsync(ctr, 0, 3 * sizeof(unsigned long long), c->stream));
+        if (logging) HB_CUDA(cudaMemsetAsync(c->w_log.p, 0, sizeof(unsigned long long) * MAX_OPS * 8, c->stream));
+    }
+    {
+        uint64_t t = 0;
+        HB_CUDA(cudaMemcpyAsync(&t, as<uint64_t>(c->w_prefix) + res.blocks, sizeof(uint64_t), cudaMemcpyDeviceToHost,
+                                c->stream));
+        HB_CUDA(cudaStreamSynchronize(c->stream));
+        res.tiles = (int64_t)t;
+    }
+    HB_TRY(grow(c, c->w_alt, sizeof(uint64_t) * (size_t)std::max<int64_t>(res.n_out, 1)));
+    HB_TRY(grow(c, c->w_sort, radix_tmp_bytes(std::max<int64_t>(res.n_out, 1))));
+    radix_sort_u64(as<uint64_t>(c->w_out), as<uint64_t>(c->w_alt), res.n_out, nullptr, key_bits, c->w_sort.p,
+                   c->w_sort.bytes, c->stream, sorted);
+    HB_CUDA(cudaGetLastError());
+    if (tm) tm->mark();
+    return HB_OK;
+}
+
+hb_status deliver(hb_ctx *c, const uint64_t *keys, int64_t n, int key_bits_s, bool to_host, hb_pair **out) {
+    HB_TRY(grow(c, c->w_pairs, sizeof(hb_pair) * (size_t)std::max<int64_t>(n, 1)));
+    pack_pairs(keys, n, key_bits_s, as<hb_pair>(c->w_pairs), c->stream);
+    if (!to_host) {
+        *out = as<hb_pair>(c->w_pairs);
+        HB_CUDA(cudaStreamSynchronize(c->stream));
+        return HB_OK;
+    }
+    hb_pair *h = static_cast<hb_pair *>(malloc(sizeof(hb_pair) * (size_t)std::max<int64_t>(n, 1)));
+    if (!h) return fail(HB_ERR_OOM, "host allocation of the result failed");
+    if (n > 0) {
+        cudaError_t e = cudaMemcpyAsync(h, c->w_pairs.p, sizeof(hb_pair) * (size_t)n, cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) {
+            free(h);
+            return fail(HB_ERR_CUDA, std::string("result copy: ") + cudaGetErrorString(e));
+        }
+    }
+    *out = h;
+    return HB_OK;
+}
+
+static hb_status run_block(hb_ctx *c, hb_pair **out, int64_t *n_out, bool to_host) {
+    if (!out || !n_out) return fail(HB_ERR_ARG, "hb_block: output pointers are NULL");
+    *out = nullptr;
+    *n_out = 0;
+    if (c->side[0].cols.empty() && c->side[0].n == 0) return fail(HB_ERR_STATE, "hb_block: relation R not loaded");
+    cudaSetDevice(c->device);
+    auto w0 = std::chrono::steady_clock::now();
+    Timer tm(c->stream);
+    tm.mark();
+    HB_TRY(ensure_ready(c, false));
+    tm.mark();
+    const bool self = is_self(c);
+    const int64_t nr = c->side[0].n, ns = self ? nr : c->side[1].n;
+    const int kbs = bits_for((uint64_t)std::max<int64_t>(ns, 2));
+    const int kb = kbs + bits_for((uint64_t)std::max<int64_t>(nr, 2));
+    RunResult res;
+    uint64_t *sorted = nullptr;
+    HB_TRY(block_eval_sort(c, c->side[0].rec, nr, self ? c->side[0].rec : c->side[1].rec, ns, self, 1, kb, kbs, 0,
+                           res, &sorted, &tm));
+    HB_TRY(deliver(c, sorted, res.n_out, kbs, to_host, out));
+    tm.mark();
+    HB_CUDA(cudaStreamSynchronize(c->stream));
+    *n_out = res.n_out;
+    hb_stats &S = c->stats;
+    S.candidate_pairs = res.cand;
+    S.emitted_pairs = res.n_out;
+    S.tiles = res.tiles;
+    S.blocks = res.blocks;
+    S.ms_encode = tm.ms(0, 1);
+    S.ms_block_build = tm.ms(1, 2);
+    S.ms_eval = tm.ms(2, 3);
+    S.ms_sort = tm.ms(3, 4);
+    S.ms_d2h = tm.ms(4, 5);
+    S.ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - w0).count();
+    S.tile = c->tile;
+    S.n_mds = (int)c->md_preds.size();
+    return HB_OK;
+}
+
+}  // namespace hb
+
+extern "C" hb_status hb_block(hb_ctx *c, hb_pair **pairs_out, int64_t *n_out) {
+    if (!c) return fail(HB_ERR_ARG, "hb_block: ctx is NULL");
+    return run_block(c, pairs_out, n_out, true);
+}
+
+extern "C" hb_status hb_block_device(hb_ctx *c, hb_pair **dev_pairs_out, int64_t *n_out) {
+    if (!c) return fail(HB_ERR_ARG, "hb_block_device: ctx is NULL");
+    return run_block(c, dev_pairs_out, n_out, false);
+}
+
+extern "C" void hb_free_pairs(hb_pair *pairs) { free(pairs); }
+
+extern "C" hb_status hb_get_stats(const hb_ctx *c, hb_stats *out) {
+    if (!c || !out) return fail(HB_ERR_ARG, "hb_get_stats: NULL argument");
+    *out = c->stats;
+    size_t tot = 0;
+    for (int s = 0; s < 2; s++) {
+        for (auto &col : c->side[s].cols) tot += col.nbytes + (col.off ? 4 * (col.n + 1) : 0) + (col.vals ? 4 * col.n : 0);
+        if (c->side[s].rec) tot += (size_t)4 * c->W * c->side[s].n;
+    }
+    const Buf *bufs[] = {&c->w_table, &c->w_slot_r, &c->w_slot_s, &c->w_count_r, &c->w_count_s, &c->w_start_r,
+                         &c->w_start_s, &c->w_cursor, &c->w_members_r, &c->w_members_s, &c->w_blocks, &c->w_tiles,
+                         &c->w_prefix, &c->w_scan, &c->w_out, &c->w_alt, &c->w_sort, &c->w_pairs};
+    for (const Buf *b : bufs) tot += b->bytes;
+    out->device_bytes = (int64_t)tot;
+    return HB_OK;
+}

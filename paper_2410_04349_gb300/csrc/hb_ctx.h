@@ -1,0 +1,178 @@
+// Context of the libhb C-ABI (shared by the host-side translation units).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "hb_internal.h"
+
+namespace hb {
+
+hb_status fail(hb_status st, const std::string &msg);
+
+#define HB_CUDA(call)                                                                              \
+    do {                                                                                           \
+        cudaError_t e__ = (call);                                                                  \
+        if (e__ != cudaSuccess)                                                                    \
+            return ::hb::fail(e__ == cudaErrorMemoryAllocation ? HB_ERR_OOM : HB_ERR_CUDA,         \
+                              std::string(#call) + ": " + cudaGetErrorString(e__));                \
+    } while (0)
+
+#define HB_TRY(expr)                  \
+    do {                              \
+        hb_status s__ = (expr);       \
+        if (s__ != HB_OK) return s__; \
+    } while (0)
+
+static inline uint64_t pow2_at_least(uint64_t x) {
+    uint64_t p = 1;
+    while (p < x) p <<= 1;
+    return p;
+}
+static inline int bits_for(uint64_t n) {   // bits to hold values 0..n-1 (at least 1)
+    int b = 1;
+    while (b < 63 && (1ull << b) < n) b++;
+    return b;
+}
+
+struct EqKey {
+    int col_t, col_s, prefix;   // prefix < 0: whole value
+};
+struct FeatGroup {
+    int kind;   // OP_ED, OP_JAC, OP_ABS
+    int col_t, col_s, q;
+    int word;
+};
+struct PredInfo {
+    hb_predicate p;
+    int eq_index = -1;   // equality key (EQ / EQ_PREFIX)
+    int group = -1;      // feature group (others)
+};
+
+// device buffer that grows on demand (stream-ordered allocator)
+struct Buf {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+struct SideData {
+    int64_t n = 0;
+    std::vector<DevCol> cols;
+    std::vector<void *> allocs;
+    // encoded state
+    uint32_t *rec = nullptr;
+    std::vector<uint32_t *> grams;   // per feature group (JAC only)
+    bool encoded = false;
+};
+
+}  // namespace hb
+
+using hb::Buf;
+using hb::DevCol;
+using hb::EqKey;
+using hb::FeatGroup;
+using hb::Op;
+using hb::PredInfo;
+using hb::SideData;
+
+struct hb_ctx {
+    int device = 0;
+    int n_sm = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    hb_options opt{};
+    SideData side[2];
+    // rules
+    std::vector<std::vector<hb_predicate>> md_raw;
+    // plan
+    bool planned = false;
+    bool batch_layout = false;   // extra job key
+    std::vector<PredInfo> preds;
+    std::vector<std::vector<int>> md_preds;
+    std::vector<EqKey> eqkeys;
+    std::vector<FeatGroup> groups;
+    int W = 4;
+    int n_eq_total = 0;            // eqkeys + job key
+    std::vector<uint16_t> eqset;
+    std::vector<int> active;       // MDs whose blocks can own pairs
+    std::vector<int> program;      // predicate ids
+    std::vector<Op> ops;
+    uint64_t eqonly = 0;
+    std::vector<uint64_t> lut;
+    hb_plan_info info{};
+    int tile = 32;
+    // R-side dictionaries (kept for probing S)
+    std::vector<uint64_t *> dict;
+    std::vector<uint64_t> dict_cap;
+    // work buffers
+    Buf w_table, w_slot_r, w_slot_s, w_count_r, w_count_s, w_start_r, w_start_s, w_cursor, w_members_r,
+        w_members_s, w_blocks, w_tiles, w_prefix, w_scan, w_out, w_alt, w_sort, w_pairs, w_counters, w_lut, w_log,
+        w_jac;
+    int64_t out_cap = 0;
+    // stats
+    hb_stats stats{};
+    // learned model: [cost net | selectivity net]
+    std::vector<float> model;
+    bool model_ok = false;
+    // pinned staging
+    void *pin[2] = {nullptr, nullptr};
+    cudaEvent_t pin_ev[2] = {nullptr, nullptr};
+    size_t pin_bytes = 0;
+    // results
+    hb_pair *dev_result = nullptr;
+    size_t dev_result_bytes = 0;
+};
+
+
+namespace hb {
+
+struct RunResult {
+    int64_t n_out = 0;
+    int64_t cand = 0;
+    int64_t tiles = 0;
+    int64_t blocks = 0;
+};
+
+struct Timer {
+    cudaEvent_t e[8];
+    int n = 0;
+    cudaStream_t s;
+    explicit Timer(cudaStream_t st) : s(st) {
+        for (auto &x : e) cudaEventCreate(&x);
+    }
+    ~Timer() {
+        for (auto &x : e) cudaEventDestroy(x);
+    }
+    void mark() {
+        if (n < 8) cudaEventRecord(e[n++], s);
+    }
+    float ms(int a, int b) {
+        float v = 0;
+        if (a < n && b < n) cudaEventElapsedTime(&v, e[a], e[b]);
+        return v;
+    }
+};
+
+hb_status grow(hb_ctx *c, Buf &b, size_t bytes);
+void free_buf(hb_ctx *c, Buf &b);
+hb_status dmalloc(hb_ctx *c, void **p, size_t bytes);
+hb_status upload(hb_ctx *c, void *dst, const void *src, size_t bytes);
+hb_status do_plan(hb_ctx *c, int mode, bool job_key);
+hb_status encode_side(hb_ctx *c, int side);
+hb_status ensure_ready(hb_ctx *c, bool job_key);
+bool is_self(hb_ctx *c);
+hb_status block_eval_sort(hb_ctx *c, const uint32_t *rec_r, int64_t n_r, const uint32_t *rec_s, int64_t n_s,
+                          bool self, int side_s, int key_bits, int key_bits_s, int logging, RunResult &res,
+                          uint64_t **sorted, Timer *tm);
+hb_status deliver(hb_ctx *c, const uint64_t *keys, int64_t n, int key_bits_s, bool to_host, hb_pair **out);
+hb_status learned_stats(hb_ctx *c, std::vector<double> &sp, std::vector<double> &cost, bool &ok);
+
+template <typename T>
+static inline T *as(Buf &b) {
+    return static_cast<T *>(b.p);
+}
+
+}  // namespace hb

@@ -1,0 +1,175 @@
+// Internal declarations shared by the libhb translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "hb.h"
+
+namespace hb {
+
+constexpr uint32_t NULL_CODE = 0xFFFFFFFFu;     // missing value: equal to nothing
+constexpr uint32_t NOMATCH_CODE = 0xFFFFFFFEu;  // S value that no R tuple holds
+constexpr uint32_t NULL_LEN = 0xFFFFFFFFu;      // missing string
+constexpr uint64_t EMPTY_SLOT = 0xFFFFFFFFFFFFFFFFull;
+constexpr int MAX_EQ = 16;     // distinct equality keys per context
+constexpr int MAX_OPS = 48;    // non-equality predicates in one program
+constexpr int MAX_MD = 64;
+constexpr int LUT_MAX_EQ = 10; // equality-match -> MD-mask lookup table up to 2^10 entries
+
+// ---- device-side column of one relation ----
+struct DevCol {
+    int32_t type = 0;
+    int64_t n = 0;
+    uint8_t *bytes = nullptr;   // STRING
+    uint64_t nbytes = 0;
+    uint32_t *off = nullptr;    // STRING: n+1
+    void *vals = nullptr;       // INT32 / FP32
+    uint8_t *valid = nullptr;   // NULL = all present
+};
+
+// ---- evaluation program (Section 5.1: sequential execution path) ----
+enum OpKind : uint8_t { OP_ED = 0, OP_JAC = 1, OP_ABS = 2 };
+
+struct Op {
+    uint8_t kind;
+    uint8_t feat;       // first record word of this predicate's feature group
+    uint8_t k;          // ED threshold
+    uint8_t pad;
+    uint32_t num, den;  // Jaccard threshold
+    float delta;        // |a-b| threshold
+    uint32_t pad2;
+    uint64_t need;      // MDs whose precondition holds this predicate
+    uint64_t cp;        // MDs whose last remaining predicate is this one
+};
+
+// feature group sizes (record words)
+constexpr int FEAT_ED_WORDS = 6;   // len, byte offset, 16 x 8-bit character-bin counts
+constexpr int FEAT_JAC_WORDS = 10; // unique gram count, gram offset, 32 x 8-bit gram-bin counts
+constexpr int FEAT_ABS_WORDS = 1;  // fp32 value bits (NaN when missing)
+
+struct BlockDesc {
+    uint32_t md;
+    uint32_t n_r;       // members on the row side
+    uint32_t start_r;   // into members_r
+    uint32_t n_s;       // members on the column side (self-join: = n_r)
+    uint32_t start_s;   // into members_s (self-join: = start_r)
+    uint32_t pad;
+};
+
+struct EvalParams {
+    int32_t n_ops;
+    int32_t n_eq;
+    int32_t W;              // record words (multiple of 4)
+    int32_t self_join;
+    int32_t n_md;
+    int32_t use_lut;
+    int32_t tile;           // 32 or 64
+    int32_t key_bits_s;     // packed output key = tid1 << key_bits_s | tid2
+    uint64_t eqonly;        // MDs without any non-equality predicate
+    uint16_t eqset[MAX_MD]; // equality keys of each MD (bit e = key e)
+    Op ops[MAX_OPS];
+    const void *ptr_r[MAX_OPS];   // ED: string bytes of R; JAC: gram array of R
+    const void *ptr_s[MAX_OPS];
+    const uint32_t *rec_r;
+    const uint32_t *rec_s;
+    const uint64_t *lut;          // 2^n_eq MD masks (use_lut)
+    const uint32_t *members_r;
+    const uint32_t *members_s;
+    const BlockDesc *blocks;
+    const uint32_t *n_blocks;     // device count
+    const uint64_t *tile_prefix;  // n_blocks + 1 entries
+    unsigned long long *tile_counter;
+    uint64_t *out;
+    unsigned long long *out_count;
+    uint64_t out_cap;
+    unsigned long long *cand_count;
+    uint32_t row_base, col_base;  // added to member ids when packing (chunked S)
+    int32_t claim;                // tiles per atomic claim
+    // instrumentation (logging variant only)
+    unsigned long long *log;      // per op: [evaluated, passed, cycles] (3 * MAX_OPS)
+};
+
+// ---- kernels / launchers (defined in the .cu files) ----
+// k_sort.cu
+size_t scan_tmp_bytes(int64_t n);
+void scan_exclusive_u32(const uint32_t *in, uint32_t *out, int64_t n, const uint32_t *n_dev, void *tmp,
+                        size_t tmp_bytes, cudaStream_t s);
+void scan_exclusive_u64(const uint64_t *in, uint64_t *out, int64_t n, const uint32_t *n_dev, void *tmp,
+                        size_t tmp_bytes, cudaStream_t s);
+size_t radix_tmp_bytes(int64_t n);
+// sorts keys[0..n) on bits [0, bits); n is read from n_dev when given (bounded by n_max)
+void radix_sort_u64(uint64_t *keys, uint64_t *alt, int64_t n_max, const unsigned long long *n_dev, int bits,
+                    void *tmp, size_t tmp_bytes, cudaStream_t s, uint64_t **result);
+
+// k_encode.cu
+void dict_build(const DevCol &c, int prefix, uint64_t *table, uint64_t cap, uint32_t *codes, cudaStream_t s);
+void dict_probe(const DevCol &probe, int prefix, const DevCol &owner, int owner_prefix, const uint64_t *table,
+                uint64_t cap, uint32_t *codes, cudaStream_t s);
+void code_feature(const uint32_t *codes, int64_t n, uint32_t *rec, int W, int feat, cudaStream_t s);
+void ed_features(const DevCol &c, uint32_t *rec, int W, int feat, cudaStream_t s);
+void abs_feature(const DevCol &c, uint32_t *rec, int W, int feat, cudaStream_t s);
+size_t jac_scratch_bytes(int64_t n);
+// grams: capacity >= the column's byte count; too_long: device flag set for strings of > 8192 grams
+void jac_features_impl(const DevCol &c, int q, uint32_t *rec, int W, int feat, uint32_t *grams, void *scratch,
+                       unsigned int *too_long, int n_sm, cudaStream_t s);
+
+// k_block.cu
+void group_build(const uint32_t *rec, int W, int64_t n, const int32_t *eq_words, int n_keys, uint64_t *table,
+                 uint64_t cap, uint32_t *slot, cudaStream_t s);
+void group_probe(const uint32_t *rec_probe, int64_t n, const uint32_t *rec_owner, int W, const int32_t *eq_words,
+                 int n_keys, const uint64_t *table, uint64_t cap, uint32_t *slot, cudaStream_t s);
+void count_slots(const uint32_t *slot, int64_t n, uint32_t *count, cudaStream_t s);
+void scatter_slots(const uint32_t *slot, int64_t n, const uint32_t *start, uint32_t *cursor, uint32_t *members,
+                   cudaStream_t s);
+void emit_blocks(const uint32_t *count_r, const uint32_t *start_r, const uint32_t *count_s, const uint32_t *start_s,
+                 uint64_t cap, uint32_t md, int self_join, uint32_t member_base_r, uint32_t member_base_s, int tile,
+                 BlockDesc *blocks, uint64_t *tiles, uint32_t *n_blocks, uint32_t block_cap, unsigned int *overflow,
+                 cudaStream_t s);
+void clamp_blocks(uint32_t *n_blocks, uint32_t block_cap, cudaStream_t s);
+
+// k_eval.cu
+size_t eval_smem_bytes(int W, int n_eq, int use_lut, int tile);
+int eval_blocks_per_sm(int tile, int logging, size_t smem);
+cudaError_t launch_eval(const EvalParams &p, int grid, size_t smem, int logging, cudaStream_t s);
+void pack_pairs(const uint64_t *keys, int64_t n, int key_bits_s, hb_pair *out, cudaStream_t s);
+
+// k_stats.cu
+struct SampleSpec {
+    int32_t kind;
+    int32_t type;
+    const uint8_t *bytes;
+    const uint32_t *off;
+    const void *vals;
+    const uint8_t *valid;
+    int32_t prefix;
+    int32_t q;
+    float delta;
+    int32_t pad;
+};
+void lsh_hist(const SampleSpec *specs_dev, int n_preds, int64_t n_rows, int n_samples, int k_buckets,
+              uint32_t *hist, uint32_t *present, uint32_t *lens, uint32_t *grams, int n_keep, cudaStream_t s);
+
+// planner.cpp
+struct PlanResult {
+    std::vector<int> pred_order;
+    std::vector<int> md_order;
+    std::vector<int> program;
+    std::vector<int> cp;
+    std::vector<double> wp;
+};
+PlanResult make_plan(int n_preds, const double *sp, const double *cost, const std::vector<std::vector<int>> &mds,
+                     const std::vector<uint8_t> &skip);
+
+// k_mlp.cu
+cudaError_t mlp_forward(const float *X, int n, const float *params, float *y, int bf16, cudaStream_t s);
+cudaError_t mlp_backward(const float *X, const float *t, int n, const float *params, float *grad, float *work,
+                         cudaStream_t s);
+size_t mlp_work_floats(int n);
+cudaError_t adam_step(float *params, const float *grad, float *m, float *v, int n, int step, float lr, float b1,
+                      float b2, float eps, cudaStream_t s);
+
+}  // namespace hb

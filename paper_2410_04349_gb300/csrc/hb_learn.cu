@@ -1,0 +1,105 @@
+// Learned cost model entry points: the MLP kernels behind the C-ABI, training
+// on logged predicate evaluations, and the learned plan statistics.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <cmath>
+#include <random>
+#include <vector>
+
+#include "hb_ctx.h"
+
+using namespace hb;
+
+extern "C" hb_status hb_mlp_forward(const float *X, int32_t n, const float *params, float *y, void *stream) {
+    if (n < 0 || (n > 0 && (!X || !params || !y))) return fail(HB_ERR_ARG, "hb_mlp_forward: bad arguments");
+    HB_CUDA(mlp_forward(X, n, params, y, 0, static_cast<cudaStream_t>(stream)));
+    return HB_OK;
+}
+
+extern "C" hb_status hb_mlp_forward_bf16(const float *X, int32_t n, const float *params, float *y, void *stream) {
+    if (n < 0 || (n > 0 && (!X || !params || !y))) return fail(HB_ERR_ARG, "hb_mlp_forward_bf16: bad arguments");
+    HB_CUDA(mlp_forward(X, n, params, y, 1, static_cast<cudaStream_t>(stream)));
+    return HB_OK;
+}
+
+extern "C" hb_status hb_mlp_backward(const float *X, const float *t, int32_t n, const float *params, float *grad,
+                                     void *stream) {
+    if (n < 0 || !params || !grad || (n > 0 && (!X || !t))) return fail(HB_ERR_ARG, "hb_mlp_backward: bad arguments");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    float *work = nullptr;
+    HB_CUDA(cudaMallocAsync(reinterpret_cast<void **>(&work), sizeof(float) * mlp_work_floats(n), s));
+    cudaError_t e = mlp_backward(X, t, n, params, grad, work, s);
+    cudaFreeAsync(work, s);
+    HB_CUDA(e);
+    return HB_OK;
+}
+
+extern "C" hb_status hb_adam_step(float *params, const float *grad, float *m, float *v, int32_t n_params, int32_t step,
+                                  float lr, float beta1, float beta2, float eps, void *stream) {
+    if (n_params < 0 || step < 1 || (n_params > 0 && (!params || !grad || !m || !v)))
+        return fail(HB_ERR_ARG, "hb_adam_step: bad arguments");
+    HB_CUDA(adam_step(params, grad, m, v, n_params, step, lr, beta1, beta2, eps, static_cast<cudaStream_t>(stream)));
+    return HB_OK;
+}
+
+namespace hb {
+
+hb_status learned_stats(hb_ctx *c, std::vector<double> &sp, std::vector<double> &cost, bool &ok) {
+    (void)sp;
+    (void)cost;
+    ok = false;
+    if (!c->model_ok) return HB_OK;
+    return HB_OK;
+}
+
+}  // namespace hb
+
+extern "C" hb_status hb_get_cost_model(hb_ctx *c, float *params_out) {
+    if (!c || !params_out) return fail(HB_ERR_ARG, "hb_get_cost_model: NULL argument");
+    if (!c->model_ok) return fail(HB_ERR_STATE, "hb_get_cost_model: no model trained or set");
+    memcpy(params_out, c->model.data(), sizeof(float) * 2 * HB_MLP_PARAMS);
+    return HB_OK;
+}
+
+extern "C" hb_status hb_set_cost_model(hb_ctx *c, const float *params) {
+    if (!c || !params) return fail(HB_ERR_ARG, "hb_set_cost_model: NULL argument");
+    c->model.assign(params, params + 2 * HB_MLP_PARAMS);
+    for (float x : c->model)
+        if (!std::isfinite(x)) {
+            c->model_ok = false;
+            return fail(HB_ERR_ARG, "hb_set_cost_model: non-finite weight");
+        }
+    c->model_ok = true;
+    return HB_OK;
+}
+
+extern "C" hb_status hb_log_predicates(hb_ctx *c, hb_pred_log *out, int32_t cap, int32_t *n_out) {
+    (void)c; (void)out; (void)cap; (void)n_out;
+    return fail(HB_ERR_STATE, "hb_log_predicates: not available yet");
+}
+
+extern "C" hb_status hb_predicate_features(hb_ctx *c, float *features_out, int32_t cap_preds, int32_t *n_out) {
+    (void)c; (void)features_out; (void)cap_preds; (void)n_out;
+    return fail(HB_ERR_STATE, "hb_predicate_features: not available yet");
+}
+
+extern "C" hb_status hb_train_cost_model(hb_ctx *c, int32_t n, const float *X, const float *y_cost,
+                                         const float *y_sel, int32_t epochs, float lr, uint64_t seed,
+                                         float *loss_out) {
+    (void)c; (void)n; (void)X; (void)y_cost; (void)y_sel; (void)epochs; (void)lr; (void)seed; (void)loss_out;
+    return fail(HB_ERR_STATE, "hb_train_cost_model: not available yet");
+}
+
+extern "C" hb_status hb_block_stream(hb_ctx *c, int64_t n_rows_s, int32_t n_cols, const hb_column *cols_s,
+                                     hb_pair **pairs_out, int64_t *n_out) {
+    (void)c; (void)n_rows_s; (void)n_cols; (void)cols_s; (void)pairs_out; (void)n_out;
+    return fail(HB_ERR_STATE, "hb_block_stream: not available yet");
+}
+
+extern "C" hb_status hb_block_batch(hb_ctx *c, int32_t n_jobs, const int64_t *job_rows, hb_pair **pairs_out,
+                                    int64_t *job_pairs_out) {
+    (void)c; (void)n_jobs; (void)job_rows; (void)pairs_out; (void)job_pairs_out;
+    return fail(HB_ERR_STATE, "hb_block_batch: not available yet");
+}

@@ -1,0 +1,230 @@
+// Block builder.  For every MD, tuples that agree on all of its equality keys
+// form one block (a pair can satisfy the MD's precondition only inside one).
+// Groups are found with an exact open-addressing table over the tuples'
+// equality codes; members are laid out per group by a counting sort; every
+// group with a pair to compare becomes a block with its tile count.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "hb_internal.h"
+
+namespace hb {
+namespace {
+
+constexpr int BT = 256;
+constexpr uint32_t NO_SLOT = 0xFFFFFFFFu;
+
+struct KeyWords {
+    int32_t w[MAX_EQ];
+    int32_t n;
+};
+
+__device__ __forceinline__ uint64_t mixk(uint64_t h, uint32_t v) {
+    h ^= (uint64_t)v + 0x9E3779B97F4A7C15ull + (h << 6) + (h >> 2);
+    h *= 0xff51afd7ed558ccdull;
+    return h ^ (h >> 32);
+}
+
+__device__ __forceinline__ bool key_of(const uint32_t *rec, int W, int64_t i, const KeyWords &kw, uint64_t &h) {
+    h = 0x243F6A8885A308D3ull;
+    for (int e = 0; e < kw.n; e++) {
+        uint32_t c = rec[i * W + kw.w[e]];
+        if (c >= NOMATCH_CODE) return false;
+        h = mixk(h, c);
+    }
+    return true;
+}
+
+__device__ __forceinline__ bool keys_equal(const uint32_t *ra, int64_t i, const uint32_t *rb, int64_t j, int W,
+                                           const KeyWords &kw) {
+    for (int e = 0; e < kw.n; e++)
+        if (ra[i * W + kw.w[e]] != rb[j * W + kw.w[e]]) return false;
+    return true;
+}
+
+__global__ void k_group_insert(const uint32_t *rec, int W, int64_t n, KeyWords kw, uint64_t *table, uint64_t mask,
+                               uint32_t *slot_out) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if (kw.n == 0) {   // an MD without equality predicates: one group holding every tuple
+        slot_out[i] = 0;
+        return;
+    }
+    uint64_t h;
+    if (!key_of(rec, W, i, kw, h)) {
+        slot_out[i] = NO_SLOT;
+        return;
+    }
+    uint32_t h32 = (uint32_t)(h >> 32);
+    uint64_t mine = ((uint64_t)h32 << 32) | (uint64_t)(uint32_t)i;
+    uint64_t slot = h & mask;
+    for (uint64_t probe = 0; probe <= mask; probe++) {
+        uint64_t cur = table[slot];
+        if (cur == EMPTY_SLOT) {
+            uint64_t prev = atomicCAS(reinterpret_cast<unsigned long long *>(table + slot),
+                                      (unsigned long long)EMPTY_SLOT, (unsigned long long)mine);
+            if (prev == EMPTY_SLOT) {
+                slot_out[i] = (uint32_t)slot;
+                return;
+            }
+            cur = prev;
+        }
+        if ((uint32_t)(cur >> 32) == h32 && keys_equal(rec, i, rec, (int64_t)(uint32_t)cur, W, kw)) {
+            slot_out[i] = (uint32_t)slot;
+            return;
+        }
+        slot = (slot + 1) & mask;
+    }
+    slot_out[i] = NO_SLOT;
+}
+
+__global__ void k_group_probe(const uint32_t *rec, int64_t n, const uint32_t *rec_owner, int W, KeyWords kw,
+                              const uint64_t *table, uint64_t mask, uint32_t *slot_out) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if (kw.n == 0) {
+        slot_out[i] = 0;
+        return;
+    }
+    uint64_t h;
+    if (!key_of(rec, W, i, kw, h)) {
+        slot_out[i] = NO_SLOT;
+        return;
+    }
+    uint32_t h32 = (uint32_t)(h >> 32);
+    uint64_t slot = h & mask;
+    for (uint64_t probe = 0; probe <= mask; probe++) {
+        uint64_t cur = table[slot];
+        if (cur == EMPTY_SLOT) break;
+        if ((uint32_t)(cur >> 32) == h32 && keys_equal(rec, i, rec_owner, (int64_t)(uint32_t)cur, W, kw)) {
+            slot_out[i] = (uint32_t)slot;
+            return;
+        }
+        slot = (slot + 1) & mask;
+    }
+    slot_out[i] = NO_SLOT;
+}
+
+// warp-aggregated increment: lanes with the same slot add once
+__global__ void k_count_slots(const uint32_t *slot, int64_t n, uint32_t *count) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    uint32_t s = i < n ? slot[i] : NO_SLOT;
+    unsigned peers = __match_any_sync(0xffffffffu, s);
+    int lane = threadIdx.x & 31;
+    if (s != NO_SLOT && (__ffs(peers) - 1) == lane) atomicAdd(&count[s], (uint32_t)__popc(peers));
+}
+
+__global__ void k_scatter_slots(const uint32_t *slot, int64_t n, const uint32_t *start, uint32_t *cursor,
+                                uint32_t *members) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    uint32_t s = i < n ? slot[i] : NO_SLOT;
+    unsigned peers = __match_any_sync(0xffffffffu, s);
+    int lane = threadIdx.x & 31;
+    int leader = __ffs(peers) - 1;
+    uint32_t base = 0;
+    if (s != NO_SLOT && leader == lane) base = atomicAdd(&cursor[s], (uint32_t)__popc(peers));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (s != NO_SLOT) members[start[s] + base + __popc(peers & ((1u << lane) - 1u))] = (uint32_t)i;
+}
+
+__device__ __forceinline__ uint64_t tiles_of(uint32_t nr, uint32_t ns, int self_join, int tile) {
+    uint64_t a = (nr + tile - 1) / tile;
+    if (self_join) return a * (a + 1) / 2;
+    uint64_t b = (ns + tile - 1) / tile;
+    return a * b;
+}
+
+__global__ void k_emit_blocks(const uint32_t *count_r, const uint32_t *start_r, const uint32_t *count_s,
+                              const uint32_t *start_s, uint64_t cap, uint32_t md, int self_join,
+                              uint32_t member_base_r, uint32_t member_base_s, int tile, BlockDesc *blocks,
+                              uint64_t *tiles, uint32_t *n_blocks, uint32_t block_cap, unsigned int *overflow) {
+    int64_t sl = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    bool keep = false;
+    uint32_t nr = 0, ns = 0;
+    if (sl < (int64_t)cap) {
+        nr = count_r[sl];
+        if (self_join) {
+            ns = nr;
+            keep = nr >= 2;
+        } else {
+            ns = count_s[sl];
+            keep = nr >= 1 && ns >= 1;
+        }
+    }
+    unsigned bal = __ballot_sync(0xffffffffu, keep);
+    int lane = threadIdx.x & 31;
+    uint32_t base = 0;
+    if (lane == 0 && bal) base = atomicAdd(n_blocks, (uint32_t)__popc(bal));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (keep) {
+        uint32_t b = base + __popc(bal & ((1u << lane) - 1u));
+        if (b >= block_cap) {
+            atomicExch(overflow, 1u);
+            return;
+        }
+        BlockDesc d;
+        d.md = md;
+        d.n_r = nr;
+        d.start_r = member_base_r + start_r[sl];
+        d.n_s = ns;
+        d.start_s = self_join ? d.start_r : member_base_s + start_s[sl];
+        d.pad = 0;
+        blocks[b] = d;
+        tiles[b] = tiles_of(nr, ns, self_join, tile);
+    }
+}
+
+__global__ void k_clamp_blocks(uint32_t *n_blocks, uint32_t block_cap) {
+    if (*n_blocks > block_cap) *n_blocks = block_cap;
+}
+
+inline unsigned nblk(int64_t n) { return (unsigned)(n > 0 ? (n + BT - 1) / BT : 1); }
+
+}  // namespace
+
+KeyWords make_keywords(const int32_t *eq_words, int n_keys) {
+    KeyWords k;
+    k.n = n_keys;
+    for (int e = 0; e < MAX_EQ; e++) k.w[e] = e < n_keys ? eq_words[e] : 0;
+    return k;
+}
+
+void group_build(const uint32_t *rec, int W, int64_t n, const int32_t *eq_words, int n_keys, uint64_t *table,
+                 uint64_t cap, uint32_t *slot, cudaStream_t s) {
+    if (n_keys > 0) cudaMemsetAsync(table, 0xFF, cap * sizeof(uint64_t), s);
+    if (n == 0) return;
+    k_group_insert<<<nblk(n), BT, 0, s>>>(rec, W, n, make_keywords(eq_words, n_keys), table, cap - 1, slot);
+}
+
+void group_probe(const uint32_t *rec_probe, int64_t n, const uint32_t *rec_owner, int W, const int32_t *eq_words,
+                 int n_keys, const uint64_t *table, uint64_t cap, uint32_t *slot, cudaStream_t s) {
+    if (n == 0) return;
+    k_group_probe<<<nblk(n), BT, 0, s>>>(rec_probe, n, rec_owner, W, make_keywords(eq_words, n_keys), table,
+                                         cap - 1, slot);
+}
+
+void count_slots(const uint32_t *slot, int64_t n, uint32_t *count, cudaStream_t s) {
+    if (n == 0) return;
+    k_count_slots<<<nblk(n), BT, 0, s>>>(slot, n, count);
+}
+
+void scatter_slots(const uint32_t *slot, int64_t n, const uint32_t *start, uint32_t *cursor, uint32_t *members,
+                   cudaStream_t s) {
+    if (n == 0) return;
+    k_scatter_slots<<<nblk(n), BT, 0, s>>>(slot, n, start, cursor, members);
+}
+
+void emit_blocks(const uint32_t *count_r, const uint32_t *start_r, const uint32_t *count_s, const uint32_t *start_s,
+                 uint64_t cap, uint32_t md, int self_join, uint32_t member_base_r, uint32_t member_base_s, int tile,
+                 BlockDesc *blocks, uint64_t *tiles, uint32_t *n_blocks, uint32_t block_cap, unsigned int *overflow,
+                 cudaStream_t s) {
+    k_emit_blocks<<<nblk((int64_t)cap), BT, 0, s>>>(count_r, start_r, count_s, start_s, cap, md, self_join,
+                                                    member_base_r, member_base_s, tile, blocks, tiles, n_blocks,
+                                                    block_cap, overflow);
+}
+
+void clamp_blocks(uint32_t *n_blocks, uint32_t block_cap, cudaStream_t s) {
+    k_clamp_blocks<<<1, 1, 0, s>>>(n_blocks, block_cap);
+}
+
+}  // namespace hb

@@ -1,0 +1,393 @@
+// Columnar encoder: exact dictionary codes for equality keys, per-string
+// features for edit distance and q-gram Jaccard, and the packed per-tuple
+// record (array of structs, W 32-bit words) that the evaluation kernel stages.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "hb_internal.h"
+
+namespace hb {
+namespace {
+
+constexpr int ENC_THREADS = 256;
+
+__device__ __forceinline__ uint64_t mix64(uint64_t x) {
+    x ^= x >> 33;
+    x *= 0xff51afd7ed558ccdull;
+    x ^= x >> 33;
+    x *= 0xc4ceb9fe1a85ec53ull;
+    x ^= x >> 33;
+    return x;
+}
+
+__device__ __forceinline__ uint64_t hash_bytes(const uint8_t *p, uint32_t len) {
+    uint64_t h = 0x9E3779B97F4A7C15ull ^ (uint64_t)len;
+    uint32_t i = 0;
+    for (; i + 4 <= len; i += 4) {
+        uint32_t w = (uint32_t)p[i] | ((uint32_t)p[i + 1] << 8) | ((uint32_t)p[i + 2] << 16) |
+                     ((uint32_t)p[i + 3] << 24);
+        h = (h ^ w) * 0x100000001B3ull;
+        h ^= h >> 29;
+    }
+    for (; i < len; i++) h = (h ^ p[i]) * 0x100000001B3ull;
+    return mix64(h);
+}
+
+struct View {
+    const uint8_t *bytes;
+    const uint32_t *off;
+    const int32_t *i32;
+    const uint8_t *valid;
+    int32_t type;
+    int32_t prefix;
+};
+
+__host__ __device__ inline View make_view(const DevCol &c, int prefix) {
+    View v;
+    v.bytes = c.bytes;
+    v.off = c.off;
+    v.i32 = static_cast<const int32_t *>(c.vals);
+    v.valid = c.valid;
+    v.type = c.type;
+    v.prefix = prefix;
+    return v;
+}
+
+__device__ __forceinline__ void view_str(const View &v, int64_t i, const uint8_t *&p, uint32_t &len) {
+    uint32_t a = v.off[i], b = v.off[i + 1];
+    p = v.bytes + a;
+    len = b - a;
+    if (v.prefix >= 0 && len > (uint32_t)v.prefix) len = (uint32_t)v.prefix;
+}
+
+__device__ __forceinline__ uint64_t view_hash(const View &v, int64_t i) {
+    if (v.type == HB_COL_STRING) {
+        const uint8_t *p;
+        uint32_t len;
+        view_str(v, i, p, len);
+        return hash_bytes(p, len);
+    }
+    return mix64((uint64_t)(uint32_t)v.i32[i] * 0x9E3779B97F4A7C15ull + 1);
+}
+
+__device__ __forceinline__ bool view_equal(const View &a, int64_t i, const View &b, int64_t j) {
+    if (a.type == HB_COL_STRING) {
+        const uint8_t *p, *q;
+        uint32_t lp, lq;
+        view_str(a, i, p, lp);
+        view_str(b, j, q, lq);
+        if (lp != lq) return false;
+        for (uint32_t k = 0; k < lp; k++)
+            if (p[k] != q[k]) return false;
+        return true;
+    }
+    return a.i32[i] == b.i32[j];
+}
+
+// Insert every present value into an open-addressing table whose slots hold
+// (32-bit hash << 32 | representative row); the code of a value is its slot.
+// Two values share a slot only after a byte-exact comparison.
+__global__ void k_dict_insert(View v, int64_t n, uint64_t *table, uint64_t mask, uint32_t *codes) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if (v.valid && !v.valid[i]) {
+        codes[i] = NULL_CODE;
+        return;
+    }
+    uint64_t h = view_hash(v, i);
+    uint32_t h32 = (uint32_t)(h >> 32);
+    uint64_t mine = ((uint64_t)h32 << 32) | (uint64_t)(uint32_t)i;
+    uint64_t slot = h & mask;
+    for (uint64_t probe = 0; probe <= mask; probe++) {
+        uint64_t cur = table[slot];
+        if (cur == EMPTY_SLOT) {
+            uint64_t prev = atomicCAS(reinterpret_cast<unsigned long long *>(table + slot),
+                                      (unsigned long long)EMPTY_SLOT, (unsigned long long)mine);
+            if (prev == EMPTY_SLOT) {
+                codes[i] = (uint32_t)slot;
+                return;
+            }
+            cur = prev;
+        }
+        if ((uint32_t)(cur >> 32) == h32 && view_equal(v, i, v, (int64_t)(uint32_t)cur)) {
+            codes[i] = (uint32_t)slot;
+            return;
+        }
+        slot = (slot + 1) & mask;
+    }
+    codes[i] = NULL_CODE;   // unreachable: the table has at least twice as many slots as rows
+}
+
+// Codes for the other relation: the slot of an equal value of the owner, or NOMATCH.
+__global__ void k_dict_probe(View v, int64_t n, View owner, const uint64_t *table, uint64_t mask, uint32_t *codes) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if (v.valid && !v.valid[i]) {
+        codes[i] = NULL_CODE;
+        return;
+    }
+    uint64_t h = view_hash(v, i);
+    uint32_t h32 = (uint32_t)(h >> 32);
+    uint64_t slot = h & mask;
+    for (uint64_t probe = 0; probe <= mask; probe++) {
+        uint64_t cur = table[slot];
+        if (cur == EMPTY_SLOT) break;
+        if ((uint32_t)(cur >> 32) == h32 && view_equal(v, i, owner, (int64_t)(uint32_t)cur)) {
+            codes[i] = (uint32_t)slot;
+            return;
+        }
+        slot = (slot + 1) & mask;
+    }
+    codes[i] = NOMATCH_CODE;
+}
+
+__global__ void k_code_feature(const uint32_t *codes, int64_t n, uint32_t *rec, int W, int feat) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) rec[i * W + feat] = codes[i];
+}
+
+// length, byte offset and 16 saturating 8-bit counts of (byte & 15)
+__global__ void k_ed_features(const uint8_t *bytes, const uint32_t *off, const uint8_t *valid, int64_t n,
+                              uint32_t *rec, int W, int feat) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint32_t *r = rec + i * W + feat;
+    if (valid && !valid[i]) {
+        r[0] = NULL_LEN;
+        r[1] = 0;
+        r[2] = r[3] = r[4] = r[5] = 0;
+        return;
+    }
+    uint32_t a = off[i], b = off[i + 1];
+    uint32_t cnt[4] = {0, 0, 0, 0};
+    for (uint32_t k = a; k < b; k++) {
+        uint32_t bin = bytes[k] & 15u;
+        uint32_t word = bin >> 2, sh = (bin & 3u) * 8u;
+        uint32_t cur = (cnt[word] >> sh) & 255u;
+        if (cur < 255u) cnt[word] += 1u << sh;
+    }
+    r[0] = b - a;
+    r[1] = a;
+    r[2] = cnt[0];
+    r[3] = cnt[1];
+    r[4] = cnt[2];
+    r[5] = cnt[3];
+}
+
+__global__ void k_abs_feature(const float *vals, const uint8_t *valid, int64_t n, uint32_t *rec, int W, int feat) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    rec[i * W + feat] = (valid && !valid[i]) ? 0x7FC00000u : __float_as_uint(vals[i]);
+}
+
+__device__ __forceinline__ uint32_t gram_at(const uint8_t *p, uint32_t k, int q) {
+    uint32_t g = 0;
+    for (int t = 0; t < q; t++) g = (g << 8) | p[k + t];
+    return g;
+}
+
+__device__ __forceinline__ uint32_t gram_bin(uint32_t g) { return (g * 0x9E3779B1u) >> 27; }
+
+constexpr int QG_SHORT = 64;       // grams per string handled by one thread
+constexpr int QG_THREADS = 128;
+constexpr int QG_LONG_MAX = 8192;  // grams per string handled by one block
+
+__global__ void k_gram_counts(const uint32_t *off, const uint8_t *valid, int64_t n, int q, uint32_t *cnt) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint32_t len = off[i + 1] - off[i];
+    cnt[i] = (valid && !valid[i]) ? 0u : (len >= (uint32_t)q ? len - (uint32_t)q + 1u : 0u);
+}
+
+__device__ void write_gram_feature(uint32_t *r, uint32_t ucount, uint32_t start, const uint32_t *g) {
+    uint32_t sig[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (uint32_t k = 0; k < ucount; k++) {
+        uint32_t bin = gram_bin(g[k]);
+        uint32_t word = bin >> 2, sh = (bin & 3u) * 8u;
+        uint32_t cur = (sig[word] >> sh) & 255u;
+        if (cur < 255u) sig[word] += 1u << sh;
+    }
+    r[0] = ucount;
+    r[1] = start;
+#pragma unroll
+    for (int k = 0; k < 8; k++) r[2 + k] = sig[k];
+}
+
+// Strings with up to 64 grams: one thread sorts its grams in shared memory
+// (insertion sort), removes duplicates and writes them at the string's slot.
+__global__ void __launch_bounds__(QG_THREADS) k_grams_short(const uint8_t *bytes, const uint32_t *off,
+                                                           const uint8_t *valid, int64_t n, int q,
+                                                           const uint32_t *gstart, uint32_t *grams, uint32_t *rec,
+                                                           int W, int feat, uint32_t *long_list,
+                                                           unsigned int *n_long) {
+    __shared__ uint32_t buf[QG_SHORT][QG_THREADS];
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint32_t *r = rec + i * W + feat;
+    if (valid && !valid[i]) {
+        r[0] = NULL_LEN;
+        r[1] = 0;
+        for (int k = 0; k < 8; k++) r[2 + k] = 0;
+        return;
+    }
+    uint32_t a = off[i], len = off[i + 1] - a;
+    uint32_t g = len >= (uint32_t)q ? len - (uint32_t)q + 1u : 0u;
+    if (g > (uint32_t)QG_SHORT) {
+        unsigned int slot = atomicAdd(n_long, 1u);
+        long_list[slot] = (uint32_t)i;
+        return;
+    }
+    const uint8_t *p = bytes + a;
+    uint32_t *s = &buf[0][threadIdx.x];
+    for (uint32_t k = 0; k < g; k++) {
+        uint32_t x = gram_at(p, k, q);
+        uint32_t j = k;
+        while (j > 0 && s[(j - 1) * QG_THREADS] > x) {
+            s[j * QG_THREADS] = s[(j - 1) * QG_THREADS];
+            j--;
+        }
+        s[j * QG_THREADS] = x;
+    }
+    uint32_t u = 0;
+    uint32_t *dst = grams + gstart[i];
+    uint32_t sig[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (uint32_t k = 0; k < g; k++) {
+        uint32_t x = s[k * QG_THREADS];
+        if (k == 0 || x != s[(k - 1) * QG_THREADS]) {
+            dst[u++] = x;
+            uint32_t bin = gram_bin(x);
+            uint32_t word = bin >> 2, sh = (bin & 3u) * 8u;
+            uint32_t cur = (sig[word] >> sh) & 255u;
+            if (cur < 255u) sig[word] += 1u << sh;
+        }
+    }
+    r[0] = u;
+    r[1] = gstart[i];
+#pragma unroll
+    for (int k = 0; k < 8; k++) r[2 + k] = sig[k];
+}
+
+// Strings with more grams: one block per string, bitonic sort in shared memory.
+__global__ void __launch_bounds__(256) k_grams_long(const uint8_t *bytes, const uint32_t *off, int q,
+                                                   const uint32_t *gstart, uint32_t *grams, uint32_t *rec, int W,
+                                                   int feat, const uint32_t *long_list, const unsigned int *n_long,
+                                                   unsigned int *too_long) {
+    __shared__ uint32_t s[QG_LONG_MAX];
+    __shared__ uint32_t wcount[8];
+    const unsigned int nl = *n_long;
+    for (unsigned int li = blockIdx.x; li < nl; li += gridDim.x) {
+        const int64_t i = long_list[li];
+        const uint32_t a = off[i], len = off[i + 1] - a;
+        const uint32_t g = len - (uint32_t)q + 1u;
+        uint32_t *r = rec + i * W + feat;
+        if (g > (uint32_t)QG_LONG_MAX) {
+            if (threadIdx.x == 0) {
+                atomicExch(too_long, 1u);
+                r[0] = NULL_LEN;
+                r[1] = 0;
+            }
+            continue;
+        }
+        uint32_t P2 = 1;
+        while (P2 < g) P2 <<= 1;
+        const uint8_t *p = bytes + a;
+        for (uint32_t k = threadIdx.x; k < P2; k += blockDim.x) s[k] = k < g ? gram_at(p, k, q) : 0xFFFFFFFFu;
+        __syncthreads();
+        for (uint32_t size = 2; size <= P2; size <<= 1) {
+            for (uint32_t stride = size >> 1; stride > 0; stride >>= 1) {
+                for (uint32_t k = threadIdx.x; k < P2; k += blockDim.x) {
+                    uint32_t partner = k ^ stride;
+                    if (partner > k) {
+                        bool up = (k & size) == 0;
+                        uint32_t x = s[k], y = s[partner];
+                        if ((x > y) == up) {
+                            s[k] = y;
+                            s[partner] = x;
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        // unique: a block-wide compaction in index order
+        uint32_t *dst = grams + gstart[i];
+        uint32_t base = 0;
+        for (uint32_t c0 = 0; c0 < g; c0 += blockDim.x) {
+            uint32_t k = c0 + threadIdx.x;
+            bool keep = k < g && (k == 0 || s[k] != s[k - 1]);
+            unsigned bal = __ballot_sync(0xffffffffu, keep);
+            int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+            if (lane == 0) wcount[w] = __popc(bal);
+            __syncthreads();
+            uint32_t before = 0, total = 0;
+            for (int t = 0; t < (int)(blockDim.x >> 5); t++) {
+                if (t < w) before += wcount[t];
+                total += wcount[t];
+            }
+            if (keep) dst[base + before + __popc(bal & ((1u << lane) - 1u))] = s[k];
+            base += total;
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) write_gram_feature(r, base, gstart[i], dst);
+        __syncthreads();
+    }
+}
+
+inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t > 0 ? (n + t - 1) / t : 1); }
+
+}  // namespace
+
+void dict_build(const DevCol &c, int prefix, uint64_t *table, uint64_t cap, uint32_t *codes, cudaStream_t s) {
+    cudaMemsetAsync(table, 0xFF, cap * sizeof(uint64_t), s);
+    if (c.n == 0) return;
+    k_dict_insert<<<blocks_for(c.n, ENC_THREADS), ENC_THREADS, 0, s>>>(make_view(c, prefix), c.n, table, cap - 1,
+                                                                      codes);
+}
+
+void dict_probe(const DevCol &probe, int prefix, const DevCol &owner, int owner_prefix, const uint64_t *table,
+                uint64_t cap, uint32_t *codes, cudaStream_t s) {
+    if (probe.n == 0) return;
+    k_dict_probe<<<blocks_for(probe.n, ENC_THREADS), ENC_THREADS, 0, s>>>(
+        make_view(probe, prefix), probe.n, make_view(owner, owner_prefix), table, cap - 1, codes);
+}
+
+void code_feature(const uint32_t *codes, int64_t n, uint32_t *rec, int W, int feat, cudaStream_t s) {
+    if (n == 0) return;
+    k_code_feature<<<blocks_for(n, ENC_THREADS), ENC_THREADS, 0, s>>>(codes, n, rec, W, feat);
+}
+
+void ed_features(const DevCol &c, uint32_t *rec, int W, int feat, cudaStream_t s) {
+    if (c.n == 0) return;
+    k_ed_features<<<blocks_for(c.n, ENC_THREADS), ENC_THREADS, 0, s>>>(c.bytes, c.off, c.valid, c.n, rec, W, feat);
+}
+
+void abs_feature(const DevCol &c, uint32_t *rec, int W, int feat, cudaStream_t s) {
+    if (c.n == 0) return;
+    k_abs_feature<<<blocks_for(c.n, ENC_THREADS), ENC_THREADS, 0, s>>>(static_cast<const float *>(c.vals), c.valid,
+                                                                      c.n, rec, W, feat);
+}
+
+size_t jac_scratch_bytes(int64_t n) {
+    return (size_t)(n + 1) * 4 * 3 + scan_tmp_bytes(n) + 4096;
+}
+
+// scratch: jac_scratch_bytes(n); grams: capacity >= nbytes of the column (one gram per byte at most)
+void jac_features_impl(const DevCol &c, int q, uint32_t *rec, int W, int feat, uint32_t *grams, void *scratch,
+                       unsigned int *too_long, int n_sm, cudaStream_t s) {
+    const int64_t n = c.n;
+    if (n == 0) return;
+    uint32_t *cnt = static_cast<uint32_t *>(scratch);
+    uint32_t *gstart = cnt + (n + 1);
+    uint32_t *long_list = gstart + (n + 1);
+    unsigned int *n_long = reinterpret_cast<unsigned int *>(long_list + (n + 1));
+    void *stmp = reinterpret_cast<void *>((reinterpret_cast<uintptr_t>(n_long + 4) + 255) & ~uintptr_t(255));
+    cudaMemsetAsync(n_long, 0, sizeof(unsigned int), s);
+    k_gram_counts<<<blocks_for(n, ENC_THREADS), ENC_THREADS, 0, s>>>(c.off, c.valid, n, q, cnt);
+    scan_exclusive_u32(cnt, gstart, n, nullptr, stmp, 0, s);
+    k_grams_short<<<blocks_for(n, QG_THREADS), QG_THREADS, 0, s>>>(c.bytes, c.off, c.valid, n, q, gstart, grams, rec,
+                                                                  W, feat, long_list, n_long);
+    k_grams_long<<<(unsigned)(n_sm * 4), 256, 0, s>>>(c.bytes, c.off, q, gstart, grams, rec, W, feat, long_list,
+                                                      n_long, too_long);
+}
+
+}  // namespace hb

@@ -1,0 +1,188 @@
+// Cost-model MLP kernels (Section 4.2, "Shallow NNs"): 32 -> 64 -> 64 -> 1
+// with ReLU, trained with mean squared error and Adam (Kingma & Ba).
+// Parameters are one fp32 vector: W1[32][64], b1[64], W2[64][64], b2[64],
+// W3[64], b3 (row-major, input index first).
+//
+// The network is tiny (6.3K weights, a few thousand rows), far below the
+// size at which tensor cores pay off, so these are plain FMA kernels; the
+// bf16 inference path rounds inputs, weights and hidden activations to
+// bfloat16 and accumulates in fp32 (a bf16 x bf16 product is exact in fp32).
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "hb_internal.h"
+
+namespace hb {
+namespace {
+
+constexpr int D0 = 32, D1 = 64, D2 = 64;
+constexpr int OFF_W1 = 0, OFF_B1 = OFF_W1 + D0 * D1, OFF_W2 = OFF_B1 + D1, OFF_B2 = OFF_W2 + D1 * D2,
+              OFF_W3 = OFF_B2 + D2, OFF_B3 = OFF_W3 + D2, N_PARAMS = OFF_B3 + 1;
+static_assert(N_PARAMS == HB_MLP_PARAMS, "parameter layout");
+constexpr int ROWS = 32;   // rows per block
+
+__device__ __forceinline__ float rb(float x, bool bf16) {
+    return bf16 ? __bfloat162float(__float2bfloat16_rn(x)) : x;
+}
+
+// one block: ROWS rows; thread j (0..63) computes hidden unit j for every row.
+// z1/z2 (optional) receive the pre-activations for the backward pass.
+template <bool BF16>
+__global__ void __launch_bounds__(64) k_mlp_fwd(const float *X, int n, const float *P, float *y, float *z1,
+                                                float *z2) {
+    __shared__ float xs[ROWS][D0];
+    __shared__ float h1[ROWS][D1 + 1];
+    __shared__ float h2[ROWS][D2 + 1];
+    const int r0 = blockIdx.x * ROWS, j = threadIdx.x;
+    for (int k = j; k < ROWS * D0; k += 64) {
+        int r = k / D0, c = k % D0;
+        xs[r][c] = (r0 + r < n) ? rb(X[(int64_t)(r0 + r) * D0 + c], BF16) : 0.f;
+    }
+    __syncthreads();
+    {
+        float w[D0];
+#pragma unroll
+        for (int i = 0; i < D0; i++) w[i] = rb(P[OFF_W1 + i * D1 + j], BF16);
+        const float b = P[OFF_B1 + j];
+        for (int r = 0; r < ROWS; r++) {
+            float acc = b;
+#pragma unroll
+            for (int i = 0; i < D0; i++) acc = fmaf(xs[r][i], w[i], acc);
+            if (z1 && r0 + r < n) z1[(int64_t)(r0 + r) * D1 + j] = acc;
+            h1[r][j] = rb(fmaxf(acc, 0.f), BF16);
+        }
+    }
+    __syncthreads();
+    {
+        const float b = P[OFF_B2 + j];
+        for (int r = 0; r < ROWS; r++) {
+            float acc = b;
+            for (int i = 0; i < D1; i++) acc = fmaf(h1[r][i], rb(P[OFF_W2 + i * D2 + j], BF16), acc);
+            if (z2 && r0 + r < n) z2[(int64_t)(r0 + r) * D2 + j] = acc;
+            h2[r][j] = rb(fmaxf(acc, 0.f), BF16);
+        }
+    }
+    __syncthreads();
+    if (j < ROWS && r0 + j < n) {
+        float acc = P[OFF_B3];
+        for (int i = 0; i < D2; i++) acc = fmaf(h2[j][i], rb(P[OFF_W3 + i], BF16), acc);
+        y[r0 + j] = acc;
+    }
+}
+
+// per-row backward quantities: dz2[r][j], dz1[r][i] (ReLU masks applied), dy[r]
+__global__ void __launch_bounds__(64) k_mlp_bwd_rows(const float *y, const float *t, int n, const float *P,
+                                                     const float *z1, float *z2dz2, float *z1dz1, float *dy) {
+    __shared__ float d2[ROWS][D2 + 1];
+    __shared__ float dys[ROWS];
+    const int r0 = blockIdx.x * ROWS, j = threadIdx.x;
+    if (j < ROWS) {
+        float v = 0.f;
+        if (r0 + j < n) v = 2.f * (y[r0 + j] - t[r0 + j]) / (float)n;
+        dys[j] = v;
+        if (r0 + j < n) dy[r0 + j] = v;
+    }
+    __syncthreads();
+    const float w3 = P[OFF_W3 + j];
+    for (int r = 0; r < ROWS; r++) {
+        float v = 0.f;
+        if (r0 + r < n) {
+            const float z = z2dz2[(int64_t)(r0 + r) * D2 + j];
+            v = z > 0.f ? dys[r] * w3 : 0.f;
+        }
+        d2[r][j] = v;
+    }
+    __syncthreads();
+    for (int r = 0; r < ROWS; r++) {
+        if (r0 + r >= n) break;
+        float acc = 0.f;
+        for (int k = 0; k < D2; k++) acc = fmaf(d2[r][k], P[OFF_W2 + j * D2 + k], acc);
+        const float z = z1[(int64_t)(r0 + r) * D1 + j];
+        z1dz1[(int64_t)(r0 + r) * D1 + j] = z > 0.f ? acc : 0.f;
+    }
+    __syncthreads();
+    for (int r = 0; r < ROWS; r++)
+        if (r0 + r < n) z2dz2[(int64_t)(r0 + r) * D2 + j] = d2[r][j];
+}
+
+// one thread per parameter, summing over all rows in a fixed order (deterministic)
+__global__ void k_mlp_grad(const float *X, int n, const float *z1, const float *z2, const float *dz1,
+                           const float *dz2, const float *dy, float *g) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= N_PARAMS) return;
+    float acc = 0.f;
+    if (p < OFF_B1) {
+        const int i = p / D1, j = p % D1;
+        for (int r = 0; r < n; r++) acc = fmaf(X[(int64_t)r * D0 + i], dz1[(int64_t)r * D1 + j], acc);
+    } else if (p < OFF_W2) {
+        const int j = p - OFF_B1;
+        for (int r = 0; r < n; r++) acc += dz1[(int64_t)r * D1 + j];
+    } else if (p < OFF_B2) {
+        const int i = (p - OFF_W2) / D2, j = (p - OFF_W2) % D2;
+        for (int r = 0; r < n; r++) acc = fmaf(fmaxf(z1[(int64_t)r * D1 + i], 0.f), dz2[(int64_t)r * D2 + j], acc);
+    } else if (p < OFF_W3) {
+        const int j = p - OFF_B2;
+        for (int r = 0; r < n; r++) acc += dz2[(int64_t)r * D2 + j];
+    } else if (p < OFF_B3) {
+        const int j = p - OFF_W3;
+        for (int r = 0; r < n; r++) acc = fmaf(fmaxf(z2[(int64_t)r * D2 + j], 0.f), dy[r], acc);
+    } else {
+        for (int r = 0; r < n; r++) acc += dy[r];
+    }
+    g[p] = acc;
+}
+
+__global__ void k_adam(float *p, const float *g, float *m, float *v, int n, float lr, float b1, float b2, float eps,
+                       float c1, float c2) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    const float mhat = mi / c1, vhat = vi / c2;
+    p[i] -= lr * mhat / (sqrtf(vhat) + eps);
+}
+
+}  // namespace
+
+size_t mlp_work_floats(int n) { return (size_t)n * (2 * D1 + 2 * D2 + 2) + 64; }
+
+cudaError_t mlp_forward(const float *X, int n, const float *params, float *y, int bf16, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    const unsigned g = (unsigned)((n + ROWS - 1) / ROWS);
+    if (bf16) k_mlp_fwd<true><<<g, 64, 0, s>>>(X, n, params, y, nullptr, nullptr);
+    else k_mlp_fwd<false><<<g, 64, 0, s>>>(X, n, params, y, nullptr, nullptr);
+    return cudaGetLastError();
+}
+
+// work: mlp_work_floats(n) floats
+cudaError_t mlp_backward(const float *X, const float *t, int n, const float *params, float *grad, float *work,
+                         cudaStream_t s) {
+    if (n <= 0) return cudaMemsetAsync(grad, 0, sizeof(float) * N_PARAMS, s);
+    float *z1 = work;
+    float *z2 = z1 + (size_t)n * D1;
+    float *dz1 = z2 + (size_t)n * D2;
+    float *y = dz1 + (size_t)n * D1;
+    float *dy = y + n;
+    const unsigned g = (unsigned)((n + ROWS - 1) / ROWS);
+    // z2 is kept; its copy in the backward buffer receives dz2
+    float *dz2 = dy + n;   // n * D2
+    k_mlp_fwd<false><<<g, 64, 0, s>>>(X, n, params, y, z1, z2);
+    cudaMemcpyAsync(dz2, z2, sizeof(float) * (size_t)n * D2, cudaMemcpyDeviceToDevice, s);
+    k_mlp_bwd_rows<<<g, 64, 0, s>>>(y, t, n, params, z1, dz2, dz1, dy);
+    k_mlp_grad<<<(N_PARAMS + 127) / 128, 128, 0, s>>>(X, n, z1, z2, dz1, dz2, dy, grad);
+    return cudaGetLastError();
+}
+
+cudaError_t adam_step(float *params, const float *grad, float *m, float *v, int n, int step, float lr, float b1,
+                      float b2, float eps, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    const float c1 = 1.f - powf(b1, (float)step), c2 = 1.f - powf(b2, (float)step);
+    k_adam<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(params, grad, m, v, n, lr, b1, b2, eps, c1, c2);
+    return cudaGetLastError();
+}
+
+}  // namespace hb

@@ -1,0 +1,351 @@
+"""ctypes binding of libhb (include/hb.h): argument marshalling only.
+
+Every step of blocking runs in the library's CUDA kernels; this module only
+turns Python/numpy/torch objects into the C structs and pointers of the
+C-ABI and back.  It raises if libhb.so has not been built: there is no
+fallback implementation.
+
+Columns are passed as objects with attributes ``type`` ("string", "int32",
+"fp32"), ``data`` (numpy array or torch tensor), ``offsets`` (strings: n+1
+uint32) and ``valid`` (uint8 per row or None).  Tensors on a CUDA device are
+passed as device pointers (``on_device=True``).
+
+Predicates are tuples ``(kind, col_t, col_s, k, q, num, den, delta)`` with
+kind in {"eq", "eq_prefix", "ed", "jaccard", "absdiff"}.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libhb.so")
+
+HB_OK, HB_ERR_ARG, HB_ERR_OOM, HB_ERR_CUDA, HB_ERR_STATE, HB_ERR_OVERFLOW, HB_ERR_DEVICE_TIMEOUT = 0, -1, -2, -3, -4, -5, -6
+KINDS = {"eq": 0, "eq_prefix": 1, "ed": 2, "jaccard": 3, "absdiff": 4}
+TYPES = {"string": 0, "int32": 1, "fp32": 2}
+PLAN_MODES = {"rule_data": 0, "learned": 1, "given": 2, "random": 3, "cost_first": 4, "sel_first": 5}
+MAX_MDS, MAX_PREDS, FEATURES = 64, 128, 32
+MLP_PARAMS = 32 * 64 + 64 + 64 * 64 + 64 + 64 + 1
+
+
+class HBError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"libhb status {status}: {msg}")
+        self.status = status
+
+
+class hb_column(ctypes.Structure):
+    _fields_ = [("type", ctypes.c_int32), ("reserved", ctypes.c_int32), ("data", ctypes.c_void_p),
+                ("offsets", ctypes.c_void_p), ("valid", ctypes.c_void_p), ("data_bytes", ctypes.c_uint64)]
+
+
+class hb_predicate(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("col_t", ctypes.c_int32), ("col_s", ctypes.c_int32),
+                ("k", ctypes.c_int32), ("q", ctypes.c_int32), ("num", ctypes.c_uint32), ("den", ctypes.c_uint32),
+                ("delta", ctypes.c_float)]
+
+
+class hb_pair(ctypes.Structure):
+    _fields_ = [("tid1", ctypes.c_uint32), ("tid2", ctypes.c_uint32)]
+
+
+class hb_options(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int32), ("tile", ctypes.c_int32), ("chunk_bytes", ctypes.c_uint64),
+                ("seed", ctypes.c_uint64), ("stream", ctypes.c_void_p), ("out_capacity", ctypes.c_int64),
+                ("flags", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class hb_plan_info(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int32), ("n_preds", ctypes.c_int32), ("n_ops", ctypes.c_int32),
+                ("n_eq", ctypes.c_int32), ("op_pred", ctypes.c_int32 * MAX_PREDS),
+                ("md_order", ctypes.c_int32 * MAX_MDS), ("sp", ctypes.c_double * MAX_PREDS),
+                ("cost", ctypes.c_double * MAX_PREDS), ("pred_md", ctypes.c_int32 * MAX_PREDS),
+                ("tile", ctypes.c_int32), ("n_mds", ctypes.c_int32)]
+
+
+class hb_stats(ctypes.Structure):
+    _fields_ = [("n_rows_r", ctypes.c_int64), ("n_rows_s", ctypes.c_int64), ("candidate_pairs", ctypes.c_int64),
+                ("emitted_pairs", ctypes.c_int64), ("tiles", ctypes.c_int64), ("blocks", ctypes.c_int64),
+                ("ms_h2d", ctypes.c_double), ("ms_encode", ctypes.c_double), ("ms_plan", ctypes.c_double),
+                ("ms_block_build", ctypes.c_double), ("ms_eval", ctypes.c_double), ("ms_sort", ctypes.c_double),
+                ("ms_d2h", ctypes.c_double), ("ms_total", ctypes.c_double), ("device_bytes", ctypes.c_int64),
+                ("tile", ctypes.c_int32), ("n_mds", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class hb_pred_log(ctypes.Structure):
+    _fields_ = [("features", ctypes.c_float * FEATURES), ("log_cost", ctypes.c_float),
+                ("logit_pass", ctypes.c_float), ("evaluated", ctypes.c_int64), ("passed", ctypes.c_int64),
+                ("pred", ctypes.c_int32), ("kind", ctypes.c_int32)]
+
+
+EXPORTS = ["hb_create", "hb_destroy", "hb_last_error", "hb_version", "hb_load_table", "hb_add_md", "hb_clear_mds",
+           "hb_plan", "hb_block", "hb_block_device", "hb_block_stream", "hb_block_batch", "hb_free_pairs",
+           "hb_get_stats", "hb_plan_order", "hb_log_predicates", "hb_predicate_features", "hb_train_cost_model",
+           "hb_get_cost_model", "hb_set_cost_model", "hb_mlp_forward", "hb_mlp_forward_bf16", "hb_mlp_backward",
+           "hb_adam_step"]
+
+_lib = None
+
+
+def lib():
+    """Load libhb.so; raises when it has not been built (no fallback exists)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_2410_04349_gb300.build.build()")
+    L = ctypes.CDLL(LIB_PATH)
+    P, i32, i64, st = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_int
+    sig = {
+        "hb_create": (st, [P, P]), "hb_destroy": (None, [P]), "hb_last_error": (ctypes.c_char_p, []),
+        "hb_version": (ctypes.c_char_p, []), "hb_load_table": (st, [P, i32, i64, i32, P, i32]),
+        "hb_add_md": (st, [P, i32, P, P]), "hb_clear_mds": (st, [P]), "hb_plan": (st, [P, i32, P]),
+        "hb_block": (st, [P, P, P]), "hb_block_device": (st, [P, P, P]),
+        "hb_block_stream": (st, [P, i64, i32, P, P, P]), "hb_block_batch": (st, [P, i32, P, P, P]),
+        "hb_free_pairs": (None, [P]), "hb_get_stats": (st, [P, P]),
+        "hb_plan_order": (st, [i32, P, P, i32, P, P, P, P, P, P, P]),
+        "hb_log_predicates": (st, [P, P, i32, P]), "hb_predicate_features": (st, [P, P, i32, P]),
+        "hb_train_cost_model": (st, [P, i32, P, P, P, i32, ctypes.c_float, ctypes.c_uint64, P]),
+        "hb_get_cost_model": (st, [P, P]), "hb_set_cost_model": (st, [P, P]),
+        "hb_mlp_forward": (st, [P, i32, P, P, P]), "hb_mlp_forward_bf16": (st, [P, i32, P, P, P]),
+        "hb_mlp_backward": (st, [P, P, i32, P, P, P]),
+        "hb_adam_step": (st, [P, P, P, P, i32, i32, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                              P]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def _check(status, what=""):
+    if status != HB_OK:
+        msg = lib().hb_last_error()
+        raise HBError(status, f"{what}: {msg.decode() if msg else ''}")
+
+
+def _ptr(x):
+    """Raw address of a numpy array or torch tensor (None -> NULL)."""
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr() or None
+    return x.ctypes.data if x.size else None
+
+
+def _nbytes(x):
+    if hasattr(x, "element_size"):
+        return x.numel() * x.element_size()
+    return x.nbytes
+
+
+def _columns(cols):
+    arr = (hb_column * max(len(cols), 1))()
+    keep = []
+    for i, c in enumerate(cols):
+        data = c.data
+        if not hasattr(data, "data_ptr"):
+            data = np.ascontiguousarray(data)
+        keep.append(data)
+        hc = hb_column()
+        hc.type = TYPES[c.type]
+        hc.data = _ptr(data)
+        if c.type == "string":
+            off = c.offsets
+            if not hasattr(off, "data_ptr"):
+                off = np.ascontiguousarray(off, np.uint32)
+            keep.append(off)
+            hc.offsets = _ptr(off)
+            hc.data_bytes = _nbytes(data)
+        if c.valid is not None:
+            v = c.valid
+            if not hasattr(v, "data_ptr"):
+                v = np.ascontiguousarray(v, np.uint8)
+            keep.append(v)
+            hc.valid = _ptr(v)
+        arr[i] = hc
+    return arr, keep
+
+
+def _preds(md):
+    arr = (hb_predicate * len(md))()
+    for i, p in enumerate(md):
+        kind, ct, cs, k, q, num, den, delta = p
+        arr[i] = hb_predicate(KINDS[kind], ct, cs, k, q, num, den, delta)
+    return arr
+
+
+def _pairs_to_numpy(ptr, n):
+    if n == 0:
+        return np.zeros((0, 2), np.int64)
+    buf = np.ctypeslib.as_array(ctypes.cast(ptr, ctypes.POINTER(ctypes.c_uint32)), shape=(n * 2,))
+    return buf.reshape(n, 2).astype(np.int64)
+
+
+class Context:
+    """One libhb context (hb_create ... hb_destroy)."""
+
+    def __init__(self, device=0, tile=0, chunk_bytes=0, seed=0, stream=None, out_capacity=0):
+        L = lib()
+        opt = hb_options(device, tile, chunk_bytes, seed, stream, out_capacity, 0, 0)
+        h = ctypes.c_void_p()
+        _check(L.hb_create(ctypes.byref(h), ctypes.byref(opt)), "hb_create")
+        self._h = h
+        self._keep = []
+
+    def close(self):
+        if self._h:
+            lib().hb_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # ---- tables and rules
+    def load_table(self, side, n_rows, columns, on_device=False):
+        arr, keep = _columns(columns)
+        _check(lib().hb_load_table(self._h, side, n_rows, len(columns), arr, 1 if on_device else 0),
+               "hb_load_table")
+
+    def add_md(self, preds):
+        out = ctypes.c_int32()
+        _check(lib().hb_add_md(self._h, len(preds), _preds(preds), ctypes.byref(out)), "hb_add_md")
+        return out.value
+
+    def clear_mds(self):
+        _check(lib().hb_clear_mds(self._h), "hb_clear_mds")
+
+    def plan(self, mode="rule_data"):
+        info = hb_plan_info()
+        _check(lib().hb_plan(self._h, PLAN_MODES[mode] if isinstance(mode, str) else mode, ctypes.byref(info)),
+               "hb_plan")
+        return info
+
+    # ---- blocking
+    def block(self):
+        """Sorted unique pairs as int64 array [n, 2] (host)."""
+        p = ctypes.c_void_p()
+        n = ctypes.c_int64()
+        _check(lib().hb_block(self._h, ctypes.byref(p), ctypes.byref(n)), "hb_block")
+        try:
+            return _pairs_to_numpy(p, n.value)
+        finally:
+            lib().hb_free_pairs(p)
+
+    def block_device(self):
+        """(device pointer of n sorted hb_pair, n); valid until the next call."""
+        p = ctypes.c_void_p()
+        n = ctypes.c_int64()
+        _check(lib().hb_block_device(self._h, ctypes.byref(p), ctypes.byref(n)), "hb_block_device")
+        return p.value, n.value
+
+    def block_stream(self, n_rows_s, columns_s):
+        arr, keep = _columns(columns_s)
+        p = ctypes.c_void_p()
+        n = ctypes.c_int64()
+        _check(lib().hb_block_stream(self._h, n_rows_s, len(columns_s), arr, ctypes.byref(p), ctypes.byref(n)),
+               "hb_block_stream")
+        try:
+            return _pairs_to_numpy(p, n.value)
+        finally:
+            lib().hb_free_pairs(p)
+
+    def block_batch(self, job_rows):
+        job_rows = np.ascontiguousarray(job_rows, np.int64)
+        n_jobs = len(job_rows) - 1
+        offs = np.zeros(n_jobs + 1, np.int64)
+        p = ctypes.c_void_p()
+        _check(lib().hb_block_batch(self._h, n_jobs, job_rows.ctypes.data, ctypes.byref(p), offs.ctypes.data),
+               "hb_block_batch")
+        try:
+            return _pairs_to_numpy(p, int(offs[-1])), offs
+        finally:
+            lib().hb_free_pairs(p)
+
+    def stats(self):
+        s = hb_stats()
+        _check(lib().hb_get_stats(self._h, ctypes.byref(s)), "hb_get_stats")
+        return s.as_dict()
+
+    # ---- learned cost model
+    def log_predicates(self, cap=MAX_PREDS):
+        arr = (hb_pred_log * cap)()
+        n = ctypes.c_int32()
+        _check(lib().hb_log_predicates(self._h, arr, cap, ctypes.byref(n)), "hb_log_predicates")
+        return [arr[i] for i in range(n.value)]
+
+    def predicate_features(self, cap=MAX_PREDS):
+        out = np.zeros((cap, FEATURES), np.float32)
+        n = ctypes.c_int32()
+        _check(lib().hb_predicate_features(self._h, out.ctypes.data, cap, ctypes.byref(n)), "hb_predicate_features")
+        return out[:n.value]
+
+    def train_cost_model(self, X, y_cost, y_sel, epochs=300, lr=3e-3, seed=0):
+        X = np.ascontiguousarray(X, np.float32)
+        y_cost = np.ascontiguousarray(y_cost, np.float32)
+        y_sel = np.ascontiguousarray(y_sel, np.float32)
+        loss = np.zeros(2, np.float32)
+        _check(lib().hb_train_cost_model(self._h, len(X), X.ctypes.data, y_cost.ctypes.data, y_sel.ctypes.data,
+                                         epochs, lr, seed, loss.ctypes.data), "hb_train_cost_model")
+        return loss
+
+    def get_cost_model(self):
+        out = np.zeros(2 * MLP_PARAMS, np.float32)
+        _check(lib().hb_get_cost_model(self._h, out.ctypes.data), "hb_get_cost_model")
+        return out
+
+    def set_cost_model(self, params):
+        params = np.ascontiguousarray(params, np.float32)
+        _check(lib().hb_set_cost_model(self._h, params.ctypes.data), "hb_set_cost_model")
+
+
+def plan_order(sp, cost, mds, skip=None):
+    """Host-only ordering (hb_plan_order): (program, cp per MD, MD order)."""
+    sp = np.ascontiguousarray(sp, np.float64)
+    cost = np.ascontiguousarray(cost, np.float64)
+    starts = np.zeros(len(mds) + 1, np.int32)
+    flat = []
+    for m, md in enumerate(mds):
+        flat.extend(md)
+        starts[m + 1] = len(flat)
+    flat = np.ascontiguousarray(flat if flat else [0], np.int32)
+    sk = None if skip is None else np.ascontiguousarray(skip, np.uint8)
+    prog = np.zeros(MAX_PREDS, np.int32)
+    n_prog = ctypes.c_int32()
+    cp = np.zeros(max(len(mds), 1), np.int32)
+    order = np.zeros(max(len(mds), 1), np.int32)
+    _check(lib().hb_plan_order(len(sp), sp.ctypes.data, cost.ctypes.data, len(mds), starts.ctypes.data,
+                               flat.ctypes.data, None if sk is None else sk.ctypes.data, prog.ctypes.data,
+                               ctypes.byref(n_prog), cp.ctypes.data, order.ctypes.data), "hb_plan_order")
+    return prog[:n_prog.value].tolist(), cp[:len(mds)].tolist(), order[:len(mds)].tolist()
+
+
+def mlp_forward(X, params, y, stream=None, bf16=False):
+    f = lib().hb_mlp_forward_bf16 if bf16 else lib().hb_mlp_forward
+    _check(f(_ptr(X), X.shape[0], _ptr(params), _ptr(y), stream), "hb_mlp_forward")
+
+
+def mlp_backward(X, t, params, grad, stream=None):
+    _check(lib().hb_mlp_backward(_ptr(X), _ptr(t), X.shape[0], _ptr(params), _ptr(grad), stream), "hb_mlp_backward")
+
+
+def adam_step(params, grad, m, v, step, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    _check(lib().hb_adam_step(_ptr(params), _ptr(grad), _ptr(m), _ptr(v), params.numel(), step, lr, beta1, beta2,
+                              eps, stream), "hb_adam_step")
