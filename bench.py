@@ -1,0 +1,360 @@
+#!/usr/bin/env python
+"""Benchmark of rule-based blocking on GB300.
+
+Workload: one relation of 1,000,000 tuples with 8 attributes (two strings of
+8-60 characters in words, three Zipf(1.1) categorical keys over 10^3 / 10^4 /
+10^5 values, two fp32 lognormal numerics, a row id), 10% near-duplicates made
+by byte edits and word swaps, and four MDs of 3-4 predicates (equality on two
+or three keys plus edit distance, 3-gram Jaccard and |a-b| <= delta).  The
+data is seeded and synthetic (the paper's datasets are not available).
+
+One step is the whole blocking path on the GPU: load the raw columns (already
+in device memory), plan, encode, build blocks, evaluate every candidate pair,
+compact and sort the result.  The metric is candidate pairs evaluated per
+second (pairs that agree on all equality keys of some MD, each counted once).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gpu|reference]
+
+With N > 1 (torchrun, one process per GPU) every rank blocks its own table
+(seed + rank): the work is independent per rank, so scaling is weak and no
+collective touches the data path.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "tuple pairs evaluated/sec"
+UNIT = "pairs/s"
+WORKLOAD = ("single table, 1,000,000 tuples x 8 attributes (2 strings 8-60 chars, 3 Zipf(1.1) keys over "
+            "1e3/1e4/1e5 values, 2 fp32), 10% near-duplicates, 4 MDs")
+
+# algorithmic integer operations per unit of work ("Roofline")
+OPS_EXAMINED_PER_KEY = 3      # compare, mask missing, merge into the match vector
+OPS_EXAMINED_FIXED = 3        # match vector -> alive MDs, owner test
+OPS = {  # kind: (per evaluation, per stage-1 pass, per stage-2 pass, per core unit)
+    "absdiff": (3, 0, 0, 0),   # subtract, absolute value, compare
+    "ed": (4, 18, 0, 5),       # length filter; 16-bin bag distance; banded DP cell
+    "jaccard": (7, 18, 0, 6),  # size filter; 32-bin count bound; merge step
+}
+KIND_NAMES = {2: "ed", 3: "jaccard", 4: "absdiff"}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
+    ap.add_argument("--rows", type=int, default=1_000_000)
+    ap.add_argument("--cpu-sample-rows", type=int, default=80_000)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), \
+        int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def aggregate(units: float, seconds: float, world: int):
+    """Whole-job units and the slowest rank's time (all_reduce SUM / MAX)."""
+    if world <= 1:
+        return units, seconds
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    u = torch.tensor([units], dtype=torch.float64, device=dev)
+    s = torch.tensor([seconds], dtype=torch.float64, device=dev)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    dist.all_reduce(s, op=dist.ReduceOp.MAX)
+    return float(u.item()), float(s.item())
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = tempfile.mktemp(suffix=".csv")
+
+    def __enter__(self):
+        try:
+            self.out = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.out,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        try:
+            self.out.close()
+        except Exception:
+            pass
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) < 9:
+                    continue
+                try:
+                    sm.append(float(f[1]))
+                    mx.append(float(f[2]))
+                except ValueError:
+                    continue
+                for name, v in zip(["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"],
+                                   f[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(name)
+        except OSError:
+            pass
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+def eval_kernel_traffic():
+    """DRAM bytes per full-workload launch of the evaluation kernel from the
+    committed ncu summary, or None when the kernel changed since it was taken."""
+    path = os.path.join(ROOT, "profiles", "k_eval_c2.txt")
+    src = os.path.join(ROOT, "paper_2410_04349_gb300", "csrc", "k_eval.cu")
+    try:
+        text = open(path).read()
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    except OSError:
+        return None
+    vals = dict(line.split(":", 1) for line in text.splitlines() if ":" in line)
+    if vals.get("k_eval.cu sha256[:16]", "").strip() != sha:
+        return None
+    try:
+        return float(vals["dram bytes per full launch"].strip())
+    except (KeyError, ValueError):
+        return None
+
+
+def algorithmic_ops(logs, examined, n_eq):
+    total = examined * (OPS_EXAMINED_PER_KEY * n_eq + OPS_EXAMINED_FIXED)
+    for L in logs:
+        base, s1, s2, core = OPS[KIND_NAMES[L["kind"]]]
+        total += L["evaluated"] * base + L["stage1"] * s1 + L["stage2"] * s2 + L["core"] * core
+    return float(total)
+
+
+def device_columns(table, device):
+    import torch
+
+    class Col:
+        pass
+
+    cols = []
+    for c in table.columns:
+        d = Col()
+        d.type = c.type
+        d.data = torch.from_numpy(c.data).to(device)
+        d.offsets = torch.from_numpy(c.offsets.view(np.int32)).to(device) if c.offsets is not None else None
+        d.valid = torch.from_numpy(c.valid).to(device) if c.valid is not None else None
+        cols.append(d)
+    return cols
+
+
+def cpu_oracle_rate(table, mds, rows: int):
+    """The oracle as it stands (grouped evaluation, all host threads) on the
+    first `rows` tuples: (pairs/s, seconds, candidate pairs, threads)."""
+    import oracle
+    sub = table.slice(0, min(rows, table.n_rows))
+    threads = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    _, cand = oracle.block_hash(sub, mds, threads=threads)
+    dt = time.perf_counter() - t0
+    return cand / dt, dt, cand, threads
+
+
+def run_reference(args, rank, world):
+    """The oracle on the host cores (this tier's reference arm)."""
+    if rank != 0:
+        return 0
+    import synth
+    t, mds = synth.config2(n=args.rows)
+    rows = args.cpu_sample_rows // 2
+    for _ in range(args.warmup):
+        cpu_oracle_rate(t, mds, rows)
+    rates, secs, cand, threads = [], [], 0, 1
+    for _ in range(args.steps):
+        r, dt, cand, threads = cpu_oracle_rate(t, mds, rows)
+        rates.append(r)
+        secs.append(dt)
+    value = cand * len(secs) / sum(secs)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(secs) / len(secs),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample": f"first {rows} tuples", "l2": "n/a (CPU)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": f"grouped oracle on the first {rows} of {args.rows} tuples, {cand} candidate pairs"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    import torch
+    import synth
+    from paper_2410_04349_gb300 import hb
+
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    device = torch.device("cuda", local)
+    torch.cuda.set_device(device)
+    table, mds = synth.config2(seed=synth.BASE_SEED + 2 + 1000 * rank, n=args.rows)
+    dev_cols = device_columns(table, device)
+    stream = torch.cuda.current_stream(device)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=device)
+    ctx = hb.Context(device=local, stream=stream.cuda_stream)
+    for md in mds:
+        ctx.add_md(md)
+
+    def step():
+        ctx.load_table(0, table.n_rows, dev_cols, on_device=True)
+        ctx.plan("rule_data")
+        _, n_out = ctx.block_device()
+        return n_out
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    launches0 = ctx.stats()["kernel_launches"]
+    if world > 1:
+        torch.distributed.barrier()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    eval_ms, cands, outs = [], [], []
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        for i in range(args.steps):
+            flush.zero_()                       # evict L2 (256 MiB > 129 MB) between steps
+            ev[i][0].record(stream)
+            n_out = step()
+            ev[i][1].record(stream)
+            st = ctx.stats()
+            eval_ms.append(st["ms_eval"])
+            cands.append(st["candidate_pairs"])
+            outs.append(n_out)
+        torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    launches = ctx.stats()["kernel_launches"] - launches0
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    local_s = sum(step_ms) / 1e3
+    units, secs = aggregate(float(sum(cands)), local_s, world)
+    value = units / secs
+    st = ctx.stats()
+
+    # roofline of the evaluation kernel: algorithmic integer ops / its launch time
+    logs = ctx.log_predicates(profile=False)
+    ex = ctx.stats()["examined_pairs"]
+    info = ctx.plan("rule_data")
+    n_eq = info.n_eq
+    alg = algorithmic_ops(logs, ex, n_eq)
+    clocks = clk.summary()
+    sm_mhz = clocks["sm_mhz"] or measured_peaks().get("clocks_under_load", {}).get("sm_mhz_median", 1440.0)
+    n_sm = torch.cuda.get_device_properties(device).multi_processor_count
+    peak_ops = n_sm * 4 * 32 * sm_mhz * 1e6          # one 32-lane integer warp instruction per SMSP per clock
+    eval_s = statistics.median(eval_ms) / 1e3
+    achieved = alg / eval_s
+    roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12, "unit": "Tops/s",
+                "frac": achieved / peak_ops, "traffic": eval_kernel_traffic(), "kernel": "k_eval",
+                "ops_per_launch": alg, "launch_ms": eval_s * 1e3,
+                "peak_basis": f"{n_sm} SMs x 4 SMSPs x 32 lanes x {sm_mhz:.0f} MHz (median SM clock sampled during "
+                              f"the timed region)"}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": max(args.warmup, 3), "ms_per_step": secs * 1e3 / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n_tuples": table.n_rows, "n_mds": len(mds), "parallelism": f"dp{world}",
+                   "l2": "flushed (256 MiB write) before every timed step", "inputs": "raw columns resident in HBM"},
+        "candidate_pairs_per_step": cands[-1], "emitted_pairs_per_step": outs[-1],
+        "examined_pairs_per_step": ex,
+        "eval_kernel_pairs_per_s": cands[-1] / eval_s,
+        "stage_ms": {k: st[k] for k in ("ms_encode", "ms_plan", "ms_block_build", "ms_eval", "ms_sort", "ms_d2h")},
+        "gpu_launches": launches,
+        "clocks": {"sm_mhz": clocks["sm_mhz"], "sm_max_mhz": clocks["sm_max_mhz"], "reasons": clocks["reasons"]},
+        "roofline": roofline,
+    }
+
+    if not args.no_e2e:
+        host_cols = table.columns
+        h2d = table.nbytes()
+        times, last_n = [], 0
+        for i in range(1 + min(args.steps, 5)):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ctx.load_table(0, table.n_rows, host_cols, on_device=False)
+            ctx.plan("rule_data")
+            pairs = ctx.block()
+            dt = time.perf_counter() - t0
+            last_n = len(pairs)
+            if i > 0:
+                times.append(dt)
+        e2e_units, e2e_s = aggregate(float(cands[-1]) * len(times), sum(times), world)
+        line["e2e"] = {"value": e2e_units / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                       "d2h_bytes_per_step": last_n * 8, "ms_per_step": 1e3 * e2e_s / len(times)}
+    ctx.close()
+
+    if rank == 0 and world == 1 and not args.no_cpu:
+        rate, dt, cand, threads = cpu_oracle_rate(table, mds, args.cpu_sample_rows)
+        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
+                                "sample": f"grouped oracle on the first {args.cpu_sample_rows} of {table.n_rows} "
+                                          f"tuples: {cand} candidate pairs in {dt:.1f} s"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -141,6 +141,8 @@ typedef struct {
     int64_t device_bytes;      /* device memory held by the context */
     int32_t tile;              /* tile side used */
     int32_t n_mds;
+    int64_t kernel_launches;   /* CUDA kernels launched by the library so far (process-wide) */
+    int64_t examined_pairs;    /* pairs inside blocks looked at by the evaluation kernel (last call) */
 } hb_stats;
 
 /* ---- context ---- */
@@ -236,16 +238,24 @@ typedef struct {
     float logit_pass;        /* logit(pass rate), clamped to [-12, 12] */
     int64_t evaluated;       /* evaluations counted */
     int64_t passed;
+    int64_t cycles;          /* clock64 cycles spent in the evaluations */
+    int64_t stage1;          /* evaluations past the length / size filter (ED, Jaccard) */
+    int64_t stage2;          /* evaluations past the character-bin / gram-bin filter (ED, Jaccard) */
+    int64_t core;            /* ED: band cells computed; Jaccard: merge steps */
     int32_t pred;            /* distinct predicate id in the context */
-    int32_t kind;
+    int32_t kind;            /* hb_pkind */
 } hb_pred_log;
 
 /*
  * Run the current plan once with per-predicate instrumentation (evaluations,
- * passes and clock cycles per predicate) and append one record per
- * non-equality predicate to out (capacity cap).  *n_out receives the count.
+ * passes, filter passes, core work and clock cycles per predicate) and write
+ * one record per non-equality predicate, in program order, to out (capacity
+ * cap).  profile = 0: the plan as it runs (early exit at the first witness
+ * or when every MD has failed); profile = 1: every predicate of every MD
+ * whose equality keys match is evaluated (no early exit), which measures each
+ * predicate's own pass rate and cost.  *n_out receives the record count.
  */
-HB_API hb_status hb_log_predicates(hb_ctx *ctx, hb_pred_log *out, int32_t cap, int32_t *n_out);
+HB_API hb_status hb_log_predicates(hb_ctx *ctx, int32_t profile, hb_pred_log *out, int32_t cap, int32_t *n_out);
 
 /* Features the cost model sees for each distinct predicate of the current plan. */
 HB_API hb_status hb_predicate_features(hb_ctx *ctx, float *features_out, int32_t cap_preds, int32_t *n_out);

@@ -27,6 +27,8 @@
 
 namespace hb {
 
+std::atomic<long long> g_kernel_launches{0};
+
 static thread_local std::string g_err;
 
 hb_status fail(hb_status st, const std::string &msg) {
@@ -881,6 +883,7 @@ static EvalParams make_params(hb_ctx *c, const uint32_t *rec_r, const uint32_t *
     P.out_count = ctr + 1;
     P.out_cap = (uint64_t)c->out_cap;
     P.cand_count = ctr + 2;
+    P.exam_count = ctr + 5;
     P.claim = 2;
     P.log = as<unsigned long long>(c->w_log);
     return P;
@@ -919,20 +922,23 @@ hb_status block_eval_sort(hb_ctx *c, const uint32_t *rec_r, int64_t n_r, const u
     const int grid = bps * c->n_sm;
     for (int attempt = 0; attempt < 2; attempt++) {
         EvalParams P = make_params(c, rec_r, rec_s, side_s, self, ctr, key_bits_s);
-        HB_CUDA(launch_eval(P, grid, smem, logging, c->stream));
+        P.profile = logging == 2 ? 1 : 0;   // 1: instrumented plan; 2: instrumented, no early exit
+        HB_CUDA(launch_eval(P, grid, smem, logging ? 1 : 0, c->stream));
         if (tm && attempt == 0) tm->mark();
-        unsigned long long h[5];
+        unsigned long long h[6];
         HB_CUDA(cudaMemcpyAsync(h, ctr, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
         HB_CUDA(cudaStreamSynchronize(c->stream));
         if (h[4]) return fail(HB_ERR_INTERNAL, "block list overflow");
         res.n_out = (int64_t)h[1];
         res.cand = (int64_t)h[2];
         res.blocks = (int64_t)(uint32_t)h[3];
+        res.examined = (int64_t)h[5];
         if (res.n_out <= c->out_cap) break;
         // the slab was too small: grow it to the exact count and evaluate again
         c->out_cap = res.n_out + res.n_out / 8 + 1024;
         HB_TRY(grow(c, c->w_out, sizeof(uint64_t) * (size_t)c->out_cap));
         HB_CUDA(cudaMemsetAsync(ctr, 0, 3 * sizeof(unsigned long long), c->stream));
+        HB_CUDA(cudaMemsetAsync(ctr + 5, 0, sizeof(unsigned long long), c->stream));
         if (logging) HB_CUDA(cudaMemsetAsync(c->w_log.p, 0, sizeof(unsigned long long) * MAX_OPS * 8, c->stream));
     }
     {
@@ -1001,6 +1007,7 @@ static hb_status run_block(hb_ctx *c, hb_pair **out, int64_t *n_out, bool to_hos
     S.emitted_pairs = res.n_out;
     S.tiles = res.tiles;
     S.blocks = res.blocks;
+    S.examined_pairs = res.examined;
     S.ms_encode = tm.ms(0, 1);
     S.ms_block_build = tm.ms(1, 2);
     S.ms_eval = tm.ms(2, 3);
@@ -1039,5 +1046,6 @@ extern "C" hb_status hb_get_stats(const hb_ctx *c, hb_stats *out) {
                          &c->w_prefix, &c->w_scan, &c->w_out, &c->w_alt, &c->w_sort, &c->w_pairs};
     for (const Buf *b : bufs) tot += b->bytes;
     out->device_bytes = (int64_t)tot;
+    out->kernel_launches = (int64_t)g_kernel_launches.load();
     return HB_OK;
 }

@@ -134,6 +134,7 @@ struct RunResult {
     int64_t cand = 0;
     int64_t tiles = 0;
     int64_t blocks = 0;
+    int64_t examined = 0;
 };
 
 struct Timer {

@@ -4,12 +4,17 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <string>
 #include <vector>
 
 #include "hb.h"
 
 namespace hb {
+
+// kernel launches made by the library (all contexts, cumulative)
+extern std::atomic<long long> g_kernel_launches;
+#define HB_LAUNCHED(n) (::hb::g_kernel_launches.fetch_add((n), std::memory_order_relaxed))
 
 constexpr uint32_t NULL_CODE = 0xFFFFFFFFu;     // missing value: equal to nothing
 constexpr uint32_t NOMATCH_CODE = 0xFFFFFFFEu;  // S value that no R tuple holds
@@ -87,8 +92,10 @@ struct EvalParams {
     unsigned long long *out_count;
     uint64_t out_cap;
     unsigned long long *cand_count;
+    unsigned long long *exam_count;
     uint32_t row_base, col_base;  // added to member ids when packing (chunked S)
     int32_t claim;                // tiles per atomic claim
+    int32_t profile;              // logging variant: evaluate every needed predicate, no early exit
     // instrumentation (logging variant only)
     unsigned long long *log;      // per op: [evaluated, passed, cycles] (3 * MAX_OPS)
 };

@@ -75,9 +75,66 @@ extern "C" hb_status hb_set_cost_model(hb_ctx *c, const float *params) {
     return HB_OK;
 }
 
-extern "C" hb_status hb_log_predicates(hb_ctx *c, hb_pred_log *out, int32_t cap, int32_t *n_out) {
-    (void)c; (void)out; (void)cap; (void)n_out;
-    return fail(HB_ERR_STATE, "hb_log_predicates: not available yet");
+namespace hb {
+
+// One instrumented evaluation over the given records; per program op the
+// counters [evaluated, passed, cycles, stage1, stage2, core].
+hb_status instrumented_run(hb_ctx *c, const uint32_t *rec_r, int64_t n_r, const uint32_t *rec_s, int64_t n_s,
+                           bool self, int profile, std::vector<unsigned long long> &counters, RunResult &res) {
+    const int kbs = bits_for((uint64_t)std::max<int64_t>(n_s, 2));
+    const int kb = kbs + bits_for((uint64_t)std::max<int64_t>(n_r, 2));
+    uint64_t *sorted = nullptr;
+    HB_TRY(block_eval_sort(c, rec_r, n_r, rec_s, n_s, self, 1, kb, kbs, profile ? 2 : 1, res, &sorted, nullptr));
+    counters.assign((size_t)MAX_OPS * 6, 0ull);
+    HB_CUDA(cudaMemcpyAsync(counters.data(), c->w_log.p, sizeof(unsigned long long) * counters.size(),
+                            cudaMemcpyDeviceToHost, c->stream));
+    HB_CUDA(cudaStreamSynchronize(c->stream));
+    return HB_OK;
+}
+
+static float logit_clamped(double p) {
+    p = std::min(std::max(p, 1e-6), 1.0 - 1e-6);
+    double v = std::log(p / (1.0 - p));
+    return (float)std::min(std::max(v, -12.0), 12.0);
+}
+
+}  // namespace hb
+
+extern "C" hb_status hb_log_predicates(hb_ctx *c, int32_t profile, hb_pred_log *out, int32_t cap, int32_t *n_out) {
+    if (!c || !out || !n_out) return fail(HB_ERR_ARG, "hb_log_predicates: NULL argument");
+    *n_out = 0;
+    cudaSetDevice(c->device);
+    HB_TRY(ensure_ready(c, false));
+    const bool self = is_self(c);
+    const int64_t nr = c->side[0].n, ns = self ? nr : c->side[1].n;
+    std::vector<unsigned long long> ctr;
+    RunResult res;
+    HB_TRY(instrumented_run(c, c->side[0].rec, nr, self ? c->side[0].rec : c->side[1].rec, ns, self, profile, ctr,
+                            res));
+    c->stats.candidate_pairs = res.cand;
+    c->stats.examined_pairs = res.examined;
+    c->stats.emitted_pairs = res.n_out;
+    const int n_ops = (int)c->ops.size();
+    if (n_ops > cap) return fail(HB_ERR_OVERFLOW, "hb_log_predicates: capacity below the number of predicates");
+    std::vector<float> feats;
+    for (int k = 0; k < n_ops; k++) {
+        hb_pred_log &L = out[k];
+        memset(&L, 0, sizeof(L));
+        const unsigned long long *v = &ctr[(size_t)k * 6];
+        L.evaluated = (int64_t)v[0];
+        L.passed = (int64_t)v[1];
+        L.cycles = (int64_t)v[2];
+        L.stage1 = (int64_t)v[3];
+        L.stage2 = (int64_t)v[4];
+        L.core = (int64_t)v[5];
+        L.pred = c->program[k];
+        L.kind = c->preds[c->program[k]].p.kind;
+        const double ev = std::max<double>((double)v[0], 1.0);
+        L.log_cost = (float)std::log(std::max((double)v[2] / ev, 1.0));
+        L.logit_pass = logit_clamped(v[0] ? (double)v[1] / ev : 0.5);
+    }
+    *n_out = n_ops;
+    return HB_OK;
 }
 
 extern "C" hb_status hb_predicate_features(hb_ctx *c, float *features_out, int32_t cap_preds, int32_t *n_out) {

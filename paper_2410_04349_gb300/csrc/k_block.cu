@@ -193,24 +193,28 @@ void group_build(const uint32_t *rec, int W, int64_t n, const int32_t *eq_words,
                  uint64_t cap, uint32_t *slot, cudaStream_t s) {
     if (n_keys > 0) cudaMemsetAsync(table, 0xFF, cap * sizeof(uint64_t), s);
     if (n == 0) return;
+    HB_LAUNCHED(1);
     k_group_insert<<<nblk(n), BT, 0, s>>>(rec, W, n, make_keywords(eq_words, n_keys), table, cap - 1, slot);
 }
 
 void group_probe(const uint32_t *rec_probe, int64_t n, const uint32_t *rec_owner, int W, const int32_t *eq_words,
                  int n_keys, const uint64_t *table, uint64_t cap, uint32_t *slot, cudaStream_t s) {
     if (n == 0) return;
+    HB_LAUNCHED(1);
     k_group_probe<<<nblk(n), BT, 0, s>>>(rec_probe, n, rec_owner, W, make_keywords(eq_words, n_keys), table,
                                          cap - 1, slot);
 }
 
 void count_slots(const uint32_t *slot, int64_t n, uint32_t *count, cudaStream_t s) {
     if (n == 0) return;
+    HB_LAUNCHED(1);
     k_count_slots<<<nblk(n), BT, 0, s>>>(slot, n, count);
 }
 
 void scatter_slots(const uint32_t *slot, int64_t n, const uint32_t *start, uint32_t *cursor, uint32_t *members,
                    cudaStream_t s) {
     if (n == 0) return;
+    HB_LAUNCHED(1);
     k_scatter_slots<<<nblk(n), BT, 0, s>>>(slot, n, start, cursor, members);
 }
 
@@ -218,12 +222,14 @@ void emit_blocks(const uint32_t *count_r, const uint32_t *start_r, const uint32_
                  uint64_t cap, uint32_t md, int self_join, uint32_t member_base_r, uint32_t member_base_s, int tile,
                  BlockDesc *blocks, uint64_t *tiles, uint32_t *n_blocks, uint32_t block_cap, unsigned int *overflow,
                  cudaStream_t s) {
+    HB_LAUNCHED(1);
     k_emit_blocks<<<nblk((int64_t)cap), BT, 0, s>>>(count_r, start_r, count_s, start_s, cap, md, self_join,
                                                     member_base_r, member_base_s, tile, blocks, tiles, n_blocks,
                                                     block_cap, overflow);
 }
 
 void clamp_blocks(uint32_t *n_blocks, uint32_t block_cap, cudaStream_t s) {
+    HB_LAUNCHED(1);
     k_clamp_blocks<<<1, 1, 0, s>>>(n_blocks, block_cap);
 }
 

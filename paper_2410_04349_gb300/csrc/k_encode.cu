@@ -340,6 +340,7 @@ inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t
 void dict_build(const DevCol &c, int prefix, uint64_t *table, uint64_t cap, uint32_t *codes, cudaStream_t s) {
     cudaMemsetAsync(table, 0xFF, cap * sizeof(uint64_t), s);
     if (c.n == 0) return;
+    HB_LAUNCHED(1);
     k_dict_insert<<<blocks_for(c.n, ENC_THREADS), ENC_THREADS, 0, s>>>(make_view(c, prefix), c.n, table, cap - 1,
                                                                       codes);
 }
@@ -347,22 +348,26 @@ void dict_build(const DevCol &c, int prefix, uint64_t *table, uint64_t cap, uint
 void dict_probe(const DevCol &probe, int prefix, const DevCol &owner, int owner_prefix, const uint64_t *table,
                 uint64_t cap, uint32_t *codes, cudaStream_t s) {
     if (probe.n == 0) return;
+    HB_LAUNCHED(1);
     k_dict_probe<<<blocks_for(probe.n, ENC_THREADS), ENC_THREADS, 0, s>>>(
         make_view(probe, prefix), probe.n, make_view(owner, owner_prefix), table, cap - 1, codes);
 }
 
 void code_feature(const uint32_t *codes, int64_t n, uint32_t *rec, int W, int feat, cudaStream_t s) {
     if (n == 0) return;
+    HB_LAUNCHED(1);
     k_code_feature<<<blocks_for(n, ENC_THREADS), ENC_THREADS, 0, s>>>(codes, n, rec, W, feat);
 }
 
 void ed_features(const DevCol &c, uint32_t *rec, int W, int feat, cudaStream_t s) {
     if (c.n == 0) return;
+    HB_LAUNCHED(1);
     k_ed_features<<<blocks_for(c.n, ENC_THREADS), ENC_THREADS, 0, s>>>(c.bytes, c.off, c.valid, c.n, rec, W, feat);
 }
 
 void abs_feature(const DevCol &c, uint32_t *rec, int W, int feat, cudaStream_t s) {
     if (c.n == 0) return;
+    HB_LAUNCHED(1);
     k_abs_feature<<<blocks_for(c.n, ENC_THREADS), ENC_THREADS, 0, s>>>(static_cast<const float *>(c.vals), c.valid,
                                                                       c.n, rec, W, feat);
 }
@@ -382,10 +387,13 @@ void jac_features_impl(const DevCol &c, int q, uint32_t *rec, int W, int feat, u
     unsigned int *n_long = reinterpret_cast<unsigned int *>(long_list + (n + 1));
     void *stmp = reinterpret_cast<void *>((reinterpret_cast<uintptr_t>(n_long + 4) + 255) & ~uintptr_t(255));
     cudaMemsetAsync(n_long, 0, sizeof(unsigned int), s);
+    HB_LAUNCHED(1);
     k_gram_counts<<<blocks_for(n, ENC_THREADS), ENC_THREADS, 0, s>>>(c.off, c.valid, n, q, cnt);
     scan_exclusive_u32(cnt, gstart, n, nullptr, stmp, 0, s);
+    HB_LAUNCHED(1);
     k_grams_short<<<blocks_for(n, QG_THREADS), QG_THREADS, 0, s>>>(c.bytes, c.off, c.valid, n, q, gstart, grams, rec,
                                                                   W, feat, long_list, n_long);
+    HB_LAUNCHED(1);
     k_grams_long<<<(unsigned)(n_sm * 4), 256, 0, s>>>(c.bytes, c.off, q, gstart, grams, rec, W, feat, long_list,
                                                       n_long, too_long);
 }

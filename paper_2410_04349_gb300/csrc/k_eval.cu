@@ -216,10 +216,15 @@ __device__ __forceinline__ bool eval_op(const EvalParams &P, int k, const uint32
 template <bool LOG>
 __device__ __forceinline__ bool run_program(const EvalParams &P, uint64_t alive, const uint32_t *a,
                                             const uint32_t *b, LogAcc &lg) {
-    if (alive & P.eqonly) return true;
+    // profile mode (logging only): evaluate every predicate the initially alive
+    // MDs hold, without early exit; the verdict is unchanged
+    const bool prof = LOG && P.profile;
+    const uint64_t alive0 = alive;
+    bool hit = (alive & P.eqonly) != 0;
+    if (hit && !prof) return true;
     for (int k = 0; k < P.n_ops; k++) {
         const uint64_t need = P.ops[k].need;
-        if (alive & need) {
+        if ((prof ? alive0 : alive) & need) {
             long long c0 = 0;
             if (LOG) c0 = clock64();
             bool r = eval_op<LOG>(P, k, a, b, lg);
@@ -230,10 +235,13 @@ __device__ __forceinline__ bool run_program(const EvalParams &P, uint64_t alive,
             }
             if (!r) alive &= ~need;
         }
-        if (alive & P.ops[k].cp) return true;
-        if (!alive) return false;
+        if (alive & P.ops[k].cp) {
+            if (!prof) return true;
+            hit = true;
+        }
+        if (!alive && !prof) return false;
     }
-    return false;
+    return hit;
 }
 
 __device__ __forceinline__ void decode_tile(uint64_t q, uint32_t nr, uint32_t ns, int self_join, int T, uint32_t &ti,
@@ -278,7 +286,7 @@ __global__ void __launch_bounds__(EV_THREADS) k_eval(const __grid_constant__ Eva
     const uint32_t nb = *P.n_blocks;
     const uint64_t total = P.tile_prefix[nb];
     const unsigned lt = (1u << lane) - 1u;
-    unsigned long long cand = 0;
+    unsigned long long cand = 0, exam = 0;
 
     for (;;) {
         unsigned long long t0 = 0;
@@ -357,6 +365,7 @@ __global__ void __launch_bounds__(EV_THREADS) k_eval(const __grid_constant__ Eva
                     }
                     const bool own = v && alive != 0 && (uint32_t)(__ffsll((long long)alive) - 1) == B.md;
                     cand += __popc(__ballot_sync(0xffffffffu, own));
+                    exam += __popc(__ballot_sync(0xffffffffu, v));
                     bool hit = false;
                     if (own) hit = run_program<LOG>(P, alive, ar, bc, lg);
                     const unsigned hm = __ballot_sync(0xffffffffu, hit);
@@ -390,6 +399,7 @@ __global__ void __launch_bounds__(EV_THREADS) k_eval(const __grid_constant__ Eva
         }
     }
     if (lane == 0 && cand) atomicAdd(P.cand_count, cand);
+    if (lane == 0 && exam) atomicAdd(P.exam_count, exam);
     if (LOG) {
         __syncthreads();
         for (int i = threadIdx.x; i < P.n_ops * LOG_FIELDS; i += blockDim.x)
@@ -430,9 +440,11 @@ int eval_blocks_per_sm(int tile, int logging, size_t smem) {
 
 cudaError_t launch_eval(const EvalParams &p, int grid, size_t smem, int logging, cudaStream_t s) {
     if (p.tile == 64) {
+        HB_LAUNCHED(1);
         if (logging) k_eval<2, true><<<grid, EV_THREADS, smem, s>>>(p);
         else k_eval<2, false><<<grid, EV_THREADS, smem, s>>>(p);
     } else {
+        HB_LAUNCHED(1);
         if (logging) k_eval<1, true><<<grid, EV_THREADS, smem, s>>>(p);
         else k_eval<1, false><<<grid, EV_THREADS, smem, s>>>(p);
     }
@@ -441,6 +453,7 @@ cudaError_t launch_eval(const EvalParams &p, int grid, size_t smem, int logging,
 
 void pack_pairs(const uint64_t *keys, int64_t n, int key_bits_s, hb_pair *out, cudaStream_t s) {
     if (n <= 0) return;
+    HB_LAUNCHED(1);
     k_pack_pairs<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(keys, n, key_bits_s, out);
 }
 

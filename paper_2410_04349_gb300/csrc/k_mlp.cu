@@ -153,6 +153,7 @@ size_t mlp_work_floats(int n) { return (size_t)n * (2 * D1 + 2 * D2 + 2) + 64; }
 cudaError_t mlp_forward(const float *X, int n, const float *params, float *y, int bf16, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     const unsigned g = (unsigned)((n + ROWS - 1) / ROWS);
+    HB_LAUNCHED(1);
     if (bf16) k_mlp_fwd<true><<<g, 64, 0, s>>>(X, n, params, y, nullptr, nullptr);
     else k_mlp_fwd<false><<<g, 64, 0, s>>>(X, n, params, y, nullptr, nullptr);
     return cudaGetLastError();
@@ -170,9 +171,12 @@ cudaError_t mlp_backward(const float *X, const float *t, int n, const float *par
     const unsigned g = (unsigned)((n + ROWS - 1) / ROWS);
     // z2 is kept; its copy in the backward buffer receives dz2
     float *dz2 = dy + n;   // n * D2
+    HB_LAUNCHED(1);
     k_mlp_fwd<false><<<g, 64, 0, s>>>(X, n, params, y, z1, z2);
     cudaMemcpyAsync(dz2, z2, sizeof(float) * (size_t)n * D2, cudaMemcpyDeviceToDevice, s);
+    HB_LAUNCHED(1);
     k_mlp_bwd_rows<<<g, 64, 0, s>>>(y, t, n, params, z1, dz2, dz1, dy);
+    HB_LAUNCHED(1);
     k_mlp_grad<<<(N_PARAMS + 127) / 128, 128, 0, s>>>(X, n, z1, z2, dz1, dz2, dy, grad);
     return cudaGetLastError();
 }
@@ -181,6 +185,7 @@ cudaError_t adam_step(float *params, const float *grad, float *m, float *v, int 
                       float b2, float eps, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     const float c1 = 1.f - powf(b1, (float)step), c2 = 1.f - powf(b2, (float)step);
+    HB_LAUNCHED(1);
     k_adam<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(params, grad, m, v, n, lr, b1, b2, eps, c1, c2);
     return cudaGetLastError();
 }

@@ -104,13 +104,16 @@ template <typename T>
 void scan_impl(const T *in, T *out, int64_t n, const uint32_t *n_dev, T *tmp, cudaStream_t s) {
     int64_t tiles = (n + 1 + SCAN_TILE - 1) / SCAN_TILE;
     if (tiles <= 1) {
+        HB_LAUNCHED(1);
         k_scan_down<T><<<1, SCAN_THREADS, 0, s>>>(in, out, n, n_dev, nullptr);
         return;
     }
     T *partial = tmp;
     T *partial_scan = tmp;   // scanned in place (exclusive), size tiles + 1
+    HB_LAUNCHED(1);
     k_scan_reduce<T><<<(unsigned)tiles, SCAN_THREADS, 0, s>>>(in, n, n_dev, partial);
     scan_impl<T>(partial, partial_scan, tiles, nullptr, tmp + tiles + 1, s);
+    HB_LAUNCHED(1);
     k_scan_down<T><<<(unsigned)tiles, SCAN_THREADS, 0, s>>>(in, out, n, n_dev, partial_scan);
 }
 
@@ -249,8 +252,10 @@ void radix_sort_u64(uint64_t *keys, uint64_t *alt, int64_t n_max, const unsigned
     stmp = reinterpret_cast<void *>((reinterpret_cast<uintptr_t>(stmp) + 255) & ~uintptr_t(255));
     uint64_t *src = keys, *dst = alt;
     for (int shift = 0; shift < bits; shift += 8) {
+        HB_LAUNCHED(1);
         k_radix_hist<<<(unsigned)ntiles, RS_THREADS, 0, s>>>(src, n_max, n_dev, shift, hist, ntiles);
         scan_impl<uint32_t>(hist, offs, h, nullptr, static_cast<uint32_t *>(stmp), s);
+        HB_LAUNCHED(1);
         k_radix_scatter<<<(unsigned)ntiles, RS_THREADS, 0, s>>>(src, dst, n_max, n_dev, shift, offs, ntiles);
         uint64_t *x = src;
         src = dst;

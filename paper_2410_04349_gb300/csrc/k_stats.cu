@@ -93,6 +93,7 @@ void lsh_hist(const SampleSpec *specs_dev, int n_preds, int64_t n_rows, int n_sa
               uint32_t *hist, uint32_t *present, uint32_t *lens, uint32_t *grams, int n_keep, cudaStream_t s) {
     if (n_preds == 0 || n_rows == 0) return;
     dim3 grid((unsigned)((n_samples + 255) / 256), (unsigned)n_preds);
+    HB_LAUNCHED(1);
     k_lsh_hist<<<grid, 256, 0, s>>>(specs_dev, n_preds, n_rows, n_samples, k_buckets, hist, present, lens, grams,
                                     n_keep);
 }

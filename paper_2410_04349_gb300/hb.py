@@ -72,7 +72,8 @@ class hb_stats(ctypes.Structure):
                 ("ms_h2d", ctypes.c_double), ("ms_encode", ctypes.c_double), ("ms_plan", ctypes.c_double),
                 ("ms_block_build", ctypes.c_double), ("ms_eval", ctypes.c_double), ("ms_sort", ctypes.c_double),
                 ("ms_d2h", ctypes.c_double), ("ms_total", ctypes.c_double), ("device_bytes", ctypes.c_int64),
-                ("tile", ctypes.c_int32), ("n_mds", ctypes.c_int32)]
+                ("tile", ctypes.c_int32), ("n_mds", ctypes.c_int32), ("kernel_launches", ctypes.c_int64),
+                ("examined_pairs", ctypes.c_int64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -81,7 +82,13 @@ class hb_stats(ctypes.Structure):
 class hb_pred_log(ctypes.Structure):
     _fields_ = [("features", ctypes.c_float * FEATURES), ("log_cost", ctypes.c_float),
                 ("logit_pass", ctypes.c_float), ("evaluated", ctypes.c_int64), ("passed", ctypes.c_int64),
-                ("pred", ctypes.c_int32), ("kind", ctypes.c_int32)]
+                ("cycles", ctypes.c_int64), ("stage1", ctypes.c_int64), ("stage2", ctypes.c_int64),
+                ("core", ctypes.c_int64), ("pred", ctypes.c_int32), ("kind", ctypes.c_int32)]
+
+    def as_dict(self):
+        d = {f: getattr(self, f) for f, _ in self._fields_ if f != "features"}
+        d["features"] = list(self.features)
+        return d
 
 
 EXPORTS = ["hb_create", "hb_destroy", "hb_last_error", "hb_version", "hb_load_table", "hb_add_md", "hb_clear_mds",
@@ -110,7 +117,7 @@ def lib():
         "hb_block_stream": (st, [P, i64, i32, P, P, P]), "hb_block_batch": (st, [P, i32, P, P, P]),
         "hb_free_pairs": (None, [P]), "hb_get_stats": (st, [P, P]),
         "hb_plan_order": (st, [i32, P, P, i32, P, P, P, P, P, P, P]),
-        "hb_log_predicates": (st, [P, P, i32, P]), "hb_predicate_features": (st, [P, P, i32, P]),
+        "hb_log_predicates": (st, [P, i32, P, i32, P]), "hb_predicate_features": (st, [P, P, i32, P]),
         "hb_train_cost_model": (st, [P, i32, P, P, P, i32, ctypes.c_float, ctypes.c_uint64, P]),
         "hb_get_cost_model": (st, [P, P]), "hb_set_cost_model": (st, [P, P]),
         "hb_mlp_forward": (st, [P, i32, P, P, P]), "hb_mlp_forward_bf16": (st, [P, i32, P, P, P]),
@@ -285,11 +292,13 @@ class Context:
         return s.as_dict()
 
     # ---- learned cost model
-    def log_predicates(self, cap=MAX_PREDS):
+    def log_predicates(self, profile=False, cap=MAX_PREDS):
+        """Per-predicate instrumentation records (dicts) of one evaluation."""
         arr = (hb_pred_log * cap)()
         n = ctypes.c_int32()
-        _check(lib().hb_log_predicates(self._h, arr, cap, ctypes.byref(n)), "hb_log_predicates")
-        return [arr[i] for i in range(n.value)]
+        _check(lib().hb_log_predicates(self._h, 1 if profile else 0, arr, cap, ctypes.byref(n)),
+               "hb_log_predicates")
+        return [arr[i].as_dict() for i in range(n.value)]
 
     def predicate_features(self, cap=MAX_PREDS):
         out = np.zeros((cap, FEATURES), np.float32)
