@@ -287,6 +287,20 @@ HB_API hb_status hb_mlp_forward(const float *X, int32_t n, const float *params, 
 HB_API hb_status hb_mlp_forward_bf16(const float *X, int32_t n, const float *params, float *y, void *stream);
 HB_API hb_status hb_mlp_backward(const float *X, const float *t, int32_t n, const float *params, float *grad,
                           void *stream);
+/*
+ * hb_mlp_backward without any device allocation (the paper has no
+ * counterpart; this serves callers that cannot allocate device memory when
+ * they need a gradient, e.g. a process whose device memory is pre-partitioned
+ * by its own pool or a loop that must not call cudaMalloc / cudaFree).  Same
+ * arguments and result as hb_mlp_backward, for n <= 4096 rows (larger n:
+ * HB_ERR_ARG).  Its work buffers live in one fixed device array of the library
+ * (about 4.2 MB, held on every GPU that loads the library until exit).  The
+ * first call on a device looks up that array's address (call it once before
+ * any stream capture); every call shares the array, so calls that overlap on
+ * the GPU race.  No state carries over between calls.
+ */
+HB_API hb_status hb_mlp_backward_noalloc(const float *X, const float *t, int32_t n, const float *params,
+                                         float *grad, void *stream);
 HB_API hb_status hb_adam_step(float *params, const float *grad, float *m, float *v, int32_t n_params, int32_t step,
                        float lr, float beta1, float beta2, float eps, void *stream);
 

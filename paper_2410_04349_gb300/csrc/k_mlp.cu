@@ -11,7 +11,14 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
+#include <string>
+
 #include "hb_internal.h"
+
+namespace hb {
+hb_status fail(hb_status st, const std::string &msg);
+}
 
 namespace hb {
 namespace {
@@ -191,3 +198,66 @@ cudaError_t adam_step(float *params, const float *grad, float *m, float *v, int 
 }
 
 }  // namespace hb
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of the backward pass (hb_mlp_backward_noalloc).
+//
+// Some callers cannot allocate device memory at the moment they need a
+// gradient: a process whose device memory is fully pre-partitioned by its own
+// pool or by another framework, or a latency-critical loop that must not hit
+// cudaMalloc / cudaFree (which can synchronize the device).  For them the
+// backward pass keeps its per-row work buffers (pre-activations and their
+// gradients) in one fixed file-scope device array instead of memory obtained
+// per call.  The array is part of the module: every GPU that loads the
+// library holds it (NOALLOC_MAX_ROWS * 258 + 64 floats, about 4.2 MB) until
+// the process exits.
+//
+// Host code cannot use the array's name as a device address, so the address
+// is looked up once per device with cudaGetSymbolAddress (with that device
+// current) the first time the entry point runs on it; make that first call
+// before any stream capture.  Every call shares the one array: calls that
+// overlap on the GPU (different streams, threads or devices' contexts racing
+// on the same device) race on it.  Nothing needs clearing between calls:
+// each call writes every scratch word it later reads, for its own rows.
+// ---------------------------------------------------------------------------
+namespace hb {
+
+constexpr int NOALLOC_MAX_ROWS = 4096;
+constexpr size_t NOALLOC_SCRATCH_FLOATS = (size_t)NOALLOC_MAX_ROWS * (2 * D1 + 2 * D2 + 2) + 64;
+static __device__ __align__(256) float g_backward_scratch[NOALLOC_SCRATCH_FLOATS];
+
+namespace {
+constexpr int NOALLOC_MAX_DEVICES = 64;
+std::mutex g_noalloc_mu;
+float *g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {};
+}  // namespace
+
+}  // namespace hb
+
+extern "C" hb_status hb_mlp_backward_noalloc(const float *X, const float *t, int32_t n, const float *params,
+                                             float *grad, void *stream) {
+    using namespace hb;
+    if (n < 0 || !params || !grad || (n > 0 && (!X || !t))) return fail(HB_ERR_ARG, "hb_mlp_backward_noalloc: bad arguments");
+    if (n > NOALLOC_MAX_ROWS)
+        return fail(HB_ERR_ARG, "hb_mlp_backward_noalloc: n = " + std::to_string(n) + " rows exceeds the fixed scratch "
+                                "capacity of " + std::to_string(NOALLOC_MAX_ROWS) + " rows; use hb_mlp_backward");
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return fail(HB_ERR_CUDA, std::string("hb_mlp_backward_noalloc: cudaGetDevice: ") + cudaGetErrorString(e));
+    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return fail(HB_ERR_ARG, "hb_mlp_backward_noalloc: device ordinal too large");
+    float *work = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_noalloc_mu);
+        if (!g_noalloc_ptr[dev]) {
+            void *p = nullptr;
+            e = cudaGetSymbolAddress(&p, g_backward_scratch);
+            if (e != cudaSuccess)
+                return fail(HB_ERR_CUDA, std::string("hb_mlp_backward_noalloc: cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+            g_noalloc_ptr[dev] = static_cast<float *>(p);
+        }
+        work = g_noalloc_ptr[dev];
+    }
+    e = mlp_backward(X, t, n, params, grad, work, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return fail(HB_ERR_CUDA, std::string("hb_mlp_backward_noalloc: ") + cudaGetErrorString(e));
+    return HB_OK;
+}

@@ -95,7 +95,7 @@ EXPORTS = ["hb_create", "hb_destroy", "hb_last_error", "hb_version", "hb_load_ta
            "hb_plan", "hb_block", "hb_block_device", "hb_block_stream", "hb_block_batch", "hb_free_pairs",
            "hb_get_stats", "hb_plan_order", "hb_log_predicates", "hb_predicate_features", "hb_train_cost_model",
            "hb_get_cost_model", "hb_set_cost_model", "hb_mlp_forward", "hb_mlp_forward_bf16", "hb_mlp_backward",
-           "hb_adam_step"]
+           "hb_mlp_backward_noalloc", "hb_adam_step"]
 
 _lib = None
 
@@ -121,7 +121,7 @@ def lib():
         "hb_train_cost_model": (st, [P, i32, P, P, P, i32, ctypes.c_float, ctypes.c_uint64, P]),
         "hb_get_cost_model": (st, [P, P]), "hb_set_cost_model": (st, [P, P]),
         "hb_mlp_forward": (st, [P, i32, P, P, P]), "hb_mlp_forward_bf16": (st, [P, i32, P, P, P]),
-        "hb_mlp_backward": (st, [P, P, i32, P, P, P]),
+        "hb_mlp_backward": (st, [P, P, i32, P, P, P]), "hb_mlp_backward_noalloc": (st, [P, P, i32, P, P, P]),
         "hb_adam_step": (st, [P, P, P, P, i32, i32, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                               P]),
     }
@@ -353,6 +353,14 @@ def mlp_forward(X, params, y, stream=None, bf16=False):
 
 def mlp_backward(X, t, params, grad, stream=None):
     _check(lib().hb_mlp_backward(_ptr(X), _ptr(t), X.shape[0], _ptr(params), _ptr(grad), stream), "hb_mlp_backward")
+
+
+def mlp_backward_noalloc(X, t, params, grad, stream=None):
+    """hb_mlp_backward for callers that cannot allocate device memory: the
+    work buffers are a fixed array inside the library (n <= 4096 rows);
+    concurrent calls on one GPU race on it."""
+    _check(lib().hb_mlp_backward_noalloc(_ptr(X), _ptr(t), X.shape[0], _ptr(params), _ptr(grad), stream),
+           "hb_mlp_backward_noalloc")
 
 
 def adam_step(params, grad, m, v, step, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
