@@ -69,6 +69,8 @@ void free_buf(hb_ctx *c, Buf &b) {
 static void free_side_encoding(hb_ctx *c, SideData &s) {
     if (s.rec) cudaFreeAsync(s.rec, c->stream);
     s.rec = nullptr;
+    if (s.hot) cudaFreeAsync(s.hot, c->stream);
+    s.hot = nullptr;
     for (auto g : s.grams)
         if (g) cudaFreeAsync(g, c->stream);
     s.grams.clear();
@@ -442,6 +444,8 @@ static hb_status build_layout(hb_ctx *c, bool job_key) {
         pi.group = g;
     }
     c->W = (word + 3) & ~3;
+    c->HW = (c->n_eq_total + (int)c->groups.size() + 3) & ~3;
+    if (c->HW > 64) return fail(HB_ERR_ARG, "too many distinct predicate columns");
     if (c->W > 252) return fail(HB_ERR_ARG, "record too wide: too many distinct predicate columns");
     // equality sets and the MDs that can own pairs
     const int n_md = (int)c->md_preds.size();
@@ -608,6 +612,7 @@ static hb_status finish_plan(hb_ctx *c, int mode, const std::vector<double> &sp,
         Op op{};
         op.kind = (uint8_t)G.kind;
         op.feat = (uint8_t)G.word;
+        op.hot = (uint8_t)(c->n_eq_total + pi.group);
         op.k = (uint8_t)(pi.p.kind == HB_P_ED_LE ? pi.p.k : 0);
         op.num = pi.p.num;
         op.den = pi.p.den;
@@ -762,6 +767,15 @@ hb_status encode_side(hb_ctx *c, int side) {
     free_buf(c, flag);
     HB_CUDA(cudaGetLastError());
     if (too_long) return fail(HB_ERR_ARG, "a string compared by q-gram Jaccard has more than 8192 grams");
+    {
+        std::vector<int32_t> map(c->HW, -1);
+        for (int e = 0; e < c->n_eq_total; e++) map[e] = e;
+        for (size_t g = 0; g < c->groups.size(); g++) map[c->n_eq_total + g] = c->groups[g].word;
+        HB_TRY(dmalloc(c, &p, sizeof(uint32_t) * (size_t)c->HW * (size_t)(n > 0 ? n : 1) + 64));
+        S.hot = static_cast<uint32_t *>(p);
+        hot_pack(S.rec, W, n, S.hot, c->HW, map.data(), c->stream);
+        HB_CUDA(cudaGetLastError());
+    }
     S.encoded = true;
     return HB_OK;
 }
@@ -851,6 +865,13 @@ static EvalParams make_params(hb_ctx *c, const uint32_t *rec_r, const uint32_t *
     P.n_ops = (int)c->ops.size();
     P.n_eq = c->n_eq_total;
     P.W = c->W;
+    P.HW = c->HW;
+    P.hot_r = c->side[0].hot;
+    P.hot_s = self ? c->side[0].hot : c->side[side_s].hot;
+    for (int m = 0; m < MAX_MD; m++) P.first_op[m] = -1;
+    for (int m = 0; m < (int)c->md_preds.size(); m++)
+        for (int k = (int)c->ops.size() - 1; k >= 0; k--)
+            if (c->ops[k].need & (1ull << m)) P.first_op[m] = (int8_t)k;
     P.self_join = self ? 1 : 0;
     P.n_md = (int)c->md_preds.size();
     P.use_lut = c->lut.empty() ? 0 : 1;
@@ -916,7 +937,7 @@ hb_status block_eval_sort(hb_ctx *c, const uint32_t *rec_r, int64_t n_r, const u
     if (tm) tm->mark();
     if (c->out_cap == 0) c->out_cap = c->opt.out_capacity > 0 ? c->opt.out_capacity : std::max<int64_t>(1 << 20, n_r);
     HB_TRY(grow(c, c->w_out, sizeof(uint64_t) * (size_t)c->out_cap));
-    const size_t smem = eval_smem_bytes(c->W, c->n_eq_total, c->lut.empty() ? 0 : 1, c->tile);
+    const size_t smem = eval_smem_bytes(c->HW, c->n_eq_total, c->lut.empty() ? 0 : 1, c->tile);
     int bps = eval_blocks_per_sm(c->tile, logging, smem);
     if (bps < 1) return fail(HB_ERR_ARG, "record too wide for the evaluation kernel's shared memory");
     const int grid = bps * c->n_sm;

@@ -64,6 +64,7 @@ struct SideData {
     std::vector<void *> allocs;
     // encoded state
     uint32_t *rec = nullptr;
+    uint32_t *hot = nullptr;   // per tuple: equality codes + one filter word per feature group
     std::vector<uint32_t *> grams;   // per feature group (JAC only)
     bool encoded = false;
 };
@@ -95,6 +96,7 @@ struct hb_ctx {
     std::vector<EqKey> eqkeys;
     std::vector<FeatGroup> groups;
     int W = 4;
+    int HW = 4;
     int n_eq_total = 0;            // eqkeys + job key
     std::vector<uint16_t> eqset;
     std::vector<int> active;       // MDs whose blocks can own pairs

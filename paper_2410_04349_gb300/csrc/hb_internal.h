@@ -43,7 +43,7 @@ struct Op {
     uint8_t kind;
     uint8_t feat;       // first record word of this predicate's feature group
     uint8_t k;          // ED threshold
-    uint8_t pad;
+    uint8_t hot;        // hot-record word holding this predicate's filter operand
     uint32_t num, den;  // Jaccard threshold
     float delta;        // |a-b| threshold
     uint32_t pad2;
@@ -76,6 +76,10 @@ struct EvalParams {
     int32_t key_bits_s;     // packed output key = tid1 << key_bits_s | tid2
     uint64_t eqonly;        // MDs without any non-equality predicate
     uint16_t eqset[MAX_MD]; // equality keys of each MD (bit e = key e)
+    int8_t first_op[MAX_MD];// first program op of each MD (-1: none)
+    int32_t HW;             // hot-record words (multiple of 4): keys, then one filter word per feature group
+    const uint32_t *hot_r;
+    const uint32_t *hot_s;
     Op ops[MAX_OPS];
     const void *ptr_r[MAX_OPS];   // ED: string bytes of R; JAC: gram array of R
     const void *ptr_s[MAX_OPS];
@@ -117,6 +121,8 @@ void dict_build(const DevCol &c, int prefix, uint64_t *table, uint64_t cap, uint
 void dict_probe(const DevCol &probe, int prefix, const DevCol &owner, int owner_prefix, const uint64_t *table,
                 uint64_t cap, uint32_t *codes, cudaStream_t s);
 void code_feature(const uint32_t *codes, int64_t n, uint32_t *rec, int W, int feat, cudaStream_t s);
+// hot[i][h] = rec[i][map[h]] (0 where map[h] < 0); HW <= 64
+void hot_pack(const uint32_t *rec, int W, int64_t n, uint32_t *hot, int HW, const int32_t *map, cudaStream_t s);
 void ed_features(const DevCol &c, uint32_t *rec, int W, int feat, cudaStream_t s);
 void abs_feature(const DevCol &c, uint32_t *rec, int W, int feat, cudaStream_t s);
 size_t jac_scratch_bytes(int64_t n);

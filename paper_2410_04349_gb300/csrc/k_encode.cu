@@ -333,6 +333,16 @@ __global__ void __launch_bounds__(256) k_grams_long(const uint8_t *bytes, const 
     }
 }
 
+struct HotMap {
+    int32_t w[64];
+};
+
+__global__ void k_hot_pack(const uint32_t *rec, int W, int64_t n, uint32_t *hot, int HW, HotMap map) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (int h = 0; h < HW; h++) hot[i * HW + h] = map.w[h] >= 0 ? rec[i * W + map.w[h]] : 0u;
+}
+
 inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t > 0 ? (n + t - 1) / t : 1); }
 
 }  // namespace
@@ -351,6 +361,14 @@ void dict_probe(const DevCol &probe, int prefix, const DevCol &owner, int owner_
     HB_LAUNCHED(1);
     k_dict_probe<<<blocks_for(probe.n, ENC_THREADS), ENC_THREADS, 0, s>>>(
         make_view(probe, prefix), probe.n, make_view(owner, owner_prefix), table, cap - 1, codes);
+}
+
+void hot_pack(const uint32_t *rec, int W, int64_t n, uint32_t *hot, int HW, const int32_t *map, cudaStream_t s) {
+    if (n == 0) return;
+    HotMap m;
+    for (int h = 0; h < 64; h++) m.w[h] = h < HW ? map[h] : -1;
+    HB_LAUNCHED(1);
+    k_hot_pack<<<blocks_for(n, ENC_THREADS), ENC_THREADS, 0, s>>>(rec, W, n, hot, HW, m);
 }
 
 void code_feature(const uint32_t *codes, int64_t n, uint32_t *rec, int W, int feat, cudaStream_t s) {

@@ -1,21 +1,27 @@
 // Pair evaluation: the hot loop of blocking.
 //
-// Work items are tiles of a block's pair space (T x T tuples, upper triangle
-// for a self-join).  A persistent grid of warps claims tiles from one atomic
-// counter (task stealing in the form of a shared queue, Section 5.2).  A warp
-// stages the packed records of its T row tuples and T column tuples in shared
-// memory; each lane owns T/32 rows and walks the columns.  For every pair:
+// Work items are tiles of a block's pair space (T x T tuples, the upper
+// triangle for a self-join).  A persistent grid of warps claims tiles from one
+// atomic counter (task stealing in the form of a shared queue, Section 5.2).
+// Each warp works on one tile at a time in two phases:
 //
-//   1. equality keys: bit e of E is set when the two tuples carry the same
-//      (present) code of key e; the MDs whose equality keys are all in E are
-//      alive (they cannot be excluded by an equality predicate);
-//   2. owner check: the pair is handled only in the block of the lowest alive
-//      MD, so every pair is evaluated once however many blocks contain it;
-//   3. the sequential execution path of Section 5.1: non-equality predicates
-//      in plan order, each evaluated once per pair (its result applies to
-//      every MD holding it: "Reusing computation"), skipped when no alive MD
-//      needs it, with a checkpoint after the last predicate of each MD;
-//   4. witnessed pairs are compacted with a warp ballot and one atomic.
+//  phase 1 (every pair, branch-light): the warp stages the tile's "hot"
+//    records (equality codes and one filter operand per predicate column) in
+//    shared memory; lane = row, loop over columns.  For every pair:
+//      - equality keys: bit e of E is set when both tuples hold the same
+//        present code of key e; the MDs whose keys are all in E are alive;
+//      - owner check: the pair is handled only in the block of the lowest
+//        alive MD, so each pair is evaluated once however many blocks hold it;
+//      - when the owner is the only alive MD, the cheap necessary condition of
+//        its first predicate (length / size filter, or the |a-b| test itself)
+//        rejects most pairs at once;
+//    the remaining pairs are compacted into a per-warp survivor list (ballot).
+//  phase 2 (survivors, 32 at a time, all lanes busy): the sequential execution
+//    path of Section 5.1 on the full records: non-equality predicates in plan
+//    order, each evaluated once per pair and its result applied to every MD
+//    holding it ("Reusing computation"), skipped when no alive MD needs it,
+//    with a checkpoint after each MD's last predicate; witnessed pairs are
+//    compacted with a warp ballot and one atomic.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -24,13 +30,21 @@
 namespace hb {
 namespace {
 
-constexpr int EV_THREADS = 128;
+constexpr int EV_THREADS = 256;
 constexpr int EV_WARPS = EV_THREADS / 32;
 constexpr int LOG_FIELDS = 6;   // evaluated, passed, cycles, stage-1 passes, stage-2 passes, core work
 
 struct LogAcc {
     unsigned long long *s;   // shared [MAX_OPS * LOG_FIELDS] or null
 };
+
+// warp-aggregated add of per-lane values to one shared counter (the index is
+// uniform over the active lanes)
+__device__ __forceinline__ void log_add(LogAcc &lg, int idx, unsigned v) {
+    const unsigned m = __activemask();
+    const unsigned s = __reduce_add_sync(m, v);
+    if ((threadIdx.x & 31) == __ffs(m) - 1) atomicAdd(&lg.s[idx], (unsigned long long)s);
+}
 
 // ---- edit distance <= K: Ukkonen-banded Wagner-Fischer, band of 2K+1 cells ----
 // D[i][j] is kept for |i - j| <= K only (other cells exceed K); values are
@@ -144,62 +158,63 @@ __device__ __forceinline__ bool ed_le(const uint8_t *a, int la, const uint8_t *b
     }
 }
 
+
 template <bool LOG>
-__device__ __forceinline__ bool eval_op(const EvalParams &P, int k, const uint32_t *a, const uint32_t *b,
-                                        LogAcc &lg) {
+__device__ __forceinline__ bool eval_op(const EvalParams &P, int k, const uint32_t *__restrict__ a,
+                                        const uint32_t *__restrict__ b, LogAcc &lg) {
     const Op &op = P.ops[k];
     const int f = op.feat;
     if (op.kind == OP_ABS) {
-        const float x = __uint_as_float(a[f]), y = __uint_as_float(b[f]);
+        const float x = __uint_as_float(__ldg(a + f)), y = __uint_as_float(__ldg(b + f));
         return fabsf(x - y) <= op.delta;
     }
     if (op.kind == OP_ED) {
-        const uint32_t la = a[f], lb = b[f];
+        const uint32_t la = __ldg(a + f), lb = __ldg(b + f);
         if (la == NULL_LEN || lb == NULL_LEN) return false;
         const uint32_t d = la > lb ? la - lb : lb - la;
         if (d > op.k) return false;
-        if (LOG) atomicAdd(&lg.s[k * LOG_FIELDS + 3], 1ull);
+        if (LOG) log_add(lg, k * LOG_FIELDS + 3, 1u);
         // bag distance over 16 character bins is a lower bound of the edit distance
         unsigned p1 = 0, p2 = 0;
 #pragma unroll
         for (int w = 0; w < 4; w++) {
-            const unsigned x = a[f + 2 + w], y = b[f + 2 + w];
+            const unsigned x = __ldg(a + f + 2 + w), y = __ldg(b + f + 2 + w);
             p1 = __dp4a(__vsubus4(x, y), 0x01010101u, p1);
             p2 = __dp4a(__vsubus4(y, x), 0x01010101u, p2);
         }
         if (max(p1, p2) > op.k) return false;
-        if (LOG) atomicAdd(&lg.s[k * LOG_FIELDS + 4], 1ull);
-        const uint8_t *sa = static_cast<const uint8_t *>(P.ptr_r[k]) + a[f + 1];
-        const uint8_t *sb = static_cast<const uint8_t *>(P.ptr_s[k]) + b[f + 1];
+        if (LOG) log_add(lg, k * LOG_FIELDS + 4, 1u);
+        const uint8_t *sa = static_cast<const uint8_t *>(P.ptr_r[k]) + __ldg(a + f + 1);
+        const uint8_t *sb = static_cast<const uint8_t *>(P.ptr_s[k]) + __ldg(b + f + 1);
         uint32_t rows = 0;
-        bool r = ed_le(sa, (int)la, sb, (int)lb, op.k, rows);
-        if (LOG) atomicAdd(&lg.s[k * LOG_FIELDS + 5], (unsigned long long)rows * (2ull * op.k + 1ull));
+        const bool r = ed_le(sa, (int)la, sb, (int)lb, op.k, rows);
+        if (LOG) log_add(lg, k * LOG_FIELDS + 5, rows * (2u * op.k + 1u));
         return r;
     }
     // OP_JAC
-    const uint32_t na = a[f], nb = b[f];
+    const uint32_t na = __ldg(a + f), nb = __ldg(b + f);
     if (na == NULL_LEN || nb == NULL_LEN) return false;
     const uint64_t num = op.num, den = op.den;
     const uint32_t mn = min(na, nb), mx = max(na, nb);
     if ((uint64_t)mn * den < num * mx) return false;   // J <= min/max
-    if (LOG) atomicAdd(&lg.s[k * LOG_FIELDS + 3], 1ull);
+    if (LOG) log_add(lg, k * LOG_FIELDS + 3, 1u);
     const uint64_t dn = den + num;
     const uint64_t need = num * ((uint64_t)na + nb);   // I*(den+num) >= num*(|A|+|B|)
     if (na <= 255u && nb <= 255u) {
         unsigned ub = 0;   // sum over 32 gram bins of min(count_a, count_b) >= |A n B|
 #pragma unroll
-        for (int w = 0; w < 8; w++) ub = __dp4a(__vminu4(a[f + 2 + w], b[f + 2 + w]), 0x01010101u, ub);
+        for (int w = 0; w < 8; w++) ub = __dp4a(__vminu4(__ldg(a + f + 2 + w), __ldg(b + f + 2 + w)), 0x01010101u, ub);
         if ((uint64_t)ub * dn < need) return false;
     }
-    if (LOG) atomicAdd(&lg.s[k * LOG_FIELDS + 4], 1ull);
+    if (LOG) log_add(lg, k * LOG_FIELDS + 4, 1u);
     const uint64_t imin = (need + dn - 1) / dn;
     if (imin == 0) return true;
-    const uint32_t *A = static_cast<const uint32_t *>(P.ptr_r[k]) + a[f + 1];
-    const uint32_t *B = static_cast<const uint32_t *>(P.ptr_s[k]) + b[f + 1];
+    const uint32_t *A = static_cast<const uint32_t *>(P.ptr_r[k]) + __ldg(a + f + 1);
+    const uint32_t *B = static_cast<const uint32_t *>(P.ptr_s[k]) + __ldg(b + f + 1);
     uint32_t i = 0, j = 0, I = 0;
     bool res = false;
     while (i < na && j < nb) {
-        const uint32_t x = A[i], y = B[j];
+        const uint32_t x = __ldg(A + i), y = __ldg(B + j);
         I += (x == y) ? 1u : 0u;
         i += (x <= y) ? 1u : 0u;
         j += (y <= x) ? 1u : 0u;
@@ -209,7 +224,7 @@ __device__ __forceinline__ bool eval_op(const EvalParams &P, int k, const uint32
         }
         if ((uint64_t)I + min(na - i, nb - j) < imin) break;
     }
-    if (LOG) atomicAdd(&lg.s[k * LOG_FIELDS + 5], (unsigned long long)(i + j));
+    if (LOG) log_add(lg, k * LOG_FIELDS + 5, i + j);
     return res;
 }
 
@@ -227,11 +242,11 @@ __device__ __forceinline__ bool run_program(const EvalParams &P, uint64_t alive,
         if ((prof ? alive0 : alive) & need) {
             long long c0 = 0;
             if (LOG) c0 = clock64();
-            bool r = eval_op<LOG>(P, k, a, b, lg);
+            const bool r = eval_op<LOG>(P, k, a, b, lg);
             if (LOG) {
-                atomicAdd(&lg.s[k * LOG_FIELDS + 0], 1ull);
-                atomicAdd(&lg.s[k * LOG_FIELDS + 1], r ? 1ull : 0ull);
-                atomicAdd(&lg.s[k * LOG_FIELDS + 2], (unsigned long long)(clock64() - c0));
+                log_add(lg, k * LOG_FIELDS + 0, 1u);
+                log_add(lg, k * LOG_FIELDS + 1, r ? 1u : 0u);
+                log_add(lg, k * LOG_FIELDS + 2, (unsigned)min(clock64() - c0, 0x7fffffffll));
             }
             if (!r) alive &= ~need;
         }
@@ -254,8 +269,8 @@ __device__ __forceinline__ void decode_tile(uint64_t q, uint32_t nr, uint32_t ns
     }
     const int64_t nt = (nr + T - 1) / T;
     // row i holds nt - i tiles; start(i) = i*nt - i*(i-1)/2
-    const double b2 = 2.0 * (double)nt + 1.0;
-    int64_t i = (int64_t)floor((b2 - sqrt(b2 * b2 - 8.0 * (double)q)) * 0.5);
+    const float b2 = 2.0f * (float)nt + 1.0f;
+    int64_t i = (int64_t)floorf((b2 - sqrtf(fmaxf(b2 * b2 - 8.0f * (float)q, 0.0f))) * 0.5f);
     if (i < 0) i = 0;
     if (i > nt - 1) i = nt - 1;
     auto start = [&](int64_t r) { return r * nt - r * (r - 1) / 2; };
@@ -265,16 +280,43 @@ __device__ __forceinline__ void decode_tile(uint64_t q, uint32_t nr, uint32_t ns
     tj = (uint32_t)(i + ((int64_t)q - start(i)));
 }
 
+// largest b in [0, nb) with prefix[b] <= t, searched 32 ways per round
+__device__ __forceinline__ uint32_t find_block(const uint64_t *prefix, uint32_t nb, uint64_t t, int lane) {
+    uint32_t lo = 0, hi = nb;   // prefix[lo] <= t < prefix[hi]
+    while (hi - lo > 1) {
+        const uint32_t step = (hi - lo + 31) / 32;
+        const uint32_t idx = lo + (uint32_t)lane * step;
+        const bool le = idx < hi && prefix[idx] <= t;
+        const unsigned m = __ballot_sync(0xffffffffu, le);
+        const uint32_t L = 31 - __clz(m);
+        const uint32_t nlo = lo + L * step;
+        hi = min(hi, nlo + step);
+        lo = nlo;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ uint64_t alive_of(const EvalParams &P, const uint64_t *lut, uint32_t E) {
+    if (P.use_lut) return lut[E];
+    uint64_t alive = 0;
+    for (int m = 0; m < P.n_md; m++) alive |= ((E & P.eqset[m]) == P.eqset[m]) ? (1ull << m) : 0ull;
+    return alive;
+}
+
 template <int R, bool LOG>
 __global__ void __launch_bounds__(EV_THREADS) k_eval(const __grid_constant__ EvalParams P) {
     extern __shared__ __align__(16) uint32_t smem[];
     constexpr int T = 32 * R;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int W = P.W, WP = P.W + 1;
+    const int HW = P.HW, HWP = P.HW + 1, W = P.W;
     uint64_t *lut = reinterpret_cast<uint64_t *>(smem);
     const int lut_words = P.use_lut ? 2 * (1 << P.n_eq) : 0;
-    uint32_t *rows = smem + lut_words + wib * (2 * T * WP);
-    uint32_t *cols = rows + T * WP;
+    uint32_t *wbase = smem + lut_words + wib * (2 * T * HWP + 2 * T + T * T / 2);
+    uint32_t *hrows = wbase;
+    uint32_t *hcols = hrows + T * HWP;
+    uint32_t *rid_s = hcols + T * HWP;
+    uint32_t *cid_s = rid_s + T;
+    uint16_t *surv = reinterpret_cast<uint16_t *>(cid_s + T);
     __shared__ unsigned long long lgs[LOG ? MAX_OPS * LOG_FIELDS : 1];
     LogAcc lg{lgs};
     if (P.use_lut)
@@ -286,6 +328,9 @@ __global__ void __launch_bounds__(EV_THREADS) k_eval(const __grid_constant__ Eva
     const uint32_t nb = *P.n_blocks;
     const uint64_t total = P.tile_prefix[nb];
     const unsigned lt = (1u << lane) - 1u;
+    const uint32_t allkeys = (P.n_eq >= 32) ? 0xffffffffu : ((1u << P.n_eq) - 1u);
+    const uint32_t *rec_c = P.self_join ? P.rec_r : P.rec_s;
+    const uint32_t *hot_c = P.self_join ? P.hot_r : P.hot_s;
     unsigned long long cand = 0, exam = 0;
 
     for (;;) {
@@ -294,13 +339,7 @@ __global__ void __launch_bounds__(EV_THREADS) k_eval(const __grid_constant__ Eva
         t0 = __shfl_sync(0xffffffffu, t0, 0);
         if (t0 >= total) break;
         const uint64_t t1 = min((uint64_t)t0 + (uint64_t)P.claim, total);
-        uint32_t lo = 0, hi = nb;
-        while (hi - lo > 1) {
-            const uint32_t mid = (lo + hi) >> 1;
-            if (P.tile_prefix[mid] <= t0) lo = mid;
-            else hi = mid;
-        }
-        uint32_t bi = lo;
+        uint32_t bi = find_block(P.tile_prefix, nb, t0, lane);
         for (uint64_t t = t0; t < t1; t++) {
             while (P.tile_prefix[bi + 1] <= t) bi++;
             const BlockDesc B = P.blocks[bi];
@@ -310,18 +349,23 @@ __global__ void __launch_bounds__(EV_THREADS) k_eval(const __grid_constant__ Eva
             const int nr = (int)min((uint32_t)T, B.n_r - r0);
             const int nc = (int)min((uint32_t)T, B.n_s - c0);
             const bool diag = P.self_join && ti == tj;
-            // stage row and column records (16-byte loads; W is a multiple of 4)
-            uint32_t rid[R], cid[R];
+            const uint32_t m = B.md;
+            const uint64_t mbit = 1ull << m;
+            const uint64_t below = mbit - 1ull;
+            const uint32_t okeys = allkeys & ~(uint32_t)P.eqset[m];
+            const int f0 = P.first_op[m];
+            // ---- stage the hot records of the tile's rows and columns
+            __syncwarp();
 #pragma unroll
             for (int rr = 0; rr < R; rr++) {
                 const int r = rr * 32 + lane;
-                rid[rr] = r < nr ? P.members_r[B.start_r + r0 + r] : 0u;
-                cid[rr] = r < nc ? P.members_s[B.start_s + c0 + r] : 0u;
                 if (r < nr) {
-                    const uint4 *src = reinterpret_cast<const uint4 *>(P.rec_r + (size_t)rid[rr] * W);
-                    uint32_t *dst = rows + r * WP;
-                    for (int w4 = 0; w4 < (W >> 2); w4++) {
-                        const uint4 v = src[w4];
+                    const uint32_t id = P.members_r[B.start_r + r0 + r];
+                    rid_s[r] = id;
+                    const uint4 *src = reinterpret_cast<const uint4 *>(P.hot_r + (size_t)id * HW);
+                    uint32_t *dst = hrows + r * HWP;
+                    for (int w4 = 0; w4 < (HW >> 2); w4++) {
+                        const uint4 v = __ldg(src + w4);
                         dst[4 * w4 + 0] = v.x;
                         dst[4 * w4 + 1] = v.y;
                         dst[4 * w4 + 2] = v.z;
@@ -329,11 +373,12 @@ __global__ void __launch_bounds__(EV_THREADS) k_eval(const __grid_constant__ Eva
                     }
                 }
                 if (r < nc) {
-                    const uint4 *src = reinterpret_cast<const uint4 *>(
-                        (P.self_join ? P.rec_r : P.rec_s) + (size_t)cid[rr] * W);
-                    uint32_t *dst = cols + r * WP;
-                    for (int w4 = 0; w4 < (W >> 2); w4++) {
-                        const uint4 v = src[w4];
+                    const uint32_t id = P.members_s[B.start_s + c0 + r];
+                    cid_s[r] = id;
+                    const uint4 *src = reinterpret_cast<const uint4 *>(hot_c + (size_t)id * HW);
+                    uint32_t *dst = hcols + r * HWP;
+                    for (int w4 = 0; w4 < (HW >> 2); w4++) {
+                        const uint4 v = __ldg(src + w4);
                         dst[4 * w4 + 0] = v.x;
                         dst[4 * w4 + 1] = v.y;
                         dst[4 * w4 + 2] = v.z;
@@ -342,60 +387,83 @@ __global__ void __launch_bounds__(EV_THREADS) k_eval(const __grid_constant__ Eva
                 }
             }
             __syncwarp();
+            // ---- phase 1: every pair of the tile
+            int cnt = 0;
 #pragma unroll
             for (int rr = 0; rr < R; rr++) {
                 const int r = rr * 32 + lane;
                 const bool rv = r < nr;
-                const uint32_t *ar = rows + r * WP;
+                const uint32_t *hr = hrows + r * HWP;
                 for (int c = 0; c < nc; c++) {
-                    const uint32_t *bc = cols + c * WP;
+                    const uint32_t *hc = hcols + c * HWP;
                     const bool v = rv && (!diag || c > r);
-                    uint32_t E = 0;
-                    for (int e = 0; e < P.n_eq; e++) {
-                        const uint32_t x = ar[e];
-                        E |= (x == bc[e] && x < NOMATCH_CODE) ? (1u << e) : 0u;
+                    uint32_t E = P.eqset[m];
+                    for (uint32_t ok = okeys; ok; ok &= ok - 1) {
+                        const int e = __ffs(ok) - 1;
+                        const uint32_t x = hr[e];
+                        E |= (x == hc[e] && x < NOMATCH_CODE) ? (1u << e) : 0u;
                     }
-                    uint64_t alive;
-                    if (P.use_lut) {
-                        alive = lut[E];
-                    } else {
-                        alive = 0;
-                        for (int m = 0; m < P.n_md; m++)
-                            alive |= ((E & P.eqset[m]) == P.eqset[m]) ? (1ull << m) : 0ull;
-                    }
-                    const bool own = v && alive != 0 && (uint32_t)(__ffsll((long long)alive) - 1) == B.md;
-                    cand += __popc(__ballot_sync(0xffffffffu, own));
-                    exam += __popc(__ballot_sync(0xffffffffu, v));
-                    bool hit = false;
-                    if (own) hit = run_program<LOG>(P, alive, ar, bc, lg);
-                    const unsigned hm = __ballot_sync(0xffffffffu, hit);
-                    if (hm) {
-                        unsigned long long base = 0;
-                        if (lane == 0) base = atomicAdd(P.out_count, (unsigned long long)__popc(hm));
-                        base = __shfl_sync(0xffffffffu, base, 0);
-                        // column id of column c: lane (c % 32) holds it in cid[c / 32]
-                        uint32_t mycid = 0;
-#pragma unroll
-                        for (int q = 0; q < R; q++)
-                            if (q == c / 32) mycid = cid[q];
-                        const uint32_t colid = __shfl_sync(0xffffffffu, mycid, c & 31);
-                        if (hit) {
-                            const unsigned long long idx = base + __popc(hm & lt);
-                            uint64_t key;
-                            if (P.self_join) {
-                                const uint32_t x = rid[rr], y = colid;
-                                const uint32_t lo2 = x < y ? x : y, hi2 = x < y ? y : x;
-                                key = ((uint64_t)lo2 << P.key_bits_s) | (uint64_t)hi2;
-                            } else {
-                                key = ((uint64_t)(rid[rr] + P.row_base) << P.key_bits_s) |
-                                      (uint64_t)(colid + P.col_base);
-                            }
-                            if (idx < P.out_cap) P.out[idx] = key;
+                    const uint64_t alive = alive_of(P, lut, E);
+                    const bool own = v && (alive & mbit) && !(alive & below);
+                    bool keep = own;
+                    if (!LOG && own && alive == mbit && f0 >= 0) {
+                        const Op &op = P.ops[f0];
+                        const uint32_t x = hr[op.hot], y = hc[op.hot];
+                        if (op.kind == OP_ED) {
+                            keep = x != NULL_LEN && y != NULL_LEN && (x > y ? x - y : y - x) <= op.k;
+                        } else if (op.kind == OP_JAC) {
+                            keep = x != NULL_LEN && y != NULL_LEN &&
+                                   (uint64_t)min(x, y) * op.den >= (uint64_t)op.num * max(x, y);
+                        } else {
+                            keep = fabsf(__uint_as_float(x) - __uint_as_float(y)) <= op.delta;
                         }
                     }
+                    exam += __popc(__ballot_sync(0xffffffffu, v));
+                    cand += __popc(__ballot_sync(0xffffffffu, own));
+                    const unsigned km = __ballot_sync(0xffffffffu, keep);
+                    if (keep) surv[cnt + __popc(km & lt)] = (uint16_t)((r << 6) | c);
+                    cnt += __popc(km);
                 }
             }
             __syncwarp();
+            // ---- phase 2: the survivors, one per lane
+            for (int s0 = 0; s0 < cnt; s0 += 32) {
+                const int s = s0 + lane;
+                bool hit = false;
+                uint32_t ra = 0, cb = 0;
+                if (s < cnt) {
+                    const uint32_t e16 = surv[s];
+                    const int r = (int)(e16 >> 6), c = (int)(e16 & 63u);
+                    ra = rid_s[r];
+                    cb = cid_s[c];
+                    const uint32_t *hr = hrows + r * HWP, *hc = hcols + c * HWP;
+                    uint32_t E = P.eqset[m];
+                    for (uint32_t ok = okeys; ok; ok &= ok - 1) {
+                        const int e = __ffs(ok) - 1;
+                        const uint32_t x = hr[e];
+                        E |= (x == hc[e] && x < NOMATCH_CODE) ? (1u << e) : 0u;
+                    }
+                    const uint64_t alive = alive_of(P, lut, E);
+                    hit = run_program<LOG>(P, alive, P.rec_r + (size_t)ra * W, rec_c + (size_t)cb * W, lg);
+                }
+                const unsigned hm = __ballot_sync(0xffffffffu, hit);
+                if (hm) {
+                    unsigned long long base = 0;
+                    if (lane == 0) base = atomicAdd(P.out_count, (unsigned long long)__popc(hm));
+                    base = __shfl_sync(0xffffffffu, base, 0);
+                    if (hit) {
+                        const unsigned long long idx = base + __popc(hm & lt);
+                        uint64_t key;
+                        if (P.self_join) {
+                            const uint32_t lo2 = ra < cb ? ra : cb, hi2 = ra < cb ? cb : ra;
+                            key = ((uint64_t)lo2 << P.key_bits_s) | (uint64_t)hi2;
+                        } else {
+                            key = ((uint64_t)(ra + P.row_base) << P.key_bits_s) | (uint64_t)(cb + P.col_base);
+                        }
+                        if (idx < P.out_cap) P.out[idx] = key;
+                    }
+                }
+            }
         }
     }
     if (lane == 0 && cand) atomicAdd(P.cand_count, cand);
@@ -419,10 +487,10 @@ __global__ void k_pack_pairs(const uint64_t *keys, int64_t n, int key_bits_s, hb
 
 }  // namespace
 
-size_t eval_smem_bytes(int W, int n_eq, int use_lut, int tile) {
-    const int R = tile / 32;
+size_t eval_smem_bytes(int HW, int n_eq, int use_lut, int tile) {
+    const size_t T = (size_t)tile;
     size_t lut = use_lut ? (size_t)8 << n_eq : 0;
-    return lut + (size_t)EV_WARPS * 2 * (32 * R) * (W + 1) * 4;
+    return lut + (size_t)EV_WARPS * (2 * T * (HW + 1) + 2 * T + T * T / 2) * 4;
 }
 
 template <int R, bool LOG>
@@ -439,12 +507,11 @@ int eval_blocks_per_sm(int tile, int logging, size_t smem) {
 }
 
 cudaError_t launch_eval(const EvalParams &p, int grid, size_t smem, int logging, cudaStream_t s) {
+    HB_LAUNCHED(1);
     if (p.tile == 64) {
-        HB_LAUNCHED(1);
         if (logging) k_eval<2, true><<<grid, EV_THREADS, smem, s>>>(p);
         else k_eval<2, false><<<grid, EV_THREADS, smem, s>>>(p);
     } else {
-        HB_LAUNCHED(1);
         if (logging) k_eval<1, true><<<grid, EV_THREADS, smem, s>>>(p);
         else k_eval<1, false><<<grid, EV_THREADS, smem, s>>>(p);
     }
