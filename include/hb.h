@@ -92,6 +92,10 @@ typedef struct {
 
 typedef struct { uint32_t tid1, tid2; } hb_pair;
 
+/* hb_options.flags */
+#define HB_FLAG_PER_JOB_LAUNCHES 1   /* hb_block_batch: one launch sequence per job (comparison baseline) */
+#define HB_FLAG_NO_GRAPH 2           /* hb_block_batch: never capture or replay a CUDA graph */
+
 typedef struct {
     int32_t device;           /* CUDA device ordinal */
     int32_t tile;             /* tuples per tile side: 0 = autotuned, else 32 or 64 */

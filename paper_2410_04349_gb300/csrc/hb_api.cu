@@ -209,8 +209,10 @@ extern "C" void hb_destroy(hb_ctx *c) {
     Buf *bufs[] = {&c->w_table, &c->w_slot_r, &c->w_slot_s, &c->w_count_r, &c->w_count_s, &c->w_start_r,
                    &c->w_start_s, &c->w_cursor, &c->w_members_r, &c->w_members_s, &c->w_blocks, &c->w_tiles,
                    &c->w_prefix, &c->w_scan, &c->w_out, &c->w_alt, &c->w_sort, &c->w_pairs, &c->w_counters,
-                   &c->w_lut, &c->w_log, &c->w_jac};
+                   &c->w_lut, &c->w_log, &c->w_jac, &c->w_jobrows, &c->w_jobcount, &c->w_joboff};
     for (Buf *b : bufs) free_buf(c, *b);
+    if (c->batch_exec) cudaGraphExecDestroy(c->batch_exec);
+    if (c->batch_graph) cudaGraphDestroy(c->batch_graph);
     cudaStreamSynchronize(c->stream);
     for (int b = 0; b < 2; b++) {
         if (c->pin[b]) cudaFreeHost(c->pin[b]);
@@ -767,6 +769,21 @@ hb_status encode_side(hb_ctx *c, int side) {
     free_buf(c, flag);
     HB_CUDA(cudaGetLastError());
     if (too_long) return fail(HB_ERR_ARG, "a string compared by q-gram Jaccard has more than 8192 grams");
+    if (c->batch_layout && side == 0) {
+        // the job id is one more equality key held by every MD: blocks never span jobs
+        const int n_jobs = (int)c->job_rows.size() - 1;
+        if (n_jobs < 1 || c->job_rows.back() != n) return fail(HB_ERR_STATE, "batch layout without job rows");
+        Buf jr;
+        HB_TRY(grow(c, jr, sizeof(int64_t) * c->job_rows.size()));
+        HB_CUDA(cudaMemcpyAsync(jr.p, c->job_rows.data(), sizeof(int64_t) * c->job_rows.size(),
+                                cudaMemcpyHostToDevice, c->stream));
+        if (n > 0) {
+            HB_LAUNCHED(1);
+            k_job_codes<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(as<int64_t>(jr), n_jobs, n, S.rec, W,
+                                                                            c->n_eq_total - 1);
+        }
+        free_buf(c, jr);
+    }
     {
         std::vector<int32_t> map(c->HW, -1);
         for (int e = 0; e < c->n_eq_total; e++) map[e] = e;
@@ -787,7 +804,7 @@ namespace hb {
 
 
 // counters layout (u64 words): 0 tile_counter, 1 out_count, 2 cand_count, 3 n_blocks (u32), 4 overflow (u32)
-static hb_status build_blocks(hb_ctx *c, const uint32_t *rec_r, int64_t n_r, const uint32_t *rec_s, int64_t n_s,
+hb_status build_blocks(hb_ctx *c, const uint32_t *rec_r, int64_t n_r, const uint32_t *rec_s, int64_t n_s,
                               bool self, unsigned long long *ctr, uint32_t &block_cap) {
     const int W = c->W;
     const uint64_t H = pow2_at_least(std::max<uint64_t>(2 * (uint64_t)std::max<int64_t>(n_r, 1), 1024));
@@ -858,7 +875,7 @@ static hb_status build_blocks(hb_ctx *c, const uint32_t *rec_r, int64_t n_r, con
     return HB_OK;
 }
 
-static EvalParams make_params(hb_ctx *c, const uint32_t *rec_r, const uint32_t *rec_s, int side_s, bool self,
+EvalParams make_params(hb_ctx *c, const uint32_t *rec_r, const uint32_t *rec_s, int side_s, bool self,
                               unsigned long long *ctr, int key_bits_s) {
     EvalParams P;
     memset(&P, 0, sizeof(P));
@@ -905,7 +922,7 @@ static EvalParams make_params(hb_ctx *c, const uint32_t *rec_r, const uint32_t *
     P.out_cap = (uint64_t)c->out_cap;
     P.cand_count = ctr + 2;
     P.exam_count = ctr + 5;
-    P.claim = 2;
+    P.claim = c->claim;
     P.log = as<unsigned long long>(c->w_log);
     return P;
 }

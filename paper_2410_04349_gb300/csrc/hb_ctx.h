@@ -123,6 +123,17 @@ struct hb_ctx {
     void *pin[2] = {nullptr, nullptr};
     cudaEvent_t pin_ev[2] = {nullptr, nullptr};
     size_t pin_bytes = 0;
+    // batched jobs: row offsets of the stacked jobs (hb_block_batch)
+    std::vector<int64_t> job_rows;
+    // captured batch pipeline and the shapes it was captured for
+    cudaGraph_t batch_graph = nullptr;
+    cudaGraphExec_t batch_exec = nullptr;
+    std::vector<int64_t> batch_graph_key;
+    Buf w_jobrows, w_jobcount, w_joboff;
+    // autotuner cache: job-size signature -> (tile, claim)
+    std::vector<std::pair<std::vector<int64_t>, std::pair<int, int>>> tune_cache;
+    int claim = 2;
+    long long graph_kernels = 0;   // kernels in the captured batch graph
     // results
     hb_pair *dev_result = nullptr;
     size_t dev_result_bytes = 0;
@@ -172,6 +183,12 @@ hb_status block_eval_sort(hb_ctx *c, const uint32_t *rec_r, int64_t n_r, const u
                           uint64_t **sorted, Timer *tm);
 hb_status deliver(hb_ctx *c, const uint64_t *keys, int64_t n, int key_bits_s, bool to_host, hb_pair **out);
 hb_status learned_stats(hb_ctx *c, std::vector<double> &sp, std::vector<double> &cost, bool &ok);
+// counters (u64 words): 0 tile claims, 1 output count, 2 candidates, 3 block count (u32), 4 block overflow,
+// 5 examined pairs
+hb_status build_blocks(hb_ctx *c, const uint32_t *rec_r, int64_t n_r, const uint32_t *rec_s, int64_t n_s, bool self,
+                       unsigned long long *ctr, uint32_t &block_cap);
+EvalParams make_params(hb_ctx *c, const uint32_t *rec_r, const uint32_t *rec_s, int side_s, bool self,
+                       unsigned long long *ctr, int key_bits_s);
 
 template <typename T>
 static inline T *as(Buf &b) {

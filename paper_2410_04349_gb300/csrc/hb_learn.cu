@@ -149,14 +149,3 @@ extern "C" hb_status hb_train_cost_model(hb_ctx *c, int32_t n, const float *X, c
     return fail(HB_ERR_STATE, "hb_train_cost_model: not available yet");
 }
 
-extern "C" hb_status hb_block_stream(hb_ctx *c, int64_t n_rows_s, int32_t n_cols, const hb_column *cols_s,
-                                     hb_pair **pairs_out, int64_t *n_out) {
-    (void)c; (void)n_rows_s; (void)n_cols; (void)cols_s; (void)pairs_out; (void)n_out;
-    return fail(HB_ERR_STATE, "hb_block_stream: not available yet");
-}
-
-extern "C" hb_status hb_block_batch(hb_ctx *c, int32_t n_jobs, const int64_t *job_rows, hb_pair **pairs_out,
-                                    int64_t *job_pairs_out) {
-    (void)c; (void)n_jobs; (void)job_rows; (void)pairs_out; (void)job_pairs_out;
-    return fail(HB_ERR_STATE, "hb_block_batch: not available yet");
-}

@@ -26,6 +26,7 @@ LIB_PATH = os.path.join(_HERE, "libhb.so")
 HB_OK, HB_ERR_ARG, HB_ERR_OOM, HB_ERR_CUDA, HB_ERR_STATE, HB_ERR_OVERFLOW, HB_ERR_DEVICE_TIMEOUT = 0, -1, -2, -3, -4, -5, -6
 KINDS = {"eq": 0, "eq_prefix": 1, "ed": 2, "jaccard": 3, "absdiff": 4}
 TYPES = {"string": 0, "int32": 1, "fp32": 2}
+FLAG_PER_JOB_LAUNCHES, FLAG_NO_GRAPH = 1, 2
 PLAN_MODES = {"rule_data": 0, "learned": 1, "given": 2, "random": 3, "cost_first": 4, "sel_first": 5}
 MAX_MDS, MAX_PREDS, FEATURES = 64, 128, 32
 MLP_PARAMS = 32 * 64 + 64 + 64 * 64 + 64 + 64 + 1
@@ -200,9 +201,9 @@ def _pairs_to_numpy(ptr, n):
 class Context:
     """One libhb context (hb_create ... hb_destroy)."""
 
-    def __init__(self, device=0, tile=0, chunk_bytes=0, seed=0, stream=None, out_capacity=0):
+    def __init__(self, device=0, tile=0, chunk_bytes=0, seed=0, stream=None, out_capacity=0, flags=0):
         L = lib()
-        opt = hb_options(device, tile, chunk_bytes, seed, stream, out_capacity, 0, 0)
+        opt = hb_options(device, tile, chunk_bytes, seed, stream, out_capacity, flags, 0)
         h = ctypes.c_void_p()
         _check(L.hb_create(ctypes.byref(h), ctypes.byref(opt)), "hb_create")
         self._h = h
