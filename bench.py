@@ -63,6 +63,10 @@ def parse():
     ap.add_argument("--cpu-sample-rows", type=int, default=80_000)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--workload", choices=["c2", "c3", "c4", "c5"], default="c2",
+                    help="c2 (default): the single-table step above; c3: R x S with S streamed from host in pinned "
+                         "chunks; c4: 10,000 jobs batched vs one launch sequence per job; c5: learned vs rule- and "
+                         "data-aware plan on 10M tuples")
     return ap.parse_args()
 
 
@@ -234,11 +238,180 @@ def run_reference(args, rank, world):
     return 0
 
 
+def _line(metric, value, unit, args, ms, workload, **extra):
+    d = {"metric": metric, "value": value, "unit": unit, "n_gpus": 1, "steps": args.steps,
+         "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+         "vs_baseline": None, "dtype": "u32", "data": "synthetic", "config": {"workload": workload}}
+    d.update(extra)
+    return d
+
+
+def run_c3(args):
+    """R (500K) x S (2M), six MDs, S streamed from host in pinned chunks."""
+    import torch
+    import synth
+    from paper_2410_04349_gb300 import hb
+    r, s, mds = synth.config3()
+    out = {}
+    for chunk in (256 << 20, 32 << 20):
+        with hb.Context(device=0, chunk_bytes=chunk) as ctx:
+            ctx.load_table(0, r.n_rows, r.columns)
+            for md in mds:
+                ctx.add_md(md)
+            for _ in range(max(args.warmup, 3)):
+                pairs = ctx.block_stream(s.n_rows, s.columns)
+            times = []
+            for _ in range(args.steps):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                pairs = ctx.block_stream(s.n_rows, s.columns)
+                times.append(time.perf_counter() - t0)
+            st = ctx.stats()
+        out[chunk] = (statistics.median(times), st, len(pairs))
+    t, st, n = out[256 << 20]
+    line = _line(METRIC, st["candidate_pairs"] / t, UNIT, args, t * 1e3,
+                 "R x S: 500,000 x 2,000,000 tuples x 8 attributes, 5% cross-duplicates, 6 MDs (one blocked only by a "
+                 "2-character prefix); S streamed from host memory in 256 MiB pinned chunks",
+                 candidate_pairs_per_step=st["candidate_pairs"], emitted_pairs_per_step=n,
+                 e2e={"value": st["candidate_pairs"] / t, "unit": UNIT, "h2d_bytes_per_step": s.nbytes(),
+                      "d2h_bytes_per_step": n * 8},
+                 chunk_32MiB={"ms_per_step": out[32 << 20][0] * 1e3,
+                              "value": out[32 << 20][1]["candidate_pairs"] / out[32 << 20][0]})
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_c4(args):
+    """10,000 independent jobs: one batched launch (graph replay) vs one launch sequence per job."""
+    import torch
+    import synth
+    from paper_2410_04349_gb300 import hb
+    t, mds = synth.config4()
+    res = {}
+    for name, flags, steps in (("batched", 0, args.steps), ("per_job", hb.FLAG_PER_JOB_LAUNCHES, 1)):
+        with hb.Context(device=0, flags=flags) as ctx:
+            ctx.load_table(0, t.n_rows, t.columns)
+            for md in mds:
+                ctx.add_md(md)
+            for _ in range(1 if flags else max(args.warmup, 3)):
+                pairs, offs = ctx.block_batch(t.job_offsets)
+            times = []
+            l0 = ctx.stats()["kernel_launches"]
+            for _ in range(steps):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                pairs, offs = ctx.block_batch(t.job_offsets)
+                times.append(time.perf_counter() - t0)
+            st = ctx.stats()
+            res[name] = (statistics.median(times), st, pairs, offs, (st["kernel_launches"] - l0) // steps)
+    tb, stb, pb, ob, lb = res["batched"]
+    tp, stp, pp, op_, lp = res["per_job"]
+    identical = bool(np.array_equal(pb, pp) and np.array_equal(ob, op_))
+    line = _line(METRIC, stb["candidate_pairs"] / tb, UNIT, args, tb * 1e3,
+                 f"10,000 independent jobs of {t.n_rows} tuples in total (lognormal sizes in [50, 20000]), C2 schema "
+                 f"and rules; one persistent launch replayed from a CUDA graph",
+                 candidate_pairs_per_step=stb["candidate_pairs"], emitted_pairs_per_step=len(pb),
+                 tile=stb["tile"], gpu_launches=lb,
+                 per_job={"ms_per_step": tp * 1e3, "value": stp["candidate_pairs"] / tp, "gpu_launches": lp},
+                 speedup_vs_per_job=tp / tb, identical_pair_sets=identical)
+    print(json.dumps(line), flush=True)
+    return 0 if identical else 1
+
+
+def c5_training_rows(ctx_factory):
+    """Training rows of the cost model from logs of configs 2-4 under the given
+    rules and seeded random rule sets."""
+    import synth
+    from paper_2410_04349_gb300 import learn
+    Xs, ycs, yss = [], [], []
+
+    def rows(table, sets, S=None):
+        with ctx_factory() as ctx:
+            ctx.load_table(0, table.n_rows, table.columns)
+            if S is not None:
+                ctx.load_table(1, S.n_rows, S.columns)
+            for mds in sets:
+                ctx.clear_mds()
+                for md in mds:
+                    ctx.add_md(md)
+                ctx.plan("rule_data")
+                X, yc, ys = learn.collect(ctx)
+                Xs.append(X)
+                ycs.append(yc)
+                yss.append(ys)
+
+    t2, m2 = synth.config2()
+    rows(t2, [m2] + [synth.random_rule_set(100 + i, 4, [2, 3, 4], [0, 1], [5, 6]) for i in range(16)])
+    r3, s3, m3 = synth.config3()
+    rows(r3, [m3] + [synth.random_rule_set(200 + i, 4, [2, 3, 4], [0, 1], [5, 6]) for i in range(8)], S=s3)
+    sizes = [20000, 16000, 12000, 9000, 7000, 5000, 4000, 3000]
+    t4, m4 = synth.config4(n_jobs=len(sizes), sizes=sizes)
+    for j in range(len(sizes)):
+        sub = t4.slice(t4.job_offsets[j], t4.job_offsets[j + 1])
+        rows(sub, [m4] + [synth.random_rule_set(300 + 10 * j + i, 4, [2, 3, 4], [0, 1], [5, 6], n_keys=(1, 2))
+                          for i in range(3)])
+    return np.concatenate(Xs), np.concatenate(ycs), np.concatenate(yss)
+
+
+def run_c5(args):
+    """Learned cost model (trained on logs of configs 2-4) vs the rule- and
+    data-aware plan on 10M tuples x 12 attributes with 16 MDs."""
+    import torch
+    import synth
+    from paper_2410_04349_gb300 import hb, learn
+    t0 = time.perf_counter()
+    X, yc, ys = c5_training_rows(lambda: hb.Context(device=0))
+    with hb.Context(device=0) as ctx:
+        loss = learn.train(ctx, X, yc, ys)
+        model = ctx.get_cost_model()
+    train_s = time.perf_counter() - t0
+    t, mds = synth.config5()
+    res = {}
+    with hb.Context(device=0) as ctx:
+        ctx.load_table(0, t.n_rows, t.columns)
+        for md in mds:
+            ctx.add_md(md)
+        ctx.set_cost_model(model)
+        for mode in ("rule_data", "learned"):
+            info = ctx.plan(mode)
+            for _ in range(max(args.warmup, 3)):
+                pairs = ctx.block()
+            ev, tot = [], []
+            for _ in range(args.steps):
+                torch.cuda.synchronize()
+                s0 = time.perf_counter()
+                pairs = ctx.block()
+                tot.append(time.perf_counter() - s0)
+                ev.append(ctx.stats()["ms_eval"])
+            st = ctx.stats()
+            res[mode] = (statistics.median(tot), statistics.median(ev), st, pairs, info.mode,
+                         list(info.op_pred[:info.n_ops]))
+    identical = bool(np.array_equal(res["rule_data"][3], res["learned"][3]))
+    tl, el, stl, pl, applied, opl = res["learned"]
+    tp, ep, stp, pp, _, opp = res["rule_data"]
+    line = _line(METRIC, stl["candidate_pairs"] / (el / 1e3), UNIT, args, tl * 1e3,
+                 "single table, 10,000,000 tuples x 12 attributes (4 strings 8-80 chars, 5 Zipf(1.1) keys, 3 fp32), "
+                 "10% near-duplicates, 16 MDs; learned plan",
+                 candidate_pairs_per_step=stl["candidate_pairs"], emitted_pairs_per_step=len(pl),
+                 learned={"eval_ms": el, "step_ms": tl * 1e3, "plan_mode_applied": applied, "program": opl},
+                 rule_data={"eval_ms": ep, "step_ms": tp * 1e3, "program": opp},
+                 eval_speedup_learned_vs_plain=ep / el, step_speedup_learned_vs_plain=tp / tl,
+                 identical_pair_sets=identical,
+                 training={"rows": int(len(X)), "loss_cost": float(loss[0]), "loss_sel": float(loss[1]),
+                           "seconds_incl_logging": train_s})
+    print(json.dumps(line), flush=True)
+    return 0 if identical else 1
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.workload != "c2":
+        if rank != 0:
+            return 0
+        return {"c3": run_c3, "c4": run_c4, "c5": run_c5}[args.workload](args)
     import torch
     import synth
     from paper_2410_04349_gb300 import hb

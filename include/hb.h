@@ -238,7 +238,9 @@ HB_API hb_status hb_plan_order(int32_t n_preds, const double *sp, const double *
 /* One logged predicate evaluation record of the blocker. */
 typedef struct {
     float features[HB_FEATURES];
-    float log_cost;          /* log(mean device cycles per evaluation) */
+    float log_cost;          /* log of the device cycles per pair when the predicate is evaluated first:
+                                16 for its cheap filter (length / size / |a-b| test on staged operands)
+                                plus, times the filter pass rate, the measured cycles of a full evaluation */
     float logit_pass;        /* logit(pass rate), clamped to [-12, 12] */
     int64_t evaluated;       /* evaluations counted */
     int64_t passed;

@@ -549,6 +549,38 @@ static hb_status plan_stats(hb_ctx *c, std::vector<double> &sp, std::vector<doub
             mlen /= cnt;
             mg /= cnt;
         }
+        {   // sampled value statistics kept for the learned cost model's features
+            std::vector<double> Ls, Gs;
+            int nulls = 0;
+            for (int s = 0; s < n_keep; s++) {
+                uint32_t L = h[(size_t)P * K + P + (size_t)p * n_keep + s];
+                uint32_t G = h[(size_t)P * K + P + (size_t)P * n_keep + (size_t)p * n_keep + s];
+                if (L == NULL_LEN) {
+                    nulls++;
+                    continue;
+                }
+                Ls.push_back(L);
+                Gs.push_back(G);
+            }
+            std::vector<float> st(10, 0.f);
+            if (!Ls.empty()) {
+                std::sort(Ls.begin(), Ls.end());
+                double m = 0, v = 0, gm = 0, gv = 0;
+                for (double x : Ls) m += x;
+                m /= Ls.size();
+                for (double x : Ls) v += (x - m) * (x - m);
+                for (double x : Gs) gm += x;
+                gm /= Gs.size();
+                for (double x : Gs) gv += (x - gm) * (x - gm);
+                auto q = [&](double f) { return Ls[std::min(Ls.size() - 1, (size_t)(f * (Ls.size() - 1) + 0.5))]; };
+                st = {(float)m, (float)std::sqrt(v / Ls.size()), (float)q(0.1), (float)q(0.5), (float)q(0.9),
+                      (float)Ls.back(), (float)gm, (float)std::sqrt(gv / Gs.size()), 0.f, 0.f};
+            }
+            st[8] = n_keep ? (float)nulls / (float)n_keep : 0.f;
+            st[9] = (float)sd[p];
+            if ((int)c->pred_stats.size() != P) c->pred_stats.assign(P, std::vector<float>(10, 0.f));
+            c->pred_stats[p] = st;
+        }
         switch (q.kind) {
         case HB_P_EQ:
         case HB_P_EQ_PREFIX: cost[p] = 1.0; break;
@@ -566,6 +598,8 @@ static hb_status plan_stats(hb_ctx *c, std::vector<double> &sp, std::vector<doub
         sp[p] = mx > 0 ? std::max(sd[p] / mx, 1e-6) : 1e-6;
         cost[p] = mc > 0 ? std::max(cost[p] / mc, 1e-6) : 1e-6;
     }
+    c->plain_sp = sp;
+    c->plain_cost = cost;
     return HB_OK;
 }
 
@@ -666,6 +700,10 @@ hb_status do_plan(hb_ctx *c, int mode, bool job_key) {
     HB_TRY(plan_stats(c, sp, cost));
     int applied = mode;
     if (mode == HB_PLAN_LEARNED) {
+        // the features come from an instrumented run of a row sample, which
+        // needs a program: the rule- and data-aware plan serves provisionally
+        // (and stays when the model is missing or its output is unusable)
+        HB_TRY(finish_plan(c, HB_PLAN_RULE_DATA, sp, cost));
         bool ok = false;
         std::vector<double> lsp = sp, lcost = cost;
         HB_TRY(learned_stats(c, lsp, lcost, ok));

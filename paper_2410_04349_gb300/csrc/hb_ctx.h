@@ -133,6 +133,10 @@ struct hb_ctx {
     // autotuner cache: job-size signature -> (tile, claim)
     std::vector<std::pair<std::vector<int64_t>, std::pair<int, int>>> tune_cache;
     int claim = 2;
+    // planner statistics kept for the learned model: per predicate [len mean, len std, p10, p50, p90, max,
+    // gram mean, gram std, null fraction, LSH bucket stddev]
+    std::vector<std::vector<float>> pred_stats;
+    std::vector<double> plain_sp, plain_cost;
     long long graph_kernels = 0;   // kernels in the captured batch graph
     // results
     hb_pair *dev_result = nullptr;

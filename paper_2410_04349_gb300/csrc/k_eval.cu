@@ -12,9 +12,9 @@
 //        present code of key e; the MDs whose keys are all in E are alive;
 //      - owner check: the pair is handled only in the block of the lowest
 //        alive MD, so each pair is evaluated once however many blocks hold it;
-//      - when the owner is the only alive MD, the cheap necessary condition of
-//        its first predicate (length / size filter, or the |a-b| test itself)
-//        rejects most pairs at once;
+//      - the cheap necessary condition of the first predicate of every alive
+//        MD (length / size filter, or the |a-b| test itself) rejects most
+//        pairs at once: a pair survives if some alive MD passes it;
 //    the remaining pairs are compacted into a per-warp survivor list (ballot).
 //  phase 2 (survivors, 32 at a time, all lanes busy): the sequential execution
 //    path of Section 5.1 on the full records: non-equality predicates in plan
@@ -303,6 +303,16 @@ __device__ __forceinline__ uint64_t alive_of(const EvalParams &P, const uint64_t
     return alive;
 }
 
+// the cheap necessary condition of a predicate on the staged filter operands
+// (length filter of edit distance, size filter of Jaccard, |a-b| <= delta itself)
+__device__ __forceinline__ bool first_filter(const Op &op, const uint32_t *hr, const uint32_t *hc) {
+    const uint32_t x = hr[op.hot], y = hc[op.hot];
+    if (op.kind == OP_ED) return x != NULL_LEN && y != NULL_LEN && (x > y ? x - y : y - x) <= op.k;
+    if (op.kind == OP_JAC)
+        return x != NULL_LEN && y != NULL_LEN && (uint64_t)min(x, y) * op.den >= (uint64_t)op.num * max(x, y);
+    return fabsf(__uint_as_float(x) - __uint_as_float(y)) <= op.delta;
+}
+
 template <int R, bool LOG>
 __global__ void __launch_bounds__(EV_THREADS) k_eval(const __grid_constant__ EvalParams P) {
     extern __shared__ __align__(16) uint32_t smem[];
@@ -405,17 +415,18 @@ __global__ void __launch_bounds__(EV_THREADS) k_eval(const __grid_constant__ Eva
                     }
                     const uint64_t alive = alive_of(P, lut, E);
                     const bool own = v && (alive & mbit) && !(alive & below);
+                    // reject the pair when the first predicate of every alive MD
+                    // fails its necessary condition (no MD can be witnessed)
                     bool keep = own;
-                    if (!LOG && own && alive == mbit && f0 >= 0) {
-                        const Op &op = P.ops[f0];
-                        const uint32_t x = hr[op.hot], y = hc[op.hot];
-                        if (op.kind == OP_ED) {
-                            keep = x != NULL_LEN && y != NULL_LEN && (x > y ? x - y : y - x) <= op.k;
-                        } else if (op.kind == OP_JAC) {
-                            keep = x != NULL_LEN && y != NULL_LEN &&
-                                   (uint64_t)min(x, y) * op.den >= (uint64_t)op.num * max(x, y);
+                    if (!LOG && own && !(alive & P.eqonly)) {
+                        if (alive == mbit) {
+                            keep = first_filter(P.ops[f0], hr, hc);
                         } else {
-                            keep = fabsf(__uint_as_float(x) - __uint_as_float(y)) <= op.delta;
+                            keep = false;
+                            for (uint64_t rem = alive; rem && !keep; rem &= rem - 1) {
+                                const int f = P.first_op[__ffsll((long long)rem) - 1];
+                                keep = f < 0 || first_filter(P.ops[f], hr, hc);
+                            }
                         }
                     }
                     exam += __popc(__ballot_sync(0xffffffffu, v));

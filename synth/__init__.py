@@ -335,8 +335,9 @@ C5_NAMES = ["s1", "s2", "s3", "s4", "c1", "c2", "c3", "c4", "c5", "x1", "x2", "x
 
 
 def c5_mds(seed=BASE_SEED + 5):
-    """16 rules of 2-5 predicates: equality on 3 of the 5 categoricals plus one
-    or two of {ED <= 2..3 on a string, 3-gram Jaccard >= 7/10 or 4/5, |x-x'| <= delta}."""
+    """16 rules of 4-6 predicates: equality on 3 of the 5 categoricals, one or
+    two string similarities (ED <= 2..3, or 3-gram Jaccard >= 7/10 or 4/5) and,
+    for about half of them, |x - x'| <= delta on a numeric column."""
     lib = _load()
     mds = []
     for m in range(16):
@@ -344,32 +345,18 @@ def c5_mds(seed=BASE_SEED + 5):
         cats = [4, 5, 6, 7, 8]
         chosen = []
         for k in range(3):
-            i = r(k) % len(cats)
-            chosen.append(cats.pop(i))
+            chosen.append(cats.pop(int(r(k) % len(cats))))
         preds = [eq(c) for c in sorted(chosen)]
-        n_sim = 1 + (r(10) % 2)
-        used = set()
-        for k in range(n_sim):
-            kind = r(20 + k) % 3
-            if kind == 0:
-                s = r(30 + k) % 4
-                if ("ed", s) in used:
-                    continue
-                used.add(("ed", s))
-                preds.append(ed(s, 2 + r(40 + k) % 2))
-            elif kind == 1:
-                s = r(30 + k) % 4
-                if ("j", s) in used:
-                    continue
-                used.add(("j", s))
-                num, den = ((7, 10), (4, 5))[r(40 + k) % 2]
-                preds.append(jac(s, num, den))
+        strs = [0, 1, 2, 3]
+        for j in range(1 + int(r(25) % 2)):       # one or two string similarities
+            s = strs.pop(int(r(30 + j) % len(strs)))
+            if r(20 + j) % 2 == 0:
+                preds.append(ed(s, 2 + int(r(40 + j) % 2)))
             else:
-                x = 9 + r(30 + k) % 3
-                if ("x", x) in used:
-                    continue
-                used.add(("x", x))
-                preds.append(absdiff(x, (0.5, 1.0, 2.0)[r(40 + k) % 3]))
+                num, den = ((7, 10), (4, 5))[int(r(40 + j) % 2)]
+                preds.append(jac(s, num, den))
+        if r(50) % 2 == 0:
+            preds.append(absdiff(9 + int(r(60) % 3), (0.5, 1.0, 2.0)[int(r(70) % 3)]))
         mds.append(preds)
     return mds
 
@@ -416,3 +403,37 @@ def table_from_rows(names, types, rows) -> Table:
             cols.append(Column(name, ty, np.array([v if v is not None else 0.0 for v in vals], np.float32),
                                None, None if valid.all() else valid))
     return Table(cols, n)
+
+
+def random_rule_set(seed, n_mds, key_cols, str_cols, num_cols, n_keys=(2, 3)):
+    """A seeded random set of MDs: each MD holds equality on n_keys of the
+    key columns, one string similarity (edit distance or 3-gram Jaccard) and
+    often |a-b| <= delta on a numeric column or a second edit distance."""
+    lib = _load()
+    mds = []
+    for m in range(n_mds):
+        r = lambda k: lib.syn_mix(seed, m * 97 + k)
+        keys = list(key_cols)
+        nk = n_keys[0] + int(r(0) % (n_keys[1] - n_keys[0] + 1))
+        chosen = []
+        for k in range(min(nk, len(keys))):
+            chosen.append(keys.pop(int(r(1 + k) % len(keys))))
+        preds = [eq(c) for c in sorted(chosen)]
+        col = str_cols[int(r(30) % len(str_cols))]
+        if r(20) % 2 == 0:
+            preds.append(ed(col, 1 + int(r(40) % 3)))
+        else:
+            num, den = ((1, 2), (3, 5), (7, 10), (4, 5), (9, 10))[int(r(40) % 5)]
+            preds.append(jac(col, num, den))
+        if r(50) % 3 != 0:
+            preds.append(absdiff(num_cols[int(r(60) % len(num_cols))], (0.1, 0.5, 1.0, 2.0, 5.0)[int(r(70) % 5)]))
+        if r(80) % 2 == 0:
+            other = [c for c in str_cols if c != col] or str_cols
+            oc = other[int(r(90) % len(other))]
+            if r(85) % 2 == 0:
+                preds.append(ed(oc, 1 + int(r(95) % 3)))
+            else:
+                num, den = ((1, 2), (3, 5), (7, 10), (4, 5), (9, 10))[int(r(95) % 5)]
+                preds.append(jac(oc, num, den))
+        mds.append(preds)
+    return mds
