@@ -927,6 +927,24 @@ EvalParams make_params(hb_ctx *c, const uint32_t *rec_r, const uint32_t *rec_s, 
     for (int m = 0; m < (int)c->md_preds.size(); m++)
         for (int k = (int)c->ops.size() - 1; k >= 0; k--)
             if (c->ops[k].need & (1ull << m)) P.first_op[m] = (int8_t)k;
+    for (int m = 0; m < (int)c->md_preds.size(); m++) {
+        uint64_t base = 0;
+        for (int j = 0; j < (int)c->md_preds.size(); j++)
+            if ((c->eqset[j] & ~c->eqset[m]) == 0) base |= 1ull << j;
+        P.base_alive[m] = base;
+        int nb = 0;
+        bool filterable = (base & c->eqonly) == 0;
+        for (int j = 0; j < (int)c->md_preds.size() && filterable; j++) {
+            if (!(base & (1ull << j))) continue;
+            const int f = P.first_op[j];
+            bool seen = false;
+            for (int i = 0; i < nb; i++) seen |= P.base_op[m][i] == f;
+            if (seen) continue;
+            if (nb == 4) filterable = false;
+            else P.base_op[m][nb++] = (uint8_t)f;
+        }
+        P.base_nops[m] = filterable ? (uint8_t)nb : 255;
+    }
     P.self_join = self ? 1 : 0;
     P.n_md = (int)c->md_preds.size();
     P.use_lut = c->lut.empty() ? 0 : 1;

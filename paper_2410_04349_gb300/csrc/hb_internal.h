@@ -77,6 +77,12 @@ struct EvalParams {
     uint64_t eqonly;        // MDs without any non-equality predicate
     uint16_t eqset[MAX_MD]; // equality keys of each MD (bit e = key e)
     int8_t first_op[MAX_MD];// first program op of each MD (-1: none)
+    // per MD m: the MDs alive for every pair of m's blocks (equality keys a
+    // subset of m's) and the distinct first ops of those MDs; base_nops 255 =
+    // no phase-1 filter (an MD without non-equality predicates, or > 4 ops)
+    uint64_t base_alive[MAX_MD];
+    uint8_t base_nops[MAX_MD];
+    uint8_t base_op[MAX_MD][4];
     int32_t HW;             // hot-record words (multiple of 4): keys, then one filter word per feature group
     const uint32_t *hot_r;
     const uint32_t *hot_s;

@@ -12,9 +12,10 @@
 //        present code of key e; the MDs whose keys are all in E are alive;
 //      - owner check: the pair is handled only in the block of the lowest
 //        alive MD, so each pair is evaluated once however many blocks hold it;
-//      - the cheap necessary condition of the first predicate of every alive
-//        MD (length / size filter, or the |a-b| test itself) rejects most
-//        pairs at once: a pair survives if some alive MD passes it;
+//      - when the alive MDs are exactly those alive in every pair of the
+//        block, the cheap necessary condition of each one's first predicate
+//        (length / size filter, or the |a-b| test itself) rejects most pairs
+//        at once: a pair survives if one of them passes;
 //    the remaining pairs are compacted into a per-warp survivor list (ballot).
 //  phase 2 (survivors, 32 at a time, all lanes busy): the sequential execution
 //    path of Section 5.1 on the full records: non-equality predicates in plan
@@ -363,7 +364,9 @@ __global__ void __launch_bounds__(EV_THREADS) k_eval(const __grid_constant__ Eva
             const uint64_t mbit = 1ull << m;
             const uint64_t below = mbit - 1ull;
             const uint32_t okeys = allkeys & ~(uint32_t)P.eqset[m];
-            const int f0 = P.first_op[m];
+            const uint64_t base = P.base_alive[m];
+            const int nbase = P.base_nops[m];
+            const Op op0 = P.ops[(nbase != 255 && nbase > 0) ? P.base_op[m][0] : 0];
             // ---- stage the hot records of the tile's rows and columns
             __syncwarp();
 #pragma unroll
@@ -399,6 +402,7 @@ __global__ void __launch_bounds__(EV_THREADS) k_eval(const __grid_constant__ Eva
             __syncwarp();
             // ---- phase 1: every pair of the tile
             int cnt = 0;
+            exam += diag ? (unsigned long long)nr * (nr - 1) / 2 : (unsigned long long)nr * nc;
 #pragma unroll
             for (int rr = 0; rr < R; rr++) {
                 const int r = rr * 32 + lane;
@@ -415,21 +419,15 @@ __global__ void __launch_bounds__(EV_THREADS) k_eval(const __grid_constant__ Eva
                     }
                     const uint64_t alive = alive_of(P, lut, E);
                     const bool own = v && (alive & mbit) && !(alive & below);
-                    // reject the pair when the first predicate of every alive MD
-                    // fails its necessary condition (no MD can be witnessed)
+                    // the MDs alive for every pair of this block (the owner and those
+                    // whose keys are a subset of its keys): when no other MD is alive,
+                    // reject the pair if the first predicate of each of them fails its
+                    // necessary condition; any other pair goes to phase 2 as it is
                     bool keep = own;
-                    if (!LOG && own && !(alive & P.eqonly)) {
-                        if (alive == mbit) {
-                            keep = first_filter(P.ops[f0], hr, hc);
-                        } else {
-                            keep = false;
-                            for (uint64_t rem = alive; rem && !keep; rem &= rem - 1) {
-                                const int f = P.first_op[__ffsll((long long)rem) - 1];
-                                keep = f < 0 || first_filter(P.ops[f], hr, hc);
-                            }
-                        }
+                    if (!LOG && own && alive == base && nbase != 255) {
+                        keep = first_filter(op0, hr, hc);
+                        for (int i = 1; i < nbase; i++) keep |= first_filter(P.ops[P.base_op[m][i]], hr, hc);
                     }
-                    exam += __popc(__ballot_sync(0xffffffffu, v));
                     cand += __popc(__ballot_sync(0xffffffffu, own));
                     const unsigned km = __ballot_sync(0xffffffffu, keep);
                     if (keep) surv[cnt + __popc(km & lt)] = (uint16_t)((r << 6) | c);
