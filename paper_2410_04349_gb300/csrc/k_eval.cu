@@ -314,6 +314,13 @@ __device__ __forceinline__ bool first_filter(const Op &op, const uint32_t *hr, c
     return fabsf(__uint_as_float(x) - __uint_as_float(y)) <= op.delta;
 }
 
+__device__ __forceinline__ bool first_filter_xy(const Op &op, uint32_t x, uint32_t y) {
+    if (op.kind == OP_ED) return x != NULL_LEN && y != NULL_LEN && (x > y ? x - y : y - x) <= op.k;
+    if (op.kind == OP_JAC)
+        return x != NULL_LEN && y != NULL_LEN && (uint64_t)min(x, y) * op.den >= (uint64_t)op.num * max(x, y);
+    return fabsf(__uint_as_float(x) - __uint_as_float(y)) <= op.delta;
+}
+
 template <int R, bool LOG>
 __global__ void __launch_bounds__(EV_THREADS) k_eval(const __grid_constant__ EvalParams P) {
     extern __shared__ __align__(16) uint32_t smem[];
@@ -403,35 +410,89 @@ __global__ void __launch_bounds__(EV_THREADS) k_eval(const __grid_constant__ Eva
             // ---- phase 1: every pair of the tile
             int cnt = 0;
             exam += diag ? (unsigned long long)nr * (nr - 1) / 2 : (unsigned long long)nr * nc;
+            // The equality keys of the owner MD hold for every pair of its block;
+            // only the other keys (okeys) vary.  With at most 4 of them, lane l
+            // works out, for the l-th combination of other-key matches, whether
+            // the owner check passes and whether exactly the block's base MDs are
+            // alive; each pair then reads its answer from two bit masks.
+            const int ko = __popc(okeys);
+            int okey[4] = {0, 0, 0, 0};
+            {
+                uint32_t ok = okeys;
+#pragma unroll
+                for (int i = 0; i < 4; i++) {
+                    if (ok) {
+                        okey[i] = __ffs(ok) - 1;
+                        ok &= ok - 1;
+                    }
+                }
+            }
+            uint32_t ownmask = 0, basemask = 0;
+            if (ko <= 4) {
+                uint32_t E = P.eqset[m];
+#pragma unroll
+                for (int i = 0; i < 4; i++)
+                    if (i < ko && ((lane >> i) & 1)) E |= 1u << okey[i];
+                const bool in = lane < (1 << ko);
+                const uint64_t al = in ? alive_of(P, lut, E) : 0ull;
+                ownmask = __ballot_sync(0xffffffffu, in && (al & mbit) && !(al & below));
+                basemask = __ballot_sync(0xffffffffu, in && al == base);
+            }
+            const bool filt = !LOG && nbase != 255;
 #pragma unroll
             for (int rr = 0; rr < R; rr++) {
                 const int r = rr * 32 + lane;
                 const bool rv = r < nr;
                 const uint32_t *hr = hrows + r * HWP;
-                for (int c = 0; c < nc; c++) {
-                    const uint32_t *hc = hcols + c * HWP;
-                    const bool v = rv && (!diag || c > r);
-                    uint32_t E = P.eqset[m];
-                    for (uint32_t ok = okeys; ok; ok &= ok - 1) {
-                        const int e = __ffs(ok) - 1;
-                        const uint32_t x = hr[e];
-                        E |= (x == hc[e] && x < NOMATCH_CODE) ? (1u << e) : 0u;
+                if (ko <= 4) {
+                    uint32_t rk[4];
+#pragma unroll
+                    for (int i = 0; i < 4; i++) rk[i] = i < ko ? hr[okey[i]] : 0u;
+                    const uint32_t x0 = hr[op0.hot];
+                    for (int c = 0; c < nc; c++) {
+                        const uint32_t *hc = hcols + c * HWP;
+                        const bool v = rv && (!diag || c > r);
+                        uint32_t combo = 0;
+#pragma unroll
+                        for (int i = 0; i < 4; i++)
+                            if (i < ko) combo |= (rk[i] == hc[okey[i]] && rk[i] < NOMATCH_CODE) ? (1u << i) : 0u;
+                        const bool own = v && ((ownmask >> combo) & 1u);
+                        // the MDs alive for every pair of this block (the owner and those
+                        // whose keys are a subset of its keys): when no other MD is alive,
+                        // reject the pair if the first predicate of each of them fails its
+                        // necessary condition; any other pair goes to phase 2 as it is
+                        bool keep = own;
+                        if (filt && own && ((basemask >> combo) & 1u)) {
+                            keep = first_filter_xy(op0, x0, hc[op0.hot]);
+                            for (int i = 1; i < nbase; i++) keep |= first_filter(P.ops[P.base_op[m][i]], hr, hc);
+                        }
+                        cand += __popc(__ballot_sync(0xffffffffu, own));
+                        const unsigned km = __ballot_sync(0xffffffffu, keep);
+                        if (keep) surv[cnt + __popc(km & lt)] = (uint16_t)((r << 6) | c);
+                        cnt += __popc(km);
                     }
-                    const uint64_t alive = alive_of(P, lut, E);
-                    const bool own = v && (alive & mbit) && !(alive & below);
-                    // the MDs alive for every pair of this block (the owner and those
-                    // whose keys are a subset of its keys): when no other MD is alive,
-                    // reject the pair if the first predicate of each of them fails its
-                    // necessary condition; any other pair goes to phase 2 as it is
-                    bool keep = own;
-                    if (!LOG && own && alive == base && nbase != 255) {
-                        keep = first_filter(op0, hr, hc);
-                        for (int i = 1; i < nbase; i++) keep |= first_filter(P.ops[P.base_op[m][i]], hr, hc);
+                } else {
+                    for (int c = 0; c < nc; c++) {
+                        const uint32_t *hc = hcols + c * HWP;
+                        const bool v = rv && (!diag || c > r);
+                        uint32_t E = P.eqset[m];
+                        for (uint32_t ok = okeys; ok; ok &= ok - 1) {
+                            const int e = __ffs(ok) - 1;
+                            const uint32_t x = hr[e];
+                            E |= (x == hc[e] && x < NOMATCH_CODE) ? (1u << e) : 0u;
+                        }
+                        const uint64_t alive = alive_of(P, lut, E);
+                        const bool own = v && (alive & mbit) && !(alive & below);
+                        bool keep = own;
+                        if (filt && own && alive == base) {
+                            keep = first_filter(op0, hr, hc);
+                            for (int i = 1; i < nbase; i++) keep |= first_filter(P.ops[P.base_op[m][i]], hr, hc);
+                        }
+                        cand += __popc(__ballot_sync(0xffffffffu, own));
+                        const unsigned km = __ballot_sync(0xffffffffu, keep);
+                        if (keep) surv[cnt + __popc(km & lt)] = (uint16_t)((r << 6) | c);
+                        cnt += __popc(km);
                     }
-                    cand += __popc(__ballot_sync(0xffffffffu, own));
-                    const unsigned km = __ballot_sync(0xffffffffu, keep);
-                    if (keep) surv[cnt + __popc(km & lt)] = (uint16_t)((r << 6) | c);
-                    cnt += __popc(km);
                 }
             }
             __syncwarp();
