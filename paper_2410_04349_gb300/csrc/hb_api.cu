@@ -660,6 +660,13 @@ static hb_status finish_plan(hb_ctx *c, int mode, const std::vector<double> &sp,
         }
         c->ops.push_back(op);
     }
+    // hot record: the equality codes, then one filter operand per feature group
+    // (length, gram count or value) - what phase 1 of the evaluation reads
+    c->hot_map.clear();
+    for (int e = 0; e < c->n_eq_total; e++) c->hot_map.push_back(e);
+    for (size_t g = 0; g < c->groups.size(); g++) c->hot_map.push_back(c->groups[g].word);
+    while (c->hot_map.size() % 4) c->hot_map.push_back(-1);
+    c->HW = (int)c->hot_map.size();
     hb_plan_info &I = c->info;
     memset(&I, 0, sizeof(I));
     I.mode = mode;
@@ -751,7 +758,18 @@ __global__ void k_job_codes(const int64_t *job_rows, int n_jobs, int64_t n, uint
 
 hb_status encode_side(hb_ctx *c, int side) {
     SideData &S = c->side[side];
-    if (S.encoded) return HB_OK;
+    if (S.encoded && S.hot_map == c->hot_map) return HB_OK;
+    if (S.encoded) {
+        // a new plan staged other filter operands: repack the hot records only
+        if (S.hot) cudaFreeAsync(S.hot, c->stream);
+        void *q = nullptr;
+        HB_TRY(dmalloc(c, &q, sizeof(uint32_t) * (size_t)c->HW * (size_t)(S.n > 0 ? S.n : 1) + 64));
+        S.hot = static_cast<uint32_t *>(q);
+        hot_pack(S.rec, c->W, S.n, S.hot, c->HW, c->hot_map.data(), c->stream);
+        S.hot_map = c->hot_map;
+        HB_CUDA(cudaGetLastError());
+        return HB_OK;
+    }
     const int64_t n = S.n;
     const int W = c->W;
     void *p = nullptr;
@@ -823,12 +841,10 @@ hb_status encode_side(hb_ctx *c, int side) {
         free_buf(c, jr);
     }
     {
-        std::vector<int32_t> map(c->HW, -1);
-        for (int e = 0; e < c->n_eq_total; e++) map[e] = e;
-        for (size_t g = 0; g < c->groups.size(); g++) map[c->n_eq_total + g] = c->groups[g].word;
         HB_TRY(dmalloc(c, &p, sizeof(uint32_t) * (size_t)c->HW * (size_t)(n > 0 ? n : 1) + 64));
         S.hot = static_cast<uint32_t *>(p);
-        hot_pack(S.rec, W, n, S.hot, c->HW, map.data(), c->stream);
+        hot_pack(S.rec, W, n, S.hot, c->HW, c->hot_map.data(), c->stream);
+        S.hot_map = c->hot_map;
         HB_CUDA(cudaGetLastError());
     }
     S.encoded = true;

@@ -64,7 +64,8 @@ struct SideData {
     std::vector<void *> allocs;
     // encoded state
     uint32_t *rec = nullptr;
-    uint32_t *hot = nullptr;   // per tuple: equality codes + one filter word per feature group
+    uint32_t *hot = nullptr;   // per tuple: equality codes + one filter word per feature group (+ bin counts)
+    std::vector<int32_t> hot_map;   // layout the hot records were packed with
     std::vector<uint32_t *> grams;   // per feature group (JAC only)
     bool encoded = false;
 };
@@ -97,6 +98,7 @@ struct hb_ctx {
     std::vector<FeatGroup> groups;
     int W = 4;
     int HW = 4;
+    std::vector<int32_t> hot_map;   // hot word -> record word (-1: zero)
     int n_eq_total = 0;            // eqkeys + job key
     std::vector<uint16_t> eqset;
     std::vector<int> active;       // MDs whose blocks can own pairs

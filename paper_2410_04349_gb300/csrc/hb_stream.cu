@@ -106,10 +106,7 @@ static hb_status encode_chunk(hb_ctx *c, SideData &S, unsigned int *too_long, Bu
             jac_features_impl(col, G.q, S.rec, W, G.word, S.grams[g], c->w_jac.p, too_long, c->n_sm, c->stream);
         }
     }
-    std::vector<int32_t> map(c->HW, -1);
-    for (int e = 0; e < c->n_eq_total; e++) map[e] = e;
-    for (size_t g = 0; g < c->groups.size(); g++) map[c->n_eq_total + g] = c->groups[g].word;
-    hot_pack(S.rec, W, n, S.hot, c->HW, map.data(), c->stream);
+    hot_pack(S.rec, W, n, S.hot, c->HW, c->hot_map.data(), c->stream);
     HB_CUDA(cudaGetLastError());
     return HB_OK;
 }

@@ -466,7 +466,7 @@ __global__ void __launch_bounds__(EV_THREADS) k_eval(const __grid_constant__ Eva
                             keep = first_filter_xy(op0, x0, hc[op0.hot]);
                             for (int i = 1; i < nbase; i++) keep |= first_filter(P.ops[P.base_op[m][i]], hr, hc);
                         }
-                        cand += __popc(__ballot_sync(0xffffffffu, own));
+                        cand += own ? 1u : 0u;
                         const unsigned km = __ballot_sync(0xffffffffu, keep);
                         if (keep) surv[cnt + __popc(km & lt)] = (uint16_t)((r << 6) | c);
                         cnt += __popc(km);
@@ -488,7 +488,7 @@ __global__ void __launch_bounds__(EV_THREADS) k_eval(const __grid_constant__ Eva
                             keep = first_filter(op0, hr, hc);
                             for (int i = 1; i < nbase; i++) keep |= first_filter(P.ops[P.base_op[m][i]], hr, hc);
                         }
-                        cand += __popc(__ballot_sync(0xffffffffu, own));
+                        cand += own ? 1u : 0u;
                         const unsigned km = __ballot_sync(0xffffffffu, keep);
                         if (keep) surv[cnt + __popc(km & lt)] = (uint16_t)((r << 6) | c);
                         cnt += __popc(km);
@@ -536,6 +536,7 @@ __global__ void __launch_bounds__(EV_THREADS) k_eval(const __grid_constant__ Eva
             }
         }
     }
+    for (int o = 16; o > 0; o >>= 1) cand += __shfl_xor_sync(0xffffffffu, cand, o);
     if (lane == 0 && cand) atomicAdd(P.cand_count, cand);
     if (lane == 0 && exam) atomicAdd(P.exam_count, exam);
     if (LOG) {
