@@ -549,38 +549,6 @@ static hb_status plan_stats(hb_ctx *c, std::vector<double> &sp, std::vector<doub
             mlen /= cnt;
             mg /= cnt;
         }
-        {   // sampled value statistics kept for the learned cost model's features
-            std::vector<double> Ls, Gs;
-            int nulls = 0;
-            for (int s = 0; s < n_keep; s++) {
-                uint32_t L = h[(size_t)P * K + P + (size_t)p * n_keep + s];
-                uint32_t G = h[(size_t)P * K + P + (size_t)P * n_keep + (size_t)p * n_keep + s];
-                if (L == NULL_LEN) {
-                    nulls++;
-                    continue;
-                }
-                Ls.push_back(L);
-                Gs.push_back(G);
-            }
-            std::vector<float> st(10, 0.f);
-            if (!Ls.empty()) {
-                std::sort(Ls.begin(), Ls.end());
-                double m = 0, v = 0, gm = 0, gv = 0;
-                for (double x : Ls) m += x;
-                m /= Ls.size();
-                for (double x : Ls) v += (x - m) * (x - m);
-                for (double x : Gs) gm += x;
-                gm /= Gs.size();
-                for (double x : Gs) gv += (x - gm) * (x - gm);
-                auto q = [&](double f) { return Ls[std::min(Ls.size() - 1, (size_t)(f * (Ls.size() - 1) + 0.5))]; };
-                st = {(float)m, (float)std::sqrt(v / Ls.size()), (float)q(0.1), (float)q(0.5), (float)q(0.9),
-                      (float)Ls.back(), (float)gm, (float)std::sqrt(gv / Gs.size()), 0.f, 0.f};
-            }
-            st[8] = n_keep ? (float)nulls / (float)n_keep : 0.f;
-            st[9] = (float)sd[p];
-            if ((int)c->pred_stats.size() != P) c->pred_stats.assign(P, std::vector<float>(10, 0.f));
-            c->pred_stats[p] = st;
-        }
         switch (q.kind) {
         case HB_P_EQ:
         case HB_P_EQ_PREFIX: cost[p] = 1.0; break;
@@ -589,6 +557,14 @@ static hb_status plan_stats(hb_ctx *c, std::vector<double> &sp, std::vector<doub
         case HB_P_JACCARD_GE: cost[p] = 6.0 + 2.0 * mg; break;
         }
     }
+    // the sampled lengths / gram counts stay for the learned cost model's
+    // features, which are summarised only when asked for (ensure_pred_stats)
+    c->stat_keep = n_keep;
+    c->stat_lens.assign(h.begin() + (size_t)P * K + P, h.begin() + (size_t)P * K + P + (size_t)P * n_keep);
+    c->stat_grams.assign(h.begin() + (size_t)P * K + P + (size_t)P * n_keep,
+                         h.begin() + (size_t)P * K + P + 2 * (size_t)P * n_keep);
+    c->stat_sd = sd;
+    c->pred_stats.clear();
     double mx = 0, mc = 0;
     for (int p = 0; p < P; p++) {
         mx = std::max(mx, sd[p]);
@@ -601,6 +577,44 @@ static hb_status plan_stats(hb_ctx *c, std::vector<double> &sp, std::vector<doub
     c->plain_sp = sp;
     c->plain_cost = cost;
     return HB_OK;
+}
+
+void ensure_pred_stats(hb_ctx *c) {
+    const int P = (int)c->preds.size();
+    const int n_keep = c->stat_keep;
+    if ((int)c->pred_stats.size() == P || (int)c->stat_sd.size() != P) return;
+    c->pred_stats.assign(P, std::vector<float>(10, 0.f));
+    for (int p = 0; p < P; p++) {
+        std::vector<double> Ls, Gs;
+        int nulls = 0;
+        for (int s = 0; s < n_keep; s++) {
+            const uint32_t L = c->stat_lens[(size_t)p * n_keep + s];
+            const uint32_t G = c->stat_grams[(size_t)p * n_keep + s];
+            if (L == NULL_LEN) {
+                nulls++;
+                continue;
+            }
+            Ls.push_back(L);
+            Gs.push_back(G);
+        }
+        std::vector<float> st(10, 0.f);
+        if (!Ls.empty()) {
+            std::sort(Ls.begin(), Ls.end());
+            double m = 0, v = 0, gm = 0, gv = 0;
+            for (double x : Ls) m += x;
+            m /= Ls.size();
+            for (double x : Ls) v += (x - m) * (x - m);
+            for (double x : Gs) gm += x;
+            gm /= Gs.size();
+            for (double x : Gs) gv += (x - gm) * (x - gm);
+            auto q = [&](double f) { return Ls[std::min(Ls.size() - 1, (size_t)(f * (Ls.size() - 1) + 0.5))]; };
+            st = {(float)m, (float)std::sqrt(v / Ls.size()), (float)q(0.1), (float)q(0.5), (float)q(0.9),
+                  (float)Ls.back(), (float)gm, (float)std::sqrt(gv / Gs.size()), 0.f, 0.f};
+        }
+        st[8] = n_keep ? (float)nulls / (float)n_keep : 0.f;
+        st[9] = (float)c->stat_sd[p];
+        c->pred_stats[p] = st;
+    }
 }
 
 static hb_status finish_plan(hb_ctx *c, int mode, const std::vector<double> &sp, const std::vector<double> &cost) {
@@ -660,13 +674,29 @@ static hb_status finish_plan(hb_ctx *c, int mode, const std::vector<double> &sp,
         }
         c->ops.push_back(op);
     }
-    // hot record: the equality codes, then one filter operand per feature group
-    // (length, gram count or value) - what phase 1 of the evaluation reads
+    // hot record (what phase 1 of the evaluation reads from shared memory for
+    // every pair): the equality codes, then the filter operand (length, gram
+    // count or value) of each MD's first program predicate
     c->hot_map.clear();
     for (int e = 0; e < c->n_eq_total; e++) c->hot_map.push_back(e);
-    for (size_t g = 0; g < c->groups.size(); g++) c->hot_map.push_back(c->groups[g].word);
+    std::vector<int> hot_word(c->groups.size(), -1);
+    for (int m = 0; m < n_md; m++) {
+        for (size_t k = 0; k < c->ops.size(); k++) {
+            if (!(c->ops[k].need & (1ull << m))) continue;
+            const int g = c->preds[program[k]].group;
+            if (hot_word[g] < 0) {
+                hot_word[g] = (int)c->hot_map.size();
+                c->hot_map.push_back(c->groups[g].word);
+            }
+            break;
+        }
+    }
     while (c->hot_map.size() % 4) c->hot_map.push_back(-1);
     c->HW = (int)c->hot_map.size();
+    for (size_t k = 0; k < c->ops.size(); k++) {
+        const int g = c->preds[program[k]].group;
+        c->ops[k].hot = hot_word[g] < 0 ? 255 : (uint8_t)hot_word[g];
+    }
     hb_plan_info &I = c->info;
     memset(&I, 0, sizeof(I));
     I.mode = mode;

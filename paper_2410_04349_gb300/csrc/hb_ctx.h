@@ -136,8 +136,12 @@ struct hb_ctx {
     std::vector<std::pair<std::vector<int64_t>, std::pair<int, int>>> tune_cache;
     int claim = 2;
     // planner statistics kept for the learned model: per predicate [len mean, len std, p10, p50, p90, max,
-    // gram mean, gram std, null fraction, LSH bucket stddev]
+    // gram mean, gram std, null fraction, LSH bucket stddev], summarised on demand (ensure_pred_stats)
+    // from the sampled lengths / gram counts ([predicate][stat_keep]) and bucket deviations
     std::vector<std::vector<float>> pred_stats;
+    std::vector<uint32_t> stat_lens, stat_grams;
+    std::vector<double> stat_sd;
+    int stat_keep = 0;
     std::vector<double> plain_sp, plain_cost;
     long long graph_kernels = 0;   // kernels in the captured batch graph
     // results
@@ -181,6 +185,8 @@ void free_buf(hb_ctx *c, Buf &b);
 hb_status dmalloc(hb_ctx *c, void **p, size_t bytes);
 hb_status upload(hb_ctx *c, void *dst, const void *src, size_t bytes);
 hb_status do_plan(hb_ctx *c, int mode, bool job_key);
+// summarise the sampled predicate statistics for the learned cost model's features
+void ensure_pred_stats(hb_ctx *c);
 hb_status encode_side(hb_ctx *c, int side);
 hb_status ensure_ready(hb_ctx *c, bool job_key);
 bool is_self(hb_ctx *c);

@@ -43,7 +43,7 @@ struct Op {
     uint8_t kind;
     uint8_t feat;       // first record word of this predicate's feature group
     uint8_t k;          // ED threshold
-    uint8_t hot;        // hot-record word holding this predicate's filter operand
+    uint8_t hot;        // hot-record word holding this predicate's filter operand (255: not staged)
     uint32_t num, den;  // Jaccard threshold
     float delta;        // |a-b| threshold
     uint32_t pad2;
@@ -83,7 +83,7 @@ struct EvalParams {
     uint64_t base_alive[MAX_MD];
     uint8_t base_nops[MAX_MD];
     uint8_t base_op[MAX_MD][4];
-    int32_t HW;             // hot-record words (multiple of 4): keys, then one filter word per feature group
+    int32_t HW;             // hot-record words (multiple of 4): keys, then first-predicate filter operands
     const uint32_t *hot_r;
     const uint32_t *hot_s;
     Op ops[MAX_OPS];

@@ -147,6 +147,7 @@ hb_status predicate_features(hb_ctx *c, std::vector<float> &F) {
     HB_TRY(st);
     std::vector<int> op_of(P, -1);
     for (size_t k = 0; k < c->program.size(); k++) op_of[c->program[k]] = (int)k;
+    ensure_pred_stats(c);
     for (int p = 0; p < P; p++) {
         float *f = &F[(size_t)p * HB_FEATURES];
         const hb_predicate &q = c->preds[p].p;

@@ -6,8 +6,9 @@
 // Each warp works on one tile at a time in two phases:
 //
 //  phase 1 (every pair, branch-light): the warp stages the tile's "hot"
-//    records (equality codes and one filter operand per predicate column) in
-//    shared memory; lane = row, loop over columns.  For every pair:
+//    records (equality codes and the filter operand of each MD's first
+//    predicate) in shared memory, rows tuple-major and columns word-major;
+//    lane = row, loop over the columns 8 at a time.  For every pair:
 //      - equality keys: bit e of E is set when both tuples hold the same
 //        present code of key e; the MDs whose keys are all in E are alive;
 //      - owner check: the pair is handled only in the block of the lowest
@@ -16,7 +17,10 @@
 //        block, the cheap necessary condition of each one's first predicate
 //        (length / size filter, or the |a-b| test itself) rejects most pairs
 //        at once: a pair survives if one of them passes;
-//    the remaining pairs are compacted into a per-warp survivor list (ballot).
+//    the owner / keep decisions come from per-tile bit masks indexed by the
+//    combination of other-key matches, and the filter is a per-row interval
+//    test; each lane collects its kept columns in a bit mask, and one warp
+//    prefix sum per tile turns the masks into a per-warp survivor list.
 //  phase 2 (survivors, 32 at a time, all lanes busy): the sequential execution
 //    path of Section 5.1 on the full records: non-equality predicates in plan
 //    order, each evaluated once per pair and its result applied to every MD
@@ -25,6 +29,8 @@
 //    compacted with a warp ballot and one atomic.
 #include <cuda_runtime.h>
 #include <stdint.h>
+
+#include <type_traits>
 
 #include "hb_internal.h"
 
@@ -305,26 +311,136 @@ __device__ __forceinline__ uint64_t alive_of(const EvalParams &P, const uint64_t
 }
 
 // the cheap necessary condition of a predicate on the staged filter operands
-// (length filter of edit distance, size filter of Jaccard, |a-b| <= delta itself)
-__device__ __forceinline__ bool first_filter(const Op &op, const uint32_t *hr, const uint32_t *hc) {
-    const uint32_t x = hr[op.hot], y = hc[op.hot];
+// (length filter of edit distance, size filter of Jaccard, |a-b| <= delta
+// itself); word w of the column record is hc[w * cs]
+__device__ __forceinline__ bool first_filter(const Op &op, const uint32_t *hr, const uint32_t *hc, int cs) {
+    const uint32_t x = hr[op.hot], y = hc[op.hot * cs];
     if (op.kind == OP_ED) return x != NULL_LEN && y != NULL_LEN && (x > y ? x - y : y - x) <= op.k;
     if (op.kind == OP_JAC)
         return x != NULL_LEN && y != NULL_LEN && (uint64_t)min(x, y) * op.den >= (uint64_t)op.num * max(x, y);
     return fabsf(__uint_as_float(x) - __uint_as_float(y)) <= op.delta;
 }
 
-__device__ __forceinline__ bool first_filter_xy(const Op &op, uint32_t x, uint32_t y) {
-    if (op.kind == OP_ED) return x != NULL_LEN && y != NULL_LEN && (x > y ? x - y : y - x) <= op.k;
-    if (op.kind == OP_JAC)
-        return x != NULL_LEN && y != NULL_LEN && (uint64_t)min(x, y) * op.den >= (uint64_t)op.num * max(x, y);
-    return fabsf(__uint_as_float(x) - __uint_as_float(y)) <= op.delta;
+// phase-1 filter forms of one tile
+enum : int { F_NONE = 0, F_RANGE = 1, F_ABS = 2 };
+
+__device__ __forceinline__ int pop(uint32_t x) { return __popc(x); }
+__device__ __forceinline__ int pop(uint64_t x) { return __popcll(x); }
+__device__ __forceinline__ int first_bit(uint32_t x) { return __ffs(x) - 1; }
+__device__ __forceinline__ int first_bit(uint64_t x) { return __ffsll((long long)x) - 1; }
+
+// columns c of row r that form a pair of the tile: c < nc, and c > r on a
+// diagonal tile of a self-join
+template <typename Mask>
+__device__ __forceinline__ Mask valid_cols(int r, int nr, int nc, bool diag) {
+    constexpr int BITS = 8 * (int)sizeof(Mask);
+    if (r >= nr) return 0;
+    Mask v = nc >= BITS ? ~(Mask)0 : (((Mask)1 << nc) - (Mask)1);
+    if (diag) v &= ~((((Mask)2) << r) - (Mask)1);
+    return v;
+}
+
+// The length filter of edit distance (|x - y| <= k) and the size filter of
+// Jaccard (min(x,y) * den >= num * max(x,y)) both hold exactly for y in an
+// interval [lo, hi] around the row's operand x: y passes iff y - lo <= hi - lo
+// in unsigned arithmetic (a missing y, 0xFFFFFFFF, never does since hi stays
+// below it).  x itself must be present.
+__device__ __forceinline__ void filter_range(const Op &op, uint32_t x, uint32_t &lo, uint32_t &span) {
+    uint64_t l, h;
+    if (op.kind == OP_ED) {
+        l = x >= op.k ? x - op.k : 0u;
+        h = (uint64_t)x + op.k;
+    } else {
+        // l = ceil(num * x / den), h = floor(x * den / num): a float estimate,
+        // then exact integer correction
+        const uint64_t a = (uint64_t)op.num * x, b = (uint64_t)op.den * x;
+        const float ratio = (float)op.num / (float)op.den;
+        uint64_t q = (uint64_t)fmaxf((float)x * ratio - 2.0f, 0.0f);
+        while (q * op.den < a) q++;
+        while (q > 0 && (q - 1) * op.den >= a) q--;
+        l = q;
+        if (op.num == 0) {
+            h = 0xFFFFFFFEull;
+        } else {
+            const float est = (float)x / ratio;
+            if (est > 8.0e9f) {   // above 2^32 whatever the rounding: the cap below applies
+                h = 0xFFFFFFFEull;
+            } else {
+                uint64_t e = (uint64_t)fmaxf(est - 2.0f, 0.0f);
+                while ((e + 1) * op.num <= b) e++;
+                while (e > 0 && e * op.num > b) e--;
+                h = e;
+            }
+        }
+    }
+    if (h > 0xFFFFFFFEull) h = 0xFFFFFFFEull;
+    lo = (uint32_t)l;
+    span = (uint32_t)(h - l);
+}
+
+// Phase 1 of one row (lane) of a tile with KO (<= 3) varying equality keys
+// and filter form FK.  For the pair's combination of other-key matches,
+// t = pk >> combo holds: bit 0 = keep if the filter passes, bit 8 = keep if
+// it fails, bit 16 = owned (pkn: the same for a row whose operand is missing,
+// which no filter passes).  Columns are visited 8 at a time (the tile's
+// column count is a multiple of 8; columns past nc are masked by the caller).
+template <int KO, int FK, int T, typename Mask>
+__device__ __forceinline__ void p1_row(const uint32_t *__restrict__ hr, const uint32_t *__restrict__ hcols, int nc,
+                                       const int *okey, const Op &op0, uint32_t pk, uint32_t pkn, Mask &km_out,
+                                       Mask &om_out) {
+    uint32_t rk[KO > 0 ? KO : 1];
+    const uint32_t *ck[KO > 0 ? KO : 1];
+#pragma unroll
+    for (int i = 0; i < KO; i++) {
+        const uint32_t x = hr[okey[i]];
+        rk[i] = x < NOMATCH_CODE ? x : 0xFFFFFFFDu;   // a missing code matches no column code
+        ck[i] = hcols + okey[i] * T;
+    }
+    const uint32_t *cf = FK != F_NONE ? hcols + op0.hot * T : hcols;
+    uint32_t lo = 0, span = 0;
+    float xf = 0.f;
+    const float dl = op0.delta;
+    if (FK == F_RANGE) {
+        const uint32_t x = hr[op0.hot];
+        if (x == NULL_LEN) pk = pkn;
+        else filter_range(op0, x, lo, span);
+    }
+    if (FK == F_ABS) xf = __uint_as_float(hr[op0.hot]);
+    Mask km = 0, om = 0;
+    for (int c0 = 0; c0 < nc; c0 += 8) {
+        uint32_t kc = 0, oc = 0;
+#pragma unroll
+        for (int u = 0; u < 8; u++) {
+            const int c = c0 + u;
+            uint32_t t;
+            if (KO == 0) {
+                t = pk;
+            } else if (KO == 1) {
+                t = ck[0][c] == rk[0] ? (pk >> 1) : pk;
+            } else {
+                uint32_t combo = 0;
+#pragma unroll
+                for (int i = 0; i < KO; i++) combo |= ck[i][c] == rk[i] ? (1u << i) : 0u;
+                t = pk >> combo;
+            }
+            bool fl = true;
+            if (FK == F_RANGE) fl = cf[c] - lo <= span;
+            if (FK == F_ABS) fl = fabsf(xf - __uint_as_float(cf[c])) <= dl;
+            if (t & (fl ? 1u : 0x100u)) kc |= 1u << u;
+            if (t & 0x10000u) oc |= 1u << u;
+        }
+        km |= (Mask)kc << c0;
+        om |= (Mask)oc << c0;
+    }
+    km_out = km;
+    om_out = om;
 }
 
 template <int R, bool LOG>
 __global__ void __launch_bounds__(EV_THREADS) k_eval(const __grid_constant__ EvalParams P) {
     extern __shared__ __align__(16) uint32_t smem[];
     constexpr int T = 32 * R;
+    using Mask = typename std::conditional<(R == 2), uint64_t, uint32_t>::type;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int HW = P.HW, HWP = P.HW + 1, W = P.W;
     uint64_t *lut = reinterpret_cast<uint64_t *>(smem);
@@ -396,19 +512,19 @@ __global__ void __launch_bounds__(EV_THREADS) k_eval(const __grid_constant__ Eva
                     const uint32_t id = P.members_s[B.start_s + c0 + r];
                     cid_s[r] = id;
                     const uint4 *src = reinterpret_cast<const uint4 *>(hot_c + (size_t)id * HW);
-                    uint32_t *dst = hcols + r * HWP;
+                    uint32_t *dst = hcols + r;   // word-major: word w of column c at w * T + c
                     for (int w4 = 0; w4 < (HW >> 2); w4++) {
                         const uint4 v = __ldg(src + w4);
-                        dst[4 * w4 + 0] = v.x;
-                        dst[4 * w4 + 1] = v.y;
-                        dst[4 * w4 + 2] = v.z;
-                        dst[4 * w4 + 3] = v.w;
+                        dst[(4 * w4 + 0) * T] = v.x;
+                        dst[(4 * w4 + 1) * T] = v.y;
+                        dst[(4 * w4 + 2) * T] = v.z;
+                        dst[(4 * w4 + 3) * T] = v.w;
                     }
                 }
             }
             __syncwarp();
-            // ---- phase 1: every pair of the tile
-            int cnt = 0;
+            // ---- phase 1: every pair of the tile; lane = row, loop over the
+            // columns; each lane collects the kept columns of its rows in a bit mask
             exam += diag ? (unsigned long long)nr * (nr - 1) / 2 : (unsigned long long)nr * nc;
             // The equality keys of the owner MD hold for every pair of its block;
             // only the other keys (okeys) vary.  With at most 4 of them, lane l
@@ -438,60 +554,110 @@ __global__ void __launch_bounds__(EV_THREADS) k_eval(const __grid_constant__ Eva
                 ownmask = __ballot_sync(0xffffffffu, in && (al & mbit) && !(al & below));
                 basemask = __ballot_sync(0xffffffffu, in && al == base);
             }
+            // the MDs alive for every pair of this block (the owner and those whose
+            // keys are a subset of its keys): when no other MD is alive, a pair is
+            // rejected if the first predicate of each of them fails its necessary
+            // condition; any other owned pair goes on as it is
             const bool filt = !LOG && nbase != 255;
+            Mask kmask[R];
+            // fast path: at most 3 varying keys and at most one filter
+            const bool fast = ko <= 3 && (!filt || nbase == 1);
+            if (fast) {
+                const uint32_t own8 = ownmask & 0xffu;
+                const uint32_t kfail = filt ? (own8 & ~basemask) : own8;
+                const uint32_t pk = own8 | (kfail << 8) | (own8 << 16);
+                const uint32_t pkn = kfail | (kfail << 8) | (own8 << 16);
+                const int fk = !filt ? F_NONE : op0.kind == OP_ABS ? F_ABS : F_RANGE;
+                const bool ownc = own8 == 0u || own8 == (1u << (1 << ko)) - 1u;   // owned alike for every combination
 #pragma unroll
-            for (int rr = 0; rr < R; rr++) {
-                const int r = rr * 32 + lane;
-                const bool rv = r < nr;
-                const uint32_t *hr = hrows + r * HWP;
-                if (ko <= 4) {
-                    uint32_t rk[4];
-#pragma unroll
-                    for (int i = 0; i < 4; i++) rk[i] = i < ko ? hr[okey[i]] : 0u;
-                    const uint32_t x0 = hr[op0.hot];
-                    for (int c = 0; c < nc; c++) {
-                        const uint32_t *hc = hcols + c * HWP;
-                        const bool v = rv && (!diag || c > r);
-                        uint32_t combo = 0;
-#pragma unroll
-                        for (int i = 0; i < 4; i++)
-                            if (i < ko) combo |= (rk[i] == hc[okey[i]] && rk[i] < NOMATCH_CODE) ? (1u << i) : 0u;
-                        const bool own = v && ((ownmask >> combo) & 1u);
-                        // the MDs alive for every pair of this block (the owner and those
-                        // whose keys are a subset of its keys): when no other MD is alive,
-                        // reject the pair if the first predicate of each of them fails its
-                        // necessary condition; any other pair goes to phase 2 as it is
-                        bool keep = own;
-                        if (filt && own && ((basemask >> combo) & 1u)) {
-                            keep = first_filter_xy(op0, x0, hc[op0.hot]);
-                            for (int i = 1; i < nbase; i++) keep |= first_filter(P.ops[P.base_op[m][i]], hr, hc);
-                        }
-                        cand += own ? 1u : 0u;
-                        const unsigned km = __ballot_sync(0xffffffffu, keep);
-                        if (keep) surv[cnt + __popc(km & lt)] = (uint16_t)((r << 6) | c);
-                        cnt += __popc(km);
+                for (int rr = 0; rr < R; rr++) {
+                    const int r = rr * 32 + lane;
+                    Mask km = 0, om = 0;
+                    const uint32_t *hr = hrows + r * HWP;
+                    switch (ko * 3 + fk) {
+                    case 0: p1_row<0, F_NONE, T>(hr, hcols, nc, okey, op0, pk, pkn, km, om); break;
+                    case 1: p1_row<0, F_RANGE, T>(hr, hcols, nc, okey, op0, pk, pkn, km, om); break;
+                    case 2: p1_row<0, F_ABS, T>(hr, hcols, nc, okey, op0, pk, pkn, km, om); break;
+                    case 3: p1_row<1, F_NONE, T>(hr, hcols, nc, okey, op0, pk, pkn, km, om); break;
+                    case 4: p1_row<1, F_RANGE, T>(hr, hcols, nc, okey, op0, pk, pkn, km, om); break;
+                    case 5: p1_row<1, F_ABS, T>(hr, hcols, nc, okey, op0, pk, pkn, km, om); break;
+                    case 6: p1_row<2, F_NONE, T>(hr, hcols, nc, okey, op0, pk, pkn, km, om); break;
+                    case 7: p1_row<2, F_RANGE, T>(hr, hcols, nc, okey, op0, pk, pkn, km, om); break;
+                    case 8: p1_row<2, F_ABS, T>(hr, hcols, nc, okey, op0, pk, pkn, km, om); break;
+                    case 9: p1_row<3, F_NONE, T>(hr, hcols, nc, okey, op0, pk, pkn, km, om); break;
+                    case 10: p1_row<3, F_RANGE, T>(hr, hcols, nc, okey, op0, pk, pkn, km, om); break;
+                    default: p1_row<3, F_ABS, T>(hr, hcols, nc, okey, op0, pk, pkn, km, om); break;
                     }
-                } else {
+                    const Mask vm = valid_cols<Mask>(r, nr, nc, diag);
+                    kmask[rr] = km & vm;
+                    cand += ownc ? (own8 ? (unsigned)pop(vm) : 0u) : (unsigned)pop(om & vm);
+                }
+            } else {
+#pragma unroll
+                for (int rr = 0; rr < R; rr++) {
+                    const int r = rr * 32 + lane;
+                    const uint32_t *hr = hrows + r * HWP;
+                    const Mask vm = valid_cols<Mask>(r, nr, nc, diag);
+                    Mask km = 0;
                     for (int c = 0; c < nc; c++) {
-                        const uint32_t *hc = hcols + c * HWP;
-                        const bool v = rv && (!diag || c > r);
-                        uint32_t E = P.eqset[m];
-                        for (uint32_t ok = okeys; ok; ok &= ok - 1) {
-                            const int e = __ffs(ok) - 1;
-                            const uint32_t x = hr[e];
-                            E |= (x == hc[e] && x < NOMATCH_CODE) ? (1u << e) : 0u;
+                        const uint32_t *hc = hcols + c;
+                        bool own, isbase;
+                        if (ko <= 4) {
+                            uint32_t combo = 0;
+#pragma unroll
+                            for (int i = 0; i < 4; i++)
+                                if (i < ko) {
+                                    const uint32_t x = hr[okey[i]];
+                                    combo |= (x == hc[okey[i] * T] && x < NOMATCH_CODE) ? (1u << i) : 0u;
+                                }
+                            own = (ownmask >> combo) & 1u;
+                            isbase = (basemask >> combo) & 1u;
+                        } else {
+                            uint32_t E = P.eqset[m];
+                            for (uint32_t ok = okeys; ok; ok &= ok - 1) {
+                                const int e = __ffs(ok) - 1;
+                                const uint32_t x = hr[e];
+                                E |= (x == hc[e * T] && x < NOMATCH_CODE) ? (1u << e) : 0u;
+                            }
+                            const uint64_t alive = alive_of(P, lut, E);
+                            own = (alive & mbit) && !(alive & below);
+                            isbase = alive == base;
                         }
-                        const uint64_t alive = alive_of(P, lut, E);
-                        const bool own = v && (alive & mbit) && !(alive & below);
                         bool keep = own;
-                        if (filt && own && alive == base) {
-                            keep = first_filter(op0, hr, hc);
-                            for (int i = 1; i < nbase; i++) keep |= first_filter(P.ops[P.base_op[m][i]], hr, hc);
+                        if (filt && own && isbase) {
+                            keep = false;
+                            for (int i = 0; i < nbase && !keep; i++) keep = first_filter(P.ops[P.base_op[m][i]], hr, hc, T);
                         }
-                        cand += own ? 1u : 0u;
-                        const unsigned km = __ballot_sync(0xffffffffu, keep);
-                        if (keep) surv[cnt + __popc(km & lt)] = (uint16_t)((r << 6) | c);
-                        cnt += __popc(km);
+                        const Mask bit = (Mask)1 << c;
+                        if (keep) km |= bit;
+                        if (own && (vm & bit)) cand++;
+                    }
+                    kmask[rr] = km & vm;
+                }
+            }
+            // survivors: a warp prefix sum of the per-lane counts places each
+            // lane's kept pairs in the warp's survivor list
+            int cnt;
+            {
+                int my = 0;
+#pragma unroll
+                for (int rr = 0; rr < R; rr++) my += pop(kmask[rr]);
+                int incl = my;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int v = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o) incl += v;
+                }
+                cnt = __shfl_sync(0xffffffffu, incl, 31);
+                int pos = incl - my;
+#pragma unroll
+                for (int rr = 0; rr < R; rr++) {
+                    Mask mk = kmask[rr];
+                    const uint32_t rb = (uint32_t)(rr * 32 + lane) << 6;
+                    while (mk) {
+                        const int c = first_bit(mk);
+                        mk &= mk - 1;
+                        surv[pos++] = (uint16_t)(rb | (uint32_t)c);
                     }
                 }
             }
@@ -506,12 +672,12 @@ __global__ void __launch_bounds__(EV_THREADS) k_eval(const __grid_constant__ Eva
                     const int r = (int)(e16 >> 6), c = (int)(e16 & 63u);
                     ra = rid_s[r];
                     cb = cid_s[c];
-                    const uint32_t *hr = hrows + r * HWP, *hc = hcols + c * HWP;
+                    const uint32_t *hr = hrows + r * HWP, *hc = hcols + c;
                     uint32_t E = P.eqset[m];
                     for (uint32_t ok = okeys; ok; ok &= ok - 1) {
                         const int e = __ffs(ok) - 1;
                         const uint32_t x = hr[e];
-                        E |= (x == hc[e] && x < NOMATCH_CODE) ? (1u << e) : 0u;
+                        E |= (x == hc[e * T] && x < NOMATCH_CODE) ? (1u << e) : 0u;
                     }
                     const uint64_t alive = alive_of(P, lut, E);
                     hit = run_program<LOG>(P, alive, P.rec_r + (size_t)ra * W, rec_c + (size_t)cb * W, lg);
