@@ -192,11 +192,65 @@ constexpr int QG_SHORT = 64;       // grams per string handled by one thread
 constexpr int QG_THREADS = 128;
 constexpr int QG_LONG_MAX = 8192;  // grams per string handled by one block
 
-__global__ void k_gram_counts(const uint32_t *off, const uint8_t *valid, int64_t n, int q, uint32_t *cnt) {
+// Strings are handed to the sorting threads in order of their gram count
+// (buckets 0..64, one more for longer strings), so that the threads of a warp
+// sort lists of one length: the insertion sort's cost is then the average, not
+// the warp's longest string.  The order only affects speed: every string
+// writes its own output slot.
+constexpr int QG_BUCKETS = 66;
+
+__device__ __forceinline__ uint32_t gram_bucket(uint32_t g) { return g < 65u ? g : 65u; }
+
+__global__ void k_gram_counts(const uint32_t *off, const uint8_t *valid, int64_t n, int q, uint32_t *cnt,
+                              uint32_t *bucket_count) {
+    __shared__ uint32_t h[QG_BUCKETS];
+    for (int t = threadIdx.x; t < QG_BUCKETS; t += blockDim.x) h[t] = 0;
+    __syncthreads();
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    uint32_t len = off[i + 1] - off[i];
-    cnt[i] = (valid && !valid[i]) ? 0u : (len >= (uint32_t)q ? len - (uint32_t)q + 1u : 0u);
+    if (i < n) {
+        uint32_t len = off[i + 1] - off[i];
+        const uint32_t g = (valid && !valid[i]) ? 0u : (len >= (uint32_t)q ? len - (uint32_t)q + 1u : 0u);
+        cnt[i] = g;
+        atomicAdd(&h[gram_bucket(g)], 1u);
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < QG_BUCKETS; t += blockDim.x)
+        if (h[t]) atomicAdd(&bucket_count[t], h[t]);
+}
+
+// exclusive scan of the bucket counts (one warp)
+__global__ void k_bucket_scan(const uint32_t *bucket_count, uint32_t *bucket_cursor) {
+    const int lane = threadIdx.x;
+    uint32_t carry = 0;
+    for (int b0 = 0; b0 < QG_BUCKETS; b0 += 32) {
+        const int b = b0 + lane;
+        const uint32_t v = b < QG_BUCKETS ? bucket_count[b] : 0u;
+        uint32_t incl = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t u = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += u;
+        }
+        if (b < QG_BUCKETS) bucket_cursor[b] = carry + incl - v;
+        carry += __shfl_sync(0xffffffffu, incl, 31);
+    }
+}
+
+// order[bucket start + rank] = string: a block reserves one range per bucket
+__global__ void k_bucket_scatter(const uint32_t *cnt, int64_t n, uint32_t *bucket_cursor, uint32_t *order) {
+    __shared__ uint32_t h[QG_BUCKETS], base[QG_BUCKETS];
+    for (int t = threadIdx.x; t < QG_BUCKETS; t += blockDim.x) h[t] = 0;
+    __syncthreads();
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    uint32_t b = 0, rank = 0;
+    if (i < n) {
+        b = gram_bucket(cnt[i]);
+        rank = atomicAdd(&h[b], 1u);
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < QG_BUCKETS; t += blockDim.x)
+        base[t] = h[t] ? atomicAdd(&bucket_cursor[t], h[t]) : 0u;
+    __syncthreads();
+    if (i < n) order[base[b] + rank] = (uint32_t)i;
 }
 
 __device__ void write_gram_feature(uint32_t *r, uint32_t ucount, uint32_t start, const uint32_t *g) {
@@ -217,12 +271,13 @@ __device__ void write_gram_feature(uint32_t *r, uint32_t ucount, uint32_t start,
 // (insertion sort), removes duplicates and writes them at the string's slot.
 __global__ void __launch_bounds__(QG_THREADS) k_grams_short(const uint8_t *bytes, const uint32_t *off,
                                                            const uint8_t *valid, int64_t n, int q,
-                                                           const uint32_t *gstart, uint32_t *grams, uint32_t *rec,
-                                                           int W, int feat, uint32_t *long_list,
-                                                           unsigned int *n_long) {
+                                                           const uint32_t *order, const uint32_t *gstart,
+                                                           uint32_t *grams, uint32_t *rec, int W, int feat,
+                                                           uint32_t *long_list, unsigned int *n_long) {
     __shared__ uint32_t buf[QG_SHORT][QG_THREADS];
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    const int64_t i = order[t];
     uint32_t *r = rec + i * W + feat;
     if (valid && !valid[i]) {
         r[0] = NULL_LEN;
@@ -239,8 +294,14 @@ __global__ void __launch_bounds__(QG_THREADS) k_grams_short(const uint8_t *bytes
     }
     const uint8_t *p = bytes + a;
     uint32_t *s = &buf[0][threadIdx.x];
+    // rolling window: the gram at k is bytes k .. k+q-1, packed big-endian
+    const uint32_t gmask = q >= 4 ? 0xFFFFFFFFu : ((1u << (8 * q)) - 1u);
+    uint32_t win = 0;
+    if (g > 0)
+        for (int t0 = 0; t0 < q - 1; t0++) win = (win << 8) | p[t0];
     for (uint32_t k = 0; k < g; k++) {
-        uint32_t x = gram_at(p, k, q);
+        win = ((win << 8) | p[k + q - 1]) & gmask;
+        const uint32_t x = win;
         uint32_t j = k;
         while (j > 0 && s[(j - 1) * QG_THREADS] > x) {
             s[j * QG_THREADS] = s[(j - 1) * QG_THREADS];
@@ -391,7 +452,7 @@ void abs_feature(const DevCol &c, uint32_t *rec, int W, int feat, cudaStream_t s
 }
 
 size_t jac_scratch_bytes(int64_t n) {
-    return (size_t)(n + 1) * 4 * 3 + scan_tmp_bytes(n) + 4096;
+    return (size_t)(n + 1) * 4 * 4 + 2 * QG_BUCKETS * 4 + scan_tmp_bytes(n) + 4096;
 }
 
 // scratch: jac_scratch_bytes(n); grams: capacity >= nbytes of the column (one gram per byte at most)
@@ -402,15 +463,20 @@ void jac_features_impl(const DevCol &c, int q, uint32_t *rec, int W, int feat, u
     uint32_t *cnt = static_cast<uint32_t *>(scratch);
     uint32_t *gstart = cnt + (n + 1);
     uint32_t *long_list = gstart + (n + 1);
-    unsigned int *n_long = reinterpret_cast<unsigned int *>(long_list + (n + 1));
+    uint32_t *order = long_list + (n + 1);
+    uint32_t *bucket_count = order + (n + 1);
+    uint32_t *bucket_cursor = bucket_count + QG_BUCKETS;
+    unsigned int *n_long = bucket_cursor + QG_BUCKETS;
     void *stmp = reinterpret_cast<void *>((reinterpret_cast<uintptr_t>(n_long + 4) + 255) & ~uintptr_t(255));
-    cudaMemsetAsync(n_long, 0, sizeof(unsigned int), s);
-    HB_LAUNCHED(1);
-    k_gram_counts<<<blocks_for(n, ENC_THREADS), ENC_THREADS, 0, s>>>(c.off, c.valid, n, q, cnt);
+    // n_long and the bucket counts are zeroed together
+    cudaMemsetAsync(bucket_count, 0, sizeof(uint32_t) * (2 * QG_BUCKETS + 1), s);
+    HB_LAUNCHED(4);
+    k_gram_counts<<<blocks_for(n, ENC_THREADS), ENC_THREADS, 0, s>>>(c.off, c.valid, n, q, cnt, bucket_count);
+    k_bucket_scan<<<1, 32, 0, s>>>(bucket_count, bucket_cursor);
+    k_bucket_scatter<<<blocks_for(n, ENC_THREADS), ENC_THREADS, 0, s>>>(cnt, n, bucket_cursor, order);
     scan_exclusive_u32(cnt, gstart, n, nullptr, stmp, 0, s);
-    HB_LAUNCHED(1);
-    k_grams_short<<<blocks_for(n, QG_THREADS), QG_THREADS, 0, s>>>(c.bytes, c.off, c.valid, n, q, gstart, grams, rec,
-                                                                  W, feat, long_list, n_long);
+    k_grams_short<<<blocks_for(n, QG_THREADS), QG_THREADS, 0, s>>>(c.bytes, c.off, c.valid, n, q, order, gstart,
+                                                                  grams, rec, W, feat, long_list, n_long);
     HB_LAUNCHED(1);
     k_grams_long<<<(unsigned)(n_sm * 4), 256, 0, s>>>(c.bytes, c.off, q, gstart, grams, rec, W, feat, long_list,
                                                       n_long, too_long);
