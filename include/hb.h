@@ -157,10 +157,12 @@ HB_API const char *hb_version(void);
 
 /*
  * Load relation `side` (0 = R, 1 = S; a self-join loads only R) of n_rows rows
- * and n_cols columns.  on_device = 0: pointers are host memory, copied through
- * pinned staging chunks of chunk_bytes; on_device = 1: pointers are device
- * memory of this context's device, copied device to device.  Replaces any
- * previous table of that side.
+ * and n_cols columns.  on_device = 0: pointers are host memory; a page-locked
+ * array (cudaMallocHost / cudaHostRegister) is copied by one DMA, a pageable
+ * one through pinned staging chunks of chunk_bytes; on_device = 1: pointers
+ * are device memory of this context's device, copied device to device.  The
+ * call returns once every host array has been read.  Replaces any previous
+ * table of that side.
  */
 HB_API hb_status hb_load_table(hb_ctx *ctx, int32_t side, int64_t n_rows, int32_t n_cols, const hb_column *cols,
                         int32_t on_device);

@@ -13,6 +13,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <array>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -109,9 +110,15 @@ hb_status dmalloc(hb_ctx *c, void **p, size_t bytes) {
     return HB_OK;
 }
 
-static hb_status ensure_pinned(hb_ctx *c) {
-    size_t want = c->opt.chunk_bytes ? c->opt.chunk_bytes : (256ull << 20);
-    if (c->pin_bytes == want) return HB_OK;
+bool page_locked(const void *p) {
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, p) == cudaSuccess && at.type == cudaMemoryTypeHost) return true;
+    cudaGetLastError();
+    return false;
+}
+
+hb_status ensure_pinned(hb_ctx *c, size_t want) {
+    if (c->pin_bytes >= want) return HB_OK;
     for (int b = 0; b < 2; b++) {
         if (c->pin[b]) {
             cudaEventSynchronize(c->pin_ev[b]);
@@ -127,11 +134,18 @@ static hb_status ensure_pinned(hb_ctx *c) {
     return HB_OK;
 }
 
-// host -> device through the two pinned chunks: the copy of chunk i into
-// pinned memory overlaps the DMA of chunk i-1.
+// host -> device.  A page-locked source (cudaMallocHost / cudaHostRegister)
+// is copied by one DMA; the caller waits for it (sync_direct) before its
+// buffer may change.  Pageable memory goes through the two pinned chunks: the
+// copy of chunk i into pinned memory overlaps the DMA of chunk i-1.
 hb_status upload(hb_ctx *c, void *dst, const void *src, size_t bytes) {
     if (bytes == 0) return HB_OK;
-    HB_TRY(ensure_pinned(c));
+    if (page_locked(src)) {
+        HB_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, c->stream));
+        c->direct_pending = true;
+        return HB_OK;
+    }
+    HB_TRY(ensure_pinned(c, c->opt.chunk_bytes ? c->opt.chunk_bytes : (256ull << 20)));
     size_t off = 0;
     int i = 0;
     while (off < bytes) {
@@ -144,6 +158,13 @@ hb_status upload(hb_ctx *c, void *dst, const void *src, size_t bytes) {
         off += len;
         i++;
     }
+    return HB_OK;
+}
+
+hb_status sync_direct(hb_ctx *c) {
+    if (!c->direct_pending) return HB_OK;
+    c->direct_pending = false;
+    HB_CUDA(cudaStreamSynchronize(c->stream));
     return HB_OK;
 }
 
@@ -209,8 +230,18 @@ extern "C" void hb_destroy(hb_ctx *c) {
     Buf *bufs[] = {&c->w_table, &c->w_slot_r, &c->w_slot_s, &c->w_count_r, &c->w_count_s, &c->w_start_r,
                    &c->w_start_s, &c->w_cursor, &c->w_members_r, &c->w_members_s, &c->w_blocks, &c->w_tiles,
                    &c->w_prefix, &c->w_scan, &c->w_out, &c->w_alt, &c->w_sort, &c->w_pairs, &c->w_counters,
-                   &c->w_lut, &c->w_log, &c->w_jac, &c->w_jobrows, &c->w_jobcount, &c->w_joboff};
+                   &c->w_lut, &c->w_log, &c->w_jac, &c->w_jobrows, &c->w_jobcount, &c->w_joboff,
+                   &c->w_small, &c->w_small_meta};
     for (Buf *b : bufs) free_buf(c, *b);
+    for (int b = 0; b < 2; b++) {
+        free_buf(c, c->w_chunk[b]);
+        if (c->chunk_copied[b]) cudaEventDestroy(c->chunk_copied[b]);
+        if (c->chunk_consumed[b]) cudaEventDestroy(c->chunk_consumed[b]);
+    }
+    if (c->copy_stream) {
+        cudaStreamSynchronize(c->copy_stream);
+        cudaStreamDestroy(c->copy_stream);
+    }
     if (c->batch_exec) cudaGraphExecDestroy(c->batch_exec);
     if (c->batch_graph) cudaGraphDestroy(c->batch_graph);
     cudaStreamSynchronize(c->stream);
@@ -239,7 +270,10 @@ extern "C" hb_status hb_load_table(hb_ctx *c, int32_t side, int64_t n_rows, int3
             if (!col.offsets) return fail(HB_ERR_ARG, "hb_load_table: string column " + std::to_string(k) + " has no offsets");
             if (!on_device) {
                 if (col.offsets[0] != 0) return fail(HB_ERR_ARG, "hb_load_table: offsets[0] must be 0");
-                for (int64_t i = 0; i < n_rows; i++)
+                // branch-free scan first (vectorises); the row is located only on failure
+                uint32_t dec = 0;
+                for (int64_t i = 0; i < n_rows; i++) dec |= col.offsets[i + 1] < col.offsets[i] ? 1u : 0u;
+                for (int64_t i = 0; dec && i < n_rows; i++)
                     if (col.offsets[i + 1] < col.offsets[i])
                         return fail(HB_ERR_ARG, "hb_load_table: offsets of column " + std::to_string(k) + " decrease at row " + std::to_string(i));
                 if ((uint64_t)col.offsets[n_rows] != col.data_bytes)
@@ -282,6 +316,7 @@ extern "C" hb_status hb_load_table(hb_ctx *c, int32_t side, int64_t n_rows, int3
             HB_TRY(copy_in(c, d.valid, col.valid, (size_t)n_rows, on_device));
         }
     }
+    HB_TRY(sync_direct(c));
     if (side == 0) c->stats.n_rows_r = n_rows;
     else c->stats.n_rows_s = n_rows;
     return HB_OK;
@@ -674,28 +709,52 @@ static hb_status finish_plan(hb_ctx *c, int mode, const std::vector<double> &sp,
         }
         c->ops.push_back(op);
     }
-    // hot record (what phase 1 of the evaluation reads from shared memory for
-    // every pair): the equality codes, then the filter operand (length, gram
-    // count or value) of each MD's first program predicate
+    // hot record: keys, first-op filter operands, then within HOT_BUDGET the
+    // bins of first ops, second-op filter operands and their bins
     c->hot_map.clear();
     for (int e = 0; e < c->n_eq_total; e++) c->hot_map.push_back(e);
-    std::vector<int> hot_word(c->groups.size(), -1);
+    std::vector<int> hot_word(c->groups.size(), -1), hot_bins(c->groups.size(), -1);
+    std::vector<std::array<int, 2>> mdops(n_md, std::array<int, 2>{-1, -1});
     for (int m = 0; m < n_md; m++) {
-        for (size_t k = 0; k < c->ops.size(); k++) {
-            if (!(c->ops[k].need & (1ull << m))) continue;
-            const int g = c->preds[program[k]].group;
-            if (hot_word[g] < 0) {
-                hot_word[g] = (int)c->hot_map.size();
-                c->hot_map.push_back(c->groups[g].word);
-            }
-            break;
+        int n = 0;
+        for (size_t k = 0; k < c->ops.size() && n < 2; k++)
+            if (c->ops[k].need & (1ull << m)) mdops[m][n++] = (int)k;
+    }
+    auto group_of = [&](int k) { return c->preds[program[k]].group; };
+    for (int m = 0; m < n_md; m++) {
+        if (mdops[m][0] < 0) continue;
+        const int g = group_of(mdops[m][0]);
+        if (hot_word[g] < 0) {
+            hot_word[g] = (int)c->hot_map.size();
+            c->hot_map.push_back(c->groups[g].word);
         }
     }
+    auto add_bins = [&](int k) {
+        const int g = group_of(k);
+        const FeatGroup &G = c->groups[g];
+        const int nb = G.kind == OP_ED ? 4 : G.kind == OP_JAC ? 8 : 0;
+        if (nb == 0 || hot_word[g] < 0 || hot_bins[g] >= 0 || (int)c->hot_map.size() + nb > HOT_BUDGET) return;
+        hot_bins[g] = (int)c->hot_map.size();
+        for (int w = 0; w < nb; w++) c->hot_map.push_back(G.word + 2 + w);
+    };
+    for (int m = 0; m < n_md; m++)
+        if (mdops[m][0] >= 0) add_bins(mdops[m][0]);
+    for (int m = 0; m < n_md; m++) {
+        if (mdops[m][1] < 0) continue;
+        const int g = group_of(mdops[m][1]);
+        if (hot_word[g] < 0 && (int)c->hot_map.size() + 1 <= HOT_BUDGET) {
+            hot_word[g] = (int)c->hot_map.size();
+            c->hot_map.push_back(c->groups[g].word);
+        }
+    }
+    for (int m = 0; m < n_md; m++)
+        if (mdops[m][1] >= 0) add_bins(mdops[m][1]);
     while (c->hot_map.size() % 4) c->hot_map.push_back(-1);
     c->HW = (int)c->hot_map.size();
     for (size_t k = 0; k < c->ops.size(); k++) {
-        const int g = c->preds[program[k]].group;
+        const int g = group_of((int)k);
         c->ops[k].hot = hot_word[g] < 0 ? 255 : (uint8_t)hot_word[g];
+        c->ops[k].hot2 = hot_bins[g] < 0 ? 255 : (uint8_t)hot_bins[g];
     }
     hb_plan_info &I = c->info;
     memset(&I, 0, sizeof(I));
@@ -914,6 +973,12 @@ hb_status build_blocks(hb_ctx *c, const uint32_t *rec_r, int64_t n_r, const uint
     HB_TRY(grow(c, c->w_scan, std::max(scan_tmp_bytes((int64_t)H + 1), scan_tmp_bytes((int64_t)bc + 1))));
     uint32_t *n_blocks = reinterpret_cast<uint32_t *>(ctr + 3);
     unsigned int *overflow = reinterpret_cast<unsigned int *>(ctr + 4);
+    uint32_t *n_packed = reinterpret_cast<uint32_t *>(ctr + 6);
+    if (self) {
+        HB_TRY(grow(c, c->w_small, sizeof(uint32_t) * (size_t)bc));
+        HB_TRY(grow(c, c->w_small_meta, sizeof(uint32_t) * SMALL_META_WORDS));
+        HB_CUDA(cudaMemsetAsync(c->w_small_meta.p, 0, sizeof(uint32_t) * SMALL_META_WORDS, c->stream));
+    }
     for (int a = 0; a < na; a++) {
         const int m = c->active[a];
         int32_t words[MAX_EQ];
@@ -930,10 +995,11 @@ hb_status build_blocks(hb_ctx *c, const uint32_t *rec_r, int64_t n_r, const uint
         scatter_slots(as<uint32_t>(c->w_slot_r), n_r, as<uint32_t>(c->w_start_r), as<uint32_t>(c->w_cursor), mem_r,
                       c->stream);
         if (self) {
-            emit_blocks(as<uint32_t>(c->w_count_r), as<uint32_t>(c->w_start_r), nullptr, nullptr, H, (uint32_t)m, 1,
-                        (uint32_t)((size_t)a * (size_t)std::max<int64_t>(n_r, 1)), 0, c->tile,
-                        as<BlockDesc>(c->w_blocks), as<uint64_t>(c->w_tiles), n_blocks, block_cap, overflow,
-                        c->stream);
+            emit_blocks_packed(as<uint32_t>(c->w_count_r), as<uint32_t>(c->w_start_r), H, (uint32_t)m,
+                               (uint32_t)((size_t)a * (size_t)std::max<int64_t>(n_r, 1)), c->tile,
+                               as<BlockDesc>(c->w_blocks), as<uint64_t>(c->w_tiles), n_blocks, n_packed, block_cap,
+                               overflow, as<uint32_t>(c->w_small_meta), as<uint32_t>(c->w_small), block_cap,
+                               reinterpret_cast<uint32_t *>(ctr + 7), c->n_sm, c->stream);
         } else {
             group_probe(rec_s, n_s, rec_r, W, words, nk, as<uint64_t>(c->w_table), H, as<uint32_t>(c->w_slot_s),
                         c->stream);
@@ -991,6 +1057,23 @@ EvalParams make_params(hb_ctx *c, const uint32_t *rec_r, const uint32_t *rec_s, 
         }
         P.base_nops[m] = filterable ? (uint8_t)nb : 255;
     }
+    P.multi = 0;
+    for (int m : c->active) P.multi |= (P.base_nops[m] >= 2 && P.base_nops[m] <= 4) ? 1 : 0;
+    memset(P.screen_op, 255, sizeof(P.screen_op));
+    P.refine = 0;
+    for (int m = 0; m < (int)c->md_preds.size(); m++) {
+        int n = 0;
+        for (size_t k = 0; k < c->ops.size() && n < 2; k++) {
+            if (!(c->ops[k].need & (1ull << m))) continue;
+            if (c->ops[k].hot != 255) {
+                P.screen_op[m][n] = (uint8_t)k;
+                // the screen adds to phase 1's filter only with a second
+                // predicate or with bins in the hot record
+                if (n == 1 || c->ops[k].hot2 != 255) P.refine = 1;
+            }
+            n++;
+        }
+    }
     P.self_join = self ? 1 : 0;
     P.n_md = (int)c->md_preds.size();
     P.use_lut = c->lut.empty() ? 0 : 1;
@@ -1015,6 +1098,7 @@ EvalParams make_params(hb_ctx *c, const uint32_t *rec_r, const uint32_t *rec_s, 
     P.lut = P.use_lut ? as<uint64_t>(c->w_lut) : nullptr;
     P.members_r = as<uint32_t>(c->w_members_r);
     P.members_s = self ? as<uint32_t>(c->w_members_r) : as<uint32_t>(c->w_members_s);
+    P.small = self ? as<uint32_t>(c->w_small) : nullptr;
     P.blocks = as<BlockDesc>(c->w_blocks);
     P.n_blocks = reinterpret_cast<const uint32_t *>(ctr + 3);
     P.tile_prefix = as<uint64_t>(c->w_prefix);
@@ -1065,7 +1149,7 @@ hb_status block_eval_sort(hb_ctx *c, const uint32_t *rec_r, int64_t n_r, const u
         P.profile = logging == 2 ? 1 : 0;   // 1: instrumented plan; 2: instrumented, no early exit
         HB_CUDA(launch_eval(P, grid, smem, logging ? 1 : 0, c->stream));
         if (tm && attempt == 0) tm->mark();
-        unsigned long long h[6];
+        unsigned long long h[8];
         HB_CUDA(cudaMemcpyAsync(h, ctr, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
         HB_CUDA(cudaStreamSynchronize(c->stream));
         if (h[4]) return fail(HB_ERR_INTERNAL, "block list overflow");
@@ -1073,6 +1157,7 @@ hb_status block_eval_sort(hb_ctx *c, const uint32_t *rec_r, int64_t n_r, const u
         res.cand = (int64_t)h[2];
         res.blocks = (int64_t)(uint32_t)h[3];
         res.examined = (int64_t)h[5];
+        res.real_blocks = res.blocks - (int64_t)(uint32_t)h[6] + (int64_t)(uint32_t)h[7];
         if (res.n_out <= c->out_cap) break;
         // the slab was too small: grow it to the exact count and evaluate again
         c->out_cap = res.n_out + res.n_out / 8 + 1024;
@@ -1146,7 +1231,7 @@ static hb_status run_block(hb_ctx *c, hb_pair **out, int64_t *n_out, bool to_hos
     S.candidate_pairs = res.cand;
     S.emitted_pairs = res.n_out;
     S.tiles = res.tiles;
-    S.blocks = res.blocks;
+    S.blocks = res.real_blocks;
     S.examined_pairs = res.examined;
     S.ms_encode = tm.ms(0, 1);
     S.ms_block_build = tm.ms(1, 2);

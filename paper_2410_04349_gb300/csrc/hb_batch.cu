@@ -286,7 +286,7 @@ extern "C" hb_status hb_block_batch(hb_ctx *c, int32_t n_jobs, const int64_t *jo
                 g_kernel_launches.fetch_sub(c->graph_kernels);
             }
         }
-        unsigned long long h[6];
+        unsigned long long h[8];
         HB_CUDA(cudaMemcpyAsync(h, c->w_counters.p, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
         HB_CUDA(cudaStreamSynchronize(c->stream));
         if (h[4]) return fail(HB_ERR_INTERNAL, "block list overflow");
@@ -317,7 +317,7 @@ extern "C" hb_status hb_block_batch(hb_ctx *c, int32_t n_jobs, const int64_t *jo
         c->stats.candidate_pairs = (int64_t)h[2];
         c->stats.examined_pairs = (int64_t)h[5];
         c->stats.emitted_pairs = n_out;
-        c->stats.blocks = (int64_t)(uint32_t)h[3];
+        c->stats.blocks = (int64_t)(uint32_t)h[3] - (int64_t)(uint32_t)h[6] + (int64_t)(uint32_t)h[7];
         c->stats.tile = c->tile;
         c->stats.ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - w0).count();
         return HB_OK;

@@ -124,6 +124,11 @@ struct hb_ctx {
     // pinned staging
     void *pin[2] = {nullptr, nullptr};
     cudaEvent_t pin_ev[2] = {nullptr, nullptr};
+    bool direct_pending = false;   // a DMA from the caller's page-locked memory is in flight
+    // streamed S chunks (hb_block_stream): device chunk buffers, copy stream, events
+    Buf w_chunk[2];
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t chunk_copied[2] = {nullptr, nullptr}, chunk_consumed[2] = {nullptr, nullptr};
     size_t pin_bytes = 0;
     // batched jobs: row offsets of the stacked jobs (hb_block_batch)
     std::vector<int64_t> job_rows;
@@ -132,6 +137,7 @@ struct hb_ctx {
     cudaGraphExec_t batch_exec = nullptr;
     std::vector<int64_t> batch_graph_key;
     Buf w_jobrows, w_jobcount, w_joboff;
+    Buf w_small, w_small_meta;   // member starts of packed small blocks, packing metadata
     // autotuner cache: job-size signature -> (tile, claim)
     std::vector<std::pair<std::vector<int64_t>, std::pair<int, int>>> tune_cache;
     int claim = 2;
@@ -156,8 +162,9 @@ struct RunResult {
     int64_t n_out = 0;
     int64_t cand = 0;
     int64_t tiles = 0;
-    int64_t blocks = 0;
+    int64_t blocks = 0;     // block descriptors (a packed one holds several small blocks)
     int64_t examined = 0;
+    int64_t real_blocks = 0;   // blocks, small ones counted one by one
 };
 
 struct Timer {
@@ -184,6 +191,12 @@ hb_status grow(hb_ctx *c, Buf &b, size_t bytes);
 void free_buf(hb_ctx *c, Buf &b);
 hb_status dmalloc(hb_ctx *c, void **p, size_t bytes);
 hb_status upload(hb_ctx *c, void *dst, const void *src, size_t bytes);
+// two pinned staging buffers of at least `bytes` each (c->pin)
+hb_status ensure_pinned(hb_ctx *c, size_t bytes);
+// true when p is page-locked host memory (cudaMallocHost / cudaHostRegister)
+bool page_locked(const void *p);
+// wait for the DMAs upload() issued from page-locked caller memory
+hb_status sync_direct(hb_ctx *c);
 hb_status do_plan(hb_ctx *c, int mode, bool job_key);
 // summarise the sampled predicate statistics for the learned cost model's features
 void ensure_pred_stats(hb_ctx *c);

@@ -24,6 +24,12 @@ constexpr int MAX_EQ = 16;     // distinct equality keys per context
 constexpr int MAX_OPS = 48;    // non-equality predicates in one program
 constexpr int MAX_MD = 64;
 constexpr int LUT_MAX_EQ = 10; // equality-match -> MD-mask lookup table up to 2^10 entries
+constexpr int SMALL_MAX = 16;  // self-join blocks of 2..SMALL_MAX tuples are packed several to a tile
+constexpr int SMALL_META_WORDS = 160;
+// hot-record words beyond which only the mandatory words (keys, first-predicate
+// filter operands) are staged: 12 keeps four 256-thread evaluation CTAs of
+// 32-tuple tiles resident per SM
+constexpr int HOT_BUDGET = 12;
 
 // ---- device-side column of one relation ----
 struct DevCol {
@@ -46,7 +52,8 @@ struct Op {
     uint8_t hot;        // hot-record word holding this predicate's filter operand (255: not staged)
     uint32_t num, den;  // Jaccard threshold
     float delta;        // |a-b| threshold
-    uint32_t pad2;
+    uint8_t hot2;       // first hot-record word of its character / gram bins (255: not staged)
+    uint8_t pad2[3];
     uint64_t need;      // MDs whose precondition holds this predicate
     uint64_t cp;        // MDs whose last remaining predicate is this one
 };
@@ -58,11 +65,11 @@ constexpr int FEAT_ABS_WORDS = 1;  // fp32 value bits (NaN when missing)
 
 struct BlockDesc {
     uint32_t md;
-    uint32_t n_r;       // members on the row side
-    uint32_t start_r;   // into members_r
+    uint32_t n_r;       // members on the row side (packed: blocks x size)
+    uint32_t start_r;   // into members_r (packed: into the small-block start list)
     uint32_t n_s;       // members on the column side (self-join: = n_r)
     uint32_t start_s;   // into members_s (self-join: = start_r)
-    uint32_t pad;
+    uint32_t packed;    // 0: one block; n: a packed tile of self-join blocks of n tuples each
 };
 
 struct EvalParams {
@@ -83,7 +90,13 @@ struct EvalParams {
     uint64_t base_alive[MAX_MD];
     uint8_t base_nops[MAX_MD];
     uint8_t base_op[MAX_MD][4];
-    int32_t HW;             // hot-record words (multiple of 4): keys, then first-predicate filter operands
+    // per MD: the (at most two) first program ops whose filter operand is in the
+    // hot record (255: none); refine = phase 1b screens the survivors with them
+    // (when some screen holds more than phase 1's filter) and batches phase 2
+    uint8_t screen_op[MAX_MD][2];
+    int32_t refine;
+    int32_t multi;          // some active MD's blocks have 2..4 distinct base filters
+    int32_t HW;             // hot-record words (multiple of 4): keys, filter operands, bins
     const uint32_t *hot_r;
     const uint32_t *hot_s;
     Op ops[MAX_OPS];
@@ -94,6 +107,7 @@ struct EvalParams {
     const uint64_t *lut;          // 2^n_eq MD masks (use_lut)
     const uint32_t *members_r;
     const uint32_t *members_s;
+    const uint32_t *small;        // member starts of packed small blocks
     const BlockDesc *blocks;
     const uint32_t *n_blocks;     // device count
     const uint64_t *tile_prefix;  // n_blocks + 1 entries
@@ -148,6 +162,12 @@ void emit_blocks(const uint32_t *count_r, const uint32_t *start_r, const uint32_
                  uint64_t cap, uint32_t md, int self_join, uint32_t member_base_r, uint32_t member_base_s, int tile,
                  BlockDesc *blocks, uint64_t *tiles, uint32_t *n_blocks, uint32_t block_cap, unsigned int *overflow,
                  cudaStream_t s);
+// self-join: blocks of more than SMALL_MAX tuples as emit_blocks; smaller ones
+// packed into tiles (start list `small`, metadata `small_meta`)
+void emit_blocks_packed(const uint32_t *count_r, const uint32_t *start_r, uint64_t cap, uint32_t md,
+                        uint32_t member_base_r, int tile, BlockDesc *blocks, uint64_t *tiles, uint32_t *n_blocks,
+                        uint32_t *n_packed, uint32_t block_cap, unsigned int *overflow, uint32_t *small_meta,
+                        uint32_t *small, uint32_t small_cap, uint32_t *small_total, int n_sm, cudaStream_t s);
 void clamp_blocks(uint32_t *n_blocks, uint32_t block_cap, cudaStream_t s);
 
 // k_eval.cu

@@ -3,8 +3,9 @@
 // Section 3 pipelines host-to-device transfer with device work so that the
 // transfer of one part overlaps the processing of another.  Here R is
 // resident and grouped once per MD; S arrives in chunks of at most
-// chunk_bytes: the chunk is packed into one of two pinned buffers and copied
-// on a copy stream while the previous chunk is encoded (dictionary codes
+// chunk_bytes, copied on a copy stream into one of two device buffers (straight
+// from page-locked caller memory, or packed into one of two pinned buffers
+// first) while the previous chunk is encoded (dictionary codes
 // looked up in R's dictionaries, string features), grouped against R's groups
 // and evaluated on the compute stream.  Pairs of all chunks accumulate in one
 // slab and are sorted once at the end.
@@ -79,6 +80,31 @@ void pack_chunk(const hb_column *cols, const std::vector<int> &need, int64_t r0,
     }
 }
 
+// the same chunk copied from page-locked caller memory, one DMA per array
+cudaError_t copy_chunk_direct(const hb_column *cols, const std::vector<int> &need, int64_t r0, int64_t r1,
+                              const std::vector<ChunkCol> &cc, uint8_t *dst, cudaStream_t s) {
+    (void)r1;
+    for (size_t i = 0; i < need.size(); i++) {
+        const hb_column &c = cols[need[i]];
+        const ChunkCol &k = cc[i];
+        cudaError_t e = cudaSuccess;
+        if (c.type == HB_COL_STRING) {
+            if (k.bytes_len)
+                e = cudaMemcpyAsync(dst + k.bytes_off, static_cast<const uint8_t *>(c.data) + c.offsets[r0],
+                                    k.bytes_len, cudaMemcpyHostToDevice, s);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(dst + k.off_off, c.offsets + r0, k.off_len, cudaMemcpyHostToDevice, s);
+        } else {
+            e = cudaMemcpyAsync(dst + k.vals_off, static_cast<const uint8_t *>(c.data) + 4 * (size_t)r0, k.vals_len,
+                                cudaMemcpyHostToDevice, s);
+        }
+        if (e == cudaSuccess && c.valid)
+            e = cudaMemcpyAsync(dst + k.valid_off, c.valid + r0, k.valid_len, cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
 }  // namespace
 
 // encoding of one S chunk, asynchronous (the Jaccard length flag is checked later)
@@ -127,8 +153,9 @@ extern "C" hb_status hb_block_stream(hb_ctx *c, int64_t n_rows_s, int32_t n_cols
         if (col.type < 0 || col.type > 2) return fail(HB_ERR_ARG, "hb_block_stream: unknown column type");
         if (col.type == HB_COL_STRING) {
             if (!col.offsets || col.offsets[0] != 0) return fail(HB_ERR_ARG, "hb_block_stream: bad string offsets");
-            for (int64_t i = 0; i < n_rows_s; i++)
-                if (col.offsets[i + 1] < col.offsets[i]) return fail(HB_ERR_ARG, "hb_block_stream: offsets decrease");
+            uint32_t dec = 0;   // branch-free (vectorises)
+            for (int64_t i = 0; i < n_rows_s; i++) dec |= col.offsets[i + 1] < col.offsets[i] ? 1u : 0u;
+            if (dec) return fail(HB_ERR_ARG, "hb_block_stream: offsets decrease");
         }
     }
     cudaSetDevice(c->device);
@@ -161,28 +188,33 @@ extern "C" hb_status hb_block_stream(hb_ctx *c, int64_t n_rows_s, int32_t n_cols
     std::sort(need.begin(), need.end());
     need.erase(std::unique(need.begin(), need.end()), need.end());
     const size_t chunk_bytes = c->opt.chunk_bytes ? c->opt.chunk_bytes : (256ull << 20);
-    auto row_bytes = [&](int64_t i) {
-        size_t b = 0;
-        for (int k : need) {
-            const hb_column &col = cols_s[k];
-            b += col.type == HB_COL_STRING ? (col.offsets[i + 1] - col.offsets[i]) + 4 : 4;
-            if (col.valid) b += 1;
-        }
+    // bytes of rows [0, i) in a chunk: string bytes (from the offsets) plus a
+    // fixed part per row; a chunk is the longest run of rows within the budget
+    size_t fixed_row = 0;
+    for (int k : need) fixed_row += 4 + (cols_s[k].valid ? 1 : 0);   // offset or value, validity byte
+    auto cum = [&](int64_t i) {
+        size_t b = (size_t)i * fixed_row;
+        for (int k : need)
+            if (cols_s[k].type == HB_COL_STRING) b += cols_s[k].offsets[i];
         return b;
     };
     std::vector<int64_t> bounds = {0};
     {
-        size_t acc = 0;
         const size_t budget = chunk_bytes > 8192 ? chunk_bytes - 256 * (need.size() * 3 + 4) : chunk_bytes / 2;
-        for (int64_t i = 0; i < n_rows_s; i++) {
-            const size_t rb = row_bytes(i);
-            if (acc + rb > budget && i > bounds.back()) {
-                bounds.push_back(i);
-                acc = 0;
+        int64_t b0 = 0;
+        while (b0 < n_rows_s) {
+            const size_t base = cum(b0);
+            int64_t lo = b0 + 1, hi = n_rows_s;   // the chunk end: largest e in [lo, hi] within the budget
+            if (cum(lo) - base <= budget) {
+                while (lo < hi) {
+                    const int64_t mid = lo + (hi - lo + 1) / 2;
+                    if (cum(mid) - base <= budget) lo = mid;
+                    else hi = mid - 1;
+                }
             }
-            acc += rb;
+            bounds.push_back(lo);
+            b0 = lo;
         }
-        if (bounds.back() != n_rows_s) bounds.push_back(n_rows_s);
     }
     const int K = (int)bounds.size() - 1;
     int64_t max_rows = 1;
@@ -198,21 +230,30 @@ extern "C" hb_status hb_block_stream(hb_ctx *c, int64_t n_rows_s, int32_t n_cols
     if (max_buf > chunk_bytes && K > 0 && max_rows > 1)
         return fail(HB_ERR_ARG, "hb_block_stream: a chunk exceeds chunk_bytes");
 
-    // staging: two pinned host buffers, two device chunk buffers, copy stream
-    std::vector<uint8_t *> pin(2, nullptr);
-    std::vector<void *> dbuf(2, nullptr);
-    cudaStream_t cs = nullptr;
-    cudaEvent_t copied[2] = {nullptr, nullptr}, consumed[2] = {nullptr, nullptr};
+    // staging: two device chunk buffers and a copy stream kept by the context;
+    // page-locked S arrays are copied straight from the caller's memory, any
+    // other S goes through two pinned buffers (c->pin)
+    bool direct = true;
+    for (int k : need) {
+        const hb_column &col = cols_s[k];
+        if (n_rows_s > 0 && col.data && !page_locked(col.data)) direct = false;
+        if (col.type == HB_COL_STRING && !page_locked(col.offsets)) direct = false;
+        if (col.valid && !page_locked(col.valid)) direct = false;
+    }
+    if (!direct) HB_TRY(ensure_pinned(c, max_buf));
+    for (int b = 0; b < 2; b++) {
+        HB_TRY(grow(c, c->w_chunk[b], max_buf));
+        if (!c->chunk_copied[b]) HB_CUDA(cudaEventCreateWithFlags(&c->chunk_copied[b], cudaEventDisableTiming));
+        if (!c->chunk_consumed[b]) HB_CUDA(cudaEventCreateWithFlags(&c->chunk_consumed[b], cudaEventDisableTiming));
+        HB_CUDA(cudaEventRecord(c->chunk_consumed[b], c->stream));
+    }
+    if (!c->copy_stream) HB_CUDA(cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
+    void *dbuf[2] = {c->w_chunk[0].p, c->w_chunk[1].p};
+    cudaStream_t cs = c->copy_stream;
+    cudaEvent_t *copied = c->chunk_copied, *consumed = c->chunk_consumed;
     auto cleanup = [&]() {
         cudaStreamSynchronize(c->stream);
-        if (cs) cudaStreamSynchronize(cs);
-        for (int b = 0; b < 2; b++) {
-            if (pin[b]) cudaFreeHost(pin[b]);
-            if (dbuf[b]) cudaFree(dbuf[b]);
-            if (copied[b]) cudaEventDestroy(copied[b]);
-            if (consumed[b]) cudaEventDestroy(consumed[b]);
-        }
-        if (cs) cudaStreamDestroy(cs);
+        cudaStreamSynchronize(cs);
         c->side[1].rec = nullptr;
         c->side[1].hot = nullptr;
         c->side[1].grams.clear();
@@ -239,13 +280,6 @@ extern "C" hb_status hb_block_stream(hb_ctx *c, int64_t n_rows_s, int32_t n_cols
             return s__;         \
         }                       \
     } while (0)
-    for (int b = 0; b < 2; b++) {
-        HB_SCUDA(cudaMallocHost(reinterpret_cast<void **>(&pin[b]), max_buf));
-        HB_SCUDA(cudaMalloc(&dbuf[b], max_buf));
-        HB_SCUDA(cudaEventCreateWithFlags(&copied[b], cudaEventDisableTiming));
-        HB_SCUDA(cudaEventCreateWithFlags(&consumed[b], cudaEventDisableTiming));
-    }
-    HB_SCUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
 
     // R side: groups of every active MD, kept for all chunks
     const int64_t n_r = c->side[0].n;
@@ -322,10 +356,21 @@ extern "C" hb_status hb_block_stream(hb_ctx *c, int64_t n_rows_s, int32_t n_cols
     // chunk 0 in flight
     auto issue_copy = [&](int k) -> cudaError_t {
         const int b = k & 1;
-        cudaError_t e = cudaEventSynchronize(consumed[b]);   // the device buffer's previous chunk is done
-        if (e != cudaSuccess) return e;
-        pack_chunk(cols_s, need, bounds[k], bounds[k + 1], layouts[k], pin[b]);
-        e = cudaMemcpyAsync(dbuf[b], pin[b], sizes[k], cudaMemcpyHostToDevice, cs);
+        cudaError_t e;
+        if (direct) {
+            // the copy stream waits for the device buffer's previous chunk
+            e = cudaStreamWaitEvent(cs, consumed[b], 0);
+            if (e != cudaSuccess) return e;
+            e = copy_chunk_direct(cols_s, need, bounds[k], bounds[k + 1], layouts[k],
+                                  static_cast<uint8_t *>(dbuf[b]), cs);
+        } else {
+            // the pinned buffer and the device buffer of chunk k-2 are both free
+            e = cudaEventSynchronize(consumed[b]);
+            if (e != cudaSuccess) return e;
+            uint8_t *pin = static_cast<uint8_t *>(c->pin[b]);
+            pack_chunk(cols_s, need, bounds[k], bounds[k + 1], layouts[k], pin);
+            e = cudaMemcpyAsync(dbuf[b], pin, sizes[k], cudaMemcpyHostToDevice, cs);
+        }
         if (e != cudaSuccess) return e;
         return cudaEventRecord(copied[b], cs);
     };

@@ -3,6 +3,12 @@
 // Groups are found with an exact open-addressing table over the tuples'
 // equality codes; members are laid out per group by a counting sort; every
 // group with a pair to compare becomes a block with its tile count.
+//
+// Small blocks of a self-join (2..SMALL_MAX tuples) are packed: blocks of one
+// size n are listed together (their member starts, by size class), and every
+// group of floor(T / n) of them becomes one packed tile, whose rows and
+// columns are those blocks' members side by side and whose valid pairs stay
+// inside each block.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -137,7 +143,8 @@ __device__ __forceinline__ uint64_t tiles_of(uint32_t nr, uint32_t ns, int self_
 __global__ void k_emit_blocks(const uint32_t *count_r, const uint32_t *start_r, const uint32_t *count_s,
                               const uint32_t *start_s, uint64_t cap, uint32_t md, int self_join,
                               uint32_t member_base_r, uint32_t member_base_s, int tile, BlockDesc *blocks,
-                              uint64_t *tiles, uint32_t *n_blocks, uint32_t block_cap, unsigned int *overflow) {
+                              uint64_t *tiles, uint32_t *n_blocks, uint32_t block_cap, unsigned int *overflow,
+                              uint32_t small_max) {
     int64_t sl = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     bool keep = false;
     uint32_t nr = 0, ns = 0;
@@ -145,7 +152,7 @@ __global__ void k_emit_blocks(const uint32_t *count_r, const uint32_t *start_r, 
         nr = count_r[sl];
         if (self_join) {
             ns = nr;
-            keep = nr >= 2;
+            keep = nr >= 2 && nr > small_max;   // smaller blocks are packed (k_emit_packed)
         } else {
             ns = count_s[sl];
             keep = nr >= 1 && ns >= 1;
@@ -168,9 +175,97 @@ __global__ void k_emit_blocks(const uint32_t *count_r, const uint32_t *start_r, 
         d.start_r = member_base_r + start_r[sl];
         d.n_s = ns;
         d.start_s = self_join ? d.start_r : member_base_s + start_s[sl];
-        d.pad = 0;
+        d.packed = 0;
         blocks[b] = d;
         tiles[b] = tiles_of(nr, ns, self_join, tile);
+    }
+}
+
+// ---- packing of small self-join blocks (metadata words: see SmallMeta)
+struct SmallMeta {
+    static constexpr int COUNT = 0;     // [n]: blocks of n tuples (this MD)
+    static constexpr int OFF = 32;      // [n]: first entry of size class n in the start list
+    static constexpr int CURSOR = 64;   // [n]: entries written so far
+    static constexpr int TILES = 96;    // [n]: first packed tile of class n; [SMALL_MAX + 1]: this MD's total
+    static constexpr int TOTAL = 128;   // entries of the start list used by all MDs so far
+};
+
+__global__ void k_small_hist(const uint32_t *count, uint64_t cap, uint32_t *meta) {
+    __shared__ uint32_t h[SMALL_MAX + 1];
+    for (int t = threadIdx.x; t <= SMALL_MAX; t += blockDim.x) h[t] = 0;
+    __syncthreads();
+    const int64_t sl = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (sl < (int64_t)cap) {
+        const uint32_t n = count[sl];
+        if (n >= 2 && n <= (uint32_t)SMALL_MAX) atomicAdd(&h[n], 1u);
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t <= SMALL_MAX; t += blockDim.x)
+        if (h[t]) atomicAdd(&meta[SmallMeta::COUNT + t], h[t]);
+}
+
+// one thread: class regions in the start list and packed-tile ranges
+__global__ void k_small_plan(uint32_t *meta, int tile, uint32_t small_cap, unsigned int *overflow,
+                             uint32_t *small_total) {
+    uint32_t base = meta[SmallMeta::TOTAL], tp = 0;
+    for (int n = 2; n <= SMALL_MAX; n++) {
+        const uint32_t cnt = meta[SmallMeta::COUNT + n];
+        const uint32_t per = (uint32_t)(tile / n);
+        meta[SmallMeta::OFF + n] = base;
+        meta[SmallMeta::CURSOR + n] = 0;
+        meta[SmallMeta::TILES + n] = tp;
+        base += cnt;
+        tp += (cnt + per - 1) / per;
+    }
+    meta[SmallMeta::TILES + SMALL_MAX + 1] = tp;
+    if (base > small_cap) {
+        atomicExch(overflow, 1u);
+        base = small_cap;
+    }
+    meta[SmallMeta::TOTAL] = base;
+    *small_total = base;
+}
+
+__global__ void k_small_scatter(const uint32_t *count, const uint32_t *start, uint64_t cap, uint32_t member_base,
+                                uint32_t *meta, uint32_t *small, uint32_t small_cap) {
+    const int64_t sl = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (sl >= (int64_t)cap) return;
+    const uint32_t n = count[sl];
+    if (n < 2 || n > (uint32_t)SMALL_MAX) return;
+    const uint32_t pos = meta[SmallMeta::OFF + n] + atomicAdd(&meta[SmallMeta::CURSOR + n], 1u);
+    if (pos < small_cap) small[pos] = member_base + start[sl];
+}
+
+// one packed tile per work item: floor(T / n) blocks of size class n
+__global__ void k_emit_packed(const uint32_t *meta, uint32_t md, int tile, BlockDesc *blocks, uint64_t *tiles,
+                              uint32_t *n_blocks, uint32_t *n_packed, uint32_t block_cap, uint32_t small_cap,
+                              unsigned int *overflow) {
+    const uint32_t total = meta[SmallMeta::TILES + SMALL_MAX + 1];
+    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < total; q += gridDim.x * blockDim.x) {
+        int n = 2;
+        while (n < SMALL_MAX && meta[SmallMeta::TILES + n + 1] <= q) n++;
+        const uint32_t per = (uint32_t)(tile / n);
+        const uint32_t first = (q - meta[SmallMeta::TILES + n]) * per;
+        const uint32_t k = min(per, meta[SmallMeta::COUNT + n] - first);
+        if ((uint64_t)meta[SmallMeta::OFF + n] + first + k > small_cap) {   // start list overflow: no tile
+            atomicExch(overflow, 1u);
+            continue;
+        }
+        const uint32_t b = atomicAdd(n_blocks, 1u);
+        atomicAdd(n_packed, 1u);
+        if (b >= block_cap) {
+            atomicExch(overflow, 1u);
+            continue;
+        }
+        BlockDesc d;
+        d.md = md;
+        d.n_r = k * (uint32_t)n;
+        d.start_r = meta[SmallMeta::OFF + n] + first;
+        d.n_s = d.n_r;
+        d.start_s = d.start_r;
+        d.packed = (uint32_t)n;
+        blocks[b] = d;
+        tiles[b] = 1;
     }
 }
 
@@ -225,7 +320,24 @@ void emit_blocks(const uint32_t *count_r, const uint32_t *start_r, const uint32_
     HB_LAUNCHED(1);
     k_emit_blocks<<<nblk((int64_t)cap), BT, 0, s>>>(count_r, start_r, count_s, start_s, cap, md, self_join,
                                                     member_base_r, member_base_s, tile, blocks, tiles, n_blocks,
-                                                    block_cap, overflow);
+                                                    block_cap, overflow, 0u);
+}
+
+void emit_blocks_packed(const uint32_t *count_r, const uint32_t *start_r, uint64_t cap, uint32_t md,
+                        uint32_t member_base_r, int tile, BlockDesc *blocks, uint64_t *tiles, uint32_t *n_blocks,
+                        uint32_t *n_packed, uint32_t block_cap, unsigned int *overflow, uint32_t *small_meta,
+                        uint32_t *small, uint32_t small_cap, uint32_t *small_total, int n_sm, cudaStream_t s) {
+    cudaMemsetAsync(small_meta + SmallMeta::COUNT, 0, sizeof(uint32_t) * (SMALL_MAX + 1), s);
+    HB_LAUNCHED(5);
+    k_small_hist<<<nblk((int64_t)cap), BT, 0, s>>>(count_r, cap, small_meta);
+    k_small_plan<<<1, 1, 0, s>>>(small_meta, tile, small_cap, overflow, small_total);
+    k_small_scatter<<<nblk((int64_t)cap), BT, 0, s>>>(count_r, start_r, cap, member_base_r, small_meta, small,
+                                                      small_cap);
+    k_emit_blocks<<<nblk((int64_t)cap), BT, 0, s>>>(count_r, start_r, nullptr, nullptr, cap, md, 1, member_base_r, 0,
+                                                    tile, blocks, tiles, n_blocks, block_cap, overflow,
+                                                    (uint32_t)SMALL_MAX);
+    k_emit_packed<<<(unsigned)(2 * n_sm), BT, 0, s>>>(small_meta, md, tile, blocks, tiles, n_blocks, n_packed,
+                                                      block_cap, small_cap, overflow);
 }
 
 void clamp_blocks(uint32_t *n_blocks, uint32_t block_cap, cudaStream_t s) {

@@ -30,6 +30,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <type_traits>
 
 #include "hb_internal.h"
@@ -330,11 +331,13 @@ __device__ __forceinline__ int first_bit(uint32_t x) { return __ffs(x) - 1; }
 __device__ __forceinline__ int first_bit(uint64_t x) { return __ffsll((long long)x) - 1; }
 
 // columns c of row r that form a pair of the tile: c < nc, and c > r on a
-// diagonal tile of a self-join
+// diagonal tile of a self-join; on a packed tile (pn > 0) c must also lie in
+// r's block [pn * (r / pn), pn * (r / pn + 1))
 template <typename Mask>
-__device__ __forceinline__ Mask valid_cols(int r, int nr, int nc, bool diag) {
+__device__ __forceinline__ Mask valid_cols(int r, int nr, int nc, bool diag, int pn) {
     constexpr int BITS = 8 * (int)sizeof(Mask);
     if (r >= nr) return 0;
+    if (pn) nc = (r / pn + 1) * pn;   // packed tile: columns of r's own block only
     Mask v = nc >= BITS ? ~(Mask)0 : (((Mask)1 << nc) - (Mask)1);
     if (diag) v &= ~((((Mask)2) << r) - (Mask)1);
     return v;
@@ -378,16 +381,15 @@ __device__ __forceinline__ void filter_range(const Op &op, uint32_t x, uint32_t 
     span = (uint32_t)(h - l);
 }
 
-// Phase 1 of one row (lane) of a tile with KO (<= 3) varying equality keys
-// and filter form FK.  For the pair's combination of other-key matches,
-// t = pk >> combo holds: bit 0 = keep if the filter passes, bit 8 = keep if
-// it fails, bit 16 = owned (pkn: the same for a row whose operand is missing,
-// which no filter passes).  Columns are visited 8 at a time (the tile's
-// column count is a multiple of 8; columns past nc are masked by the caller).
-template <int KO, int FK, int T, typename Mask>
-__device__ __forceinline__ void p1_row(const uint32_t *__restrict__ hr, const uint32_t *__restrict__ hcols, int nc,
-                                       const int *okey, const Op &op0, uint32_t pk, uint32_t pkn, Mask &km_out,
-                                       Mask &om_out) {
+// Phase 1 of one row (lane) of a tile, as bit masks over the tile's columns
+// (visited 8 at a time: the tile's column count is a multiple of 8, and bits
+// past nc are cleared by the valid mask).
+//
+// p1_keys: bit c of em[i] = the row's code of the i-th varying equality key
+// (okey[i]) equals column c's.
+template <int KO, int T, typename Mask>
+__device__ __forceinline__ void p1_keys(const uint32_t *__restrict__ hr, const uint32_t *__restrict__ hcols, int nc,
+                                        const int *okey, Mask *em) {
     uint32_t rk[KO > 0 ? KO : 1];
     const uint32_t *ck[KO > 0 ? KO : 1];
 #pragma unroll
@@ -395,49 +397,209 @@ __device__ __forceinline__ void p1_row(const uint32_t *__restrict__ hr, const ui
         const uint32_t x = hr[okey[i]];
         rk[i] = x < NOMATCH_CODE ? x : 0xFFFFFFFDu;   // a missing code matches no column code
         ck[i] = hcols + okey[i] * T;
+        em[i] = 0;
+    }
+    if (KO == 0) return;
+    for (int c0 = 0; c0 < nc; c0 += 8) {
+        uint32_t ec[KO > 0 ? KO : 1];
+#pragma unroll
+        for (int i = 0; i < KO; i++) ec[i] = 0;
+#pragma unroll
+        for (int u = 0; u < 8; u++)
+#pragma unroll
+            for (int i = 0; i < KO; i++)
+                if (ck[i][c0 + u] == rk[i]) ec[i] |= 1u << u;
+#pragma unroll
+        for (int i = 0; i < KO; i++) em[i] |= (Mask)ec[i] << c0;
+    }
+}
+
+// p1_filter: bit c = the cheap necessary condition of op holds for (row, column
+// c): an interval test on the column's operand (F_RANGE: edit-distance length
+// or Jaccard size filter; none passes a missing row operand) or |a - b| <= delta
+// (F_ABS).
+template <int FK, int T, typename Mask>
+__device__ __forceinline__ Mask p1_filter(const uint32_t *__restrict__ hr, const uint32_t *__restrict__ hcols,
+                                          int nc, const Op &op) {
+    const uint32_t *cf = hcols + op.hot * T;
+    const uint32_t x = hr[op.hot];
+    uint32_t lo = 0, span = 0;
+    if (FK == F_RANGE) {
+        if (x == NULL_LEN) return 0;
+        filter_range(op, x, lo, span);
+    }
+    const float xf = __uint_as_float(x), dl = op.delta;
+    Mask fm = 0;
+    for (int c0 = 0; c0 < nc; c0 += 8) {
+        uint32_t fc = 0;
+#pragma unroll
+        for (int u = 0; u < 8; u++) {
+            const uint32_t y = cf[c0 + u];
+            const bool pass = FK == F_RANGE ? y - lo <= span : fabsf(xf - __uint_as_float(y)) <= dl;
+            if (pass) fc |= 1u << u;
+        }
+        fm |= (Mask)fc << c0;
+    }
+    return fm;
+}
+
+// p1_combine: the tile's decisions applied to whole masks.  For each
+// combination cb of other-key matches, own8 bit cb = the pair is owned, kf8
+// bit cb = it is kept even when every base filter fails (an owned pair is kept
+// when one passes: fm).  Returns the row's surviving columns; owned = its
+// owned (candidate) pairs.
+template <int KO, typename Mask>
+__device__ __forceinline__ Mask p1_combine(const Mask *em, Mask fm, uint32_t own8, uint32_t kf8, Mask vm,
+                                           unsigned &owned) {
+    Mask keep = 0;
+    owned = 0;
+#pragma unroll
+    for (int cb = 0; cb < (1 << KO); cb++) {
+        if (!((own8 >> cb) & 1u)) continue;
+        Mask mt = vm;
+#pragma unroll
+        for (int i = 0; i < KO; i++) mt &= ((cb >> i) & 1) ? em[i] : ~em[i];
+        owned += (unsigned)pop(mt);
+        keep |= ((kf8 >> cb) & 1u) ? mt : (mt & fm);
+    }
+    return keep;
+}
+
+// p1_row: the same for one row with at most one base filter (FK), in a single
+// pass over the columns (keys and filter together), then the decisions of
+// p1_combine applied inline; keep_out = surviving columns, owned_out = owned
+// (candidate) pairs.
+template <int KO, int FK, int T, typename Mask>
+__device__ __forceinline__ void p1_row(const uint32_t *__restrict__ hr, const uint32_t *__restrict__ hcols, int nc,
+                                       const int *okey, const Op &op0, uint32_t own8, uint32_t kf8, Mask vm,
+                                       Mask &keep_out, unsigned &owned_out) {
+    uint32_t rk[KO > 0 ? KO : 1];
+    const uint32_t *ck[KO > 0 ? KO : 1];
+#pragma unroll
+    for (int i = 0; i < KO; i++) {
+        const uint32_t x = hr[okey[i]];
+        rk[i] = x < NOMATCH_CODE ? x : 0xFFFFFFFDu;
+        ck[i] = hcols + okey[i] * T;
     }
     const uint32_t *cf = FK != F_NONE ? hcols + op0.hot * T : hcols;
     uint32_t lo = 0, span = 0;
+    bool rnull = false;
     float xf = 0.f;
     const float dl = op0.delta;
     if (FK == F_RANGE) {
         const uint32_t x = hr[op0.hot];
-        if (x == NULL_LEN) pk = pkn;
-        else filter_range(op0, x, lo, span);
+        rnull = x == NULL_LEN;
+        if (!rnull) filter_range(op0, x, lo, span);
     }
     if (FK == F_ABS) xf = __uint_as_float(hr[op0.hot]);
-    Mask km = 0, om = 0;
-    for (int c0 = 0; c0 < nc; c0 += 8) {
-        uint32_t kc = 0, oc = 0;
+    Mask em[KO > 0 ? KO : 1];
 #pragma unroll
-        for (int u = 0; u < 8; u++) {
-            const int c = c0 + u;
-            uint32_t t;
-            if (KO == 0) {
-                t = pk;
-            } else if (KO == 1) {
-                t = ck[0][c] == rk[0] ? (pk >> 1) : pk;
-            } else {
-                uint32_t combo = 0;
+    for (int i = 0; i < KO; i++) em[i] = 0;
+    Mask fm = 0;
+    if (KO > 0 || FK != F_NONE) {
+        for (int c0 = 0; c0 < nc; c0 += 8) {
+            uint32_t ec[KO > 0 ? KO : 1], fc = 0;
 #pragma unroll
-                for (int i = 0; i < KO; i++) combo |= ck[i][c] == rk[i] ? (1u << i) : 0u;
-                t = pk >> combo;
+            for (int i = 0; i < KO; i++) ec[i] = 0;
+#pragma unroll
+            for (int u = 0; u < 8; u++) {
+                const int c = c0 + u;
+#pragma unroll
+                for (int i = 0; i < KO; i++)
+                    if (ck[i][c] == rk[i]) ec[i] |= 1u << u;
+                if (FK == F_RANGE && cf[c] - lo <= span) fc |= 1u << u;
+                if (FK == F_ABS && fabsf(xf - __uint_as_float(cf[c])) <= dl) fc |= 1u << u;
             }
-            bool fl = true;
-            if (FK == F_RANGE) fl = cf[c] - lo <= span;
-            if (FK == F_ABS) fl = fabsf(xf - __uint_as_float(cf[c])) <= dl;
-            if (t & (fl ? 1u : 0x100u)) kc |= 1u << u;
-            if (t & 0x10000u) oc |= 1u << u;
+#pragma unroll
+            for (int i = 0; i < KO; i++) em[i] |= (Mask)ec[i] << c0;
+            fm |= (Mask)fc << c0;
         }
-        km |= (Mask)kc << c0;
-        om |= (Mask)oc << c0;
     }
-    km_out = km;
-    om_out = om;
+    if (FK == F_NONE) fm = ~(Mask)0;
+    if (FK == F_RANGE && rnull) fm = 0;
+    Mask keep = 0;
+    unsigned owned = 0;
+#pragma unroll
+    for (int cb = 0; cb < (1 << KO); cb++) {
+        if (!((own8 >> cb) & 1u)) continue;
+        Mask mt = vm;
+#pragma unroll
+        for (int i = 0; i < KO; i++) mt &= ((cb >> i) & 1) ? em[i] : ~em[i];
+        owned += (unsigned)pop(mt);
+        keep |= ((kf8 >> cb) & 1u) ? mt : (mt & fm);
+    }
+    keep_out = keep;
+    owned_out = owned;
 }
 
-template <int R, bool LOG>
-__global__ void __launch_bounds__(EV_THREADS) k_eval(const __grid_constant__ EvalParams P) {
+// A necessary condition of a predicate from the hot records alone: the filter
+// operand test and, where the bins are staged, the bag-distance bound of edit
+// distance or the gram-bin bound of Jaccard (the tests eval_op applies before
+// its exact stage).  Word w of the column record is hc[w * cs].
+__device__ __forceinline__ bool screen(const Op &op, const uint32_t *hr, const uint32_t *hc, int cs) {
+    const uint32_t x = hr[op.hot], y = hc[op.hot * cs];
+    if (op.kind == OP_ABS) return fabsf(__uint_as_float(x) - __uint_as_float(y)) <= op.delta;
+    if (x == NULL_LEN || y == NULL_LEN) return false;
+    const int h2 = op.hot2;
+    if (op.kind == OP_ED) {
+        if ((x > y ? x - y : y - x) > op.k) return false;
+        if (h2 == 255) return true;
+        unsigned p1 = 0, p2 = 0;
+#pragma unroll
+        for (int w = 0; w < 4; w++) {
+            const unsigned bx = hr[h2 + w], by = hc[(h2 + w) * cs];
+            p1 = __dp4a(__vsubus4(bx, by), 0x01010101u, p1);
+            p2 = __dp4a(__vsubus4(by, bx), 0x01010101u, p2);
+        }
+        return max(p1, p2) <= op.k;
+    }
+    if ((uint64_t)min(x, y) * op.den < (uint64_t)op.num * max(x, y)) return false;
+    if (h2 == 255 || x > 255u || y > 255u) return true;
+    unsigned ub = 0;
+#pragma unroll
+    for (int w = 0; w < 8; w++) ub = __dp4a(__vminu4(hr[h2 + w], hc[(h2 + w) * cs]), 0x01010101u, ub);
+    return (uint64_t)ub * ((uint64_t)op.den + op.num) >= (uint64_t)op.num * ((uint64_t)x + y);
+}
+
+// per-warp ring of survivors waiting for phase 2: tuple ids and equality-match bits
+constexpr int RING_SLOTS = 64;
+
+// phase 2 for one survivor per lane (act): the sequential program on the full
+// records; witnessed pairs are compacted with a warp ballot and one atomic
+template <bool LOG>
+__device__ __forceinline__ void phase2(const EvalParams &P, const uint64_t *lut, bool act, uint32_t ra,
+                                       uint32_t cb, uint32_t E, const uint32_t *rec_c, int W, int lane,
+                                       unsigned lt, LogAcc &lg) {
+    bool hit = false;
+    if (act) {
+        const uint64_t alive = alive_of(P, lut, E);
+        hit = run_program<LOG>(P, alive, P.rec_r + (size_t)ra * W, rec_c + (size_t)cb * W, lg);
+    }
+    const unsigned hm = __ballot_sync(0xffffffffu, hit);
+    if (hm) {
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd(P.out_count, (unsigned long long)__popc(hm));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (hit) {
+            const unsigned long long idx = base + __popc(hm & lt);
+            uint64_t key;
+            if (P.self_join) {
+                const uint32_t lo2 = ra < cb ? ra : cb, hi2 = ra < cb ? cb : ra;
+                key = ((uint64_t)lo2 << P.key_bits_s) | (uint64_t)hi2;
+            } else {
+                key = ((uint64_t)(ra + P.row_base) << P.key_bits_s) | (uint64_t)(cb + P.col_base);
+            }
+            if (idx < P.out_cap) P.out[idx] = key;
+        }
+    }
+}
+
+// MULTI: tiles whose block has 2..4 distinct base filters take the multi-pass
+// phase 1 (instantiated only for rule sets that have such blocks).  RING: the
+// survivors are screened (phase 1b) and batched through the warp's ring;
+// otherwise phase 2 runs per tile.
+template <int R, bool LOG, bool MULTI, bool RING>
+__global__ void __launch_bounds__(EV_THREADS, 4) k_eval(const __grid_constant__ EvalParams P) {
     extern __shared__ __align__(16) uint32_t smem[];
     constexpr int T = 32 * R;
     using Mask = typename std::conditional<(R == 2), uint64_t, uint32_t>::type;
@@ -445,12 +607,16 @@ __global__ void __launch_bounds__(EV_THREADS) k_eval(const __grid_constant__ Eva
     const int HW = P.HW, HWP = P.HW + 1, W = P.W;
     uint64_t *lut = reinterpret_cast<uint64_t *>(smem);
     const int lut_words = P.use_lut ? 2 * (1 << P.n_eq) : 0;
-    uint32_t *wbase = smem + lut_words + wib * (2 * T * HWP + 2 * T + T * T / 2);
+    uint32_t *wbase = smem + lut_words + wib * (T * HWP + T * HW + 2 * T + T * T / 2 + 3 * RING_SLOTS);
     uint32_t *hrows = wbase;
     uint32_t *hcols = hrows + T * HWP;
-    uint32_t *rid_s = hcols + T * HWP;
+    uint32_t *rid_s = hcols + T * HW;
     uint32_t *cid_s = rid_s + T;
     uint16_t *surv = reinterpret_cast<uint16_t *>(cid_s + T);
+    uint32_t *ring_ra = cid_s + T + T * T / 2;
+    uint32_t *ring_cb = ring_ra + RING_SLOTS;
+    uint32_t *ring_e = ring_cb + RING_SLOTS;
+    int pend = 0;   // survivors in the ring (warp-uniform)
     __shared__ unsigned long long lgs[LOG ? MAX_OPS * LOG_FIELDS : 1];
     LogAcc lg{lgs};
     if (P.use_lut)
@@ -477,8 +643,10 @@ __global__ void __launch_bounds__(EV_THREADS) k_eval(const __grid_constant__ Eva
         for (uint64_t t = t0; t < t1; t++) {
             while (P.tile_prefix[bi + 1] <= t) bi++;
             const BlockDesc B = P.blocks[bi];
-            uint32_t ti, tj;
-            decode_tile(t - P.tile_prefix[bi], B.n_r, B.n_s, P.self_join, T, ti, tj);
+            // pn > 0: a packed tile of self-join blocks of pn tuples, side by side
+            const int pn = (int)B.packed;
+            uint32_t ti = 0, tj = 0;
+            if (!pn) decode_tile(t - P.tile_prefix[bi], B.n_r, B.n_s, P.self_join, T, ti, tj);
             const uint32_t r0 = ti * T, c0 = tj * T;
             const int nr = (int)min((uint32_t)T, B.n_r - r0);
             const int nc = (int)min((uint32_t)T, B.n_s - c0);
@@ -495,8 +663,10 @@ __global__ void __launch_bounds__(EV_THREADS) k_eval(const __grid_constant__ Eva
 #pragma unroll
             for (int rr = 0; rr < R; rr++) {
                 const int r = rr * 32 + lane;
+                uint32_t pid = 0;   // packed tile: row r = member r % pn of block r / pn; columns alike
+                if (pn && r < nr) pid = P.members_r[P.small[B.start_r + r / pn] + r % pn];
                 if (r < nr) {
-                    const uint32_t id = P.members_r[B.start_r + r0 + r];
+                    const uint32_t id = pn ? pid : P.members_r[B.start_r + r0 + r];
                     rid_s[r] = id;
                     const uint4 *src = reinterpret_cast<const uint4 *>(P.hot_r + (size_t)id * HW);
                     uint32_t *dst = hrows + r * HWP;
@@ -509,7 +679,7 @@ __global__ void __launch_bounds__(EV_THREADS) k_eval(const __grid_constant__ Eva
                     }
                 }
                 if (r < nc) {
-                    const uint32_t id = P.members_s[B.start_s + c0 + r];
+                    const uint32_t id = pn ? pid : P.members_s[B.start_s + c0 + r];
                     cid_s[r] = id;
                     const uint4 *src = reinterpret_cast<const uint4 *>(hot_c + (size_t)id * HW);
                     uint32_t *dst = hcols + r;   // word-major: word w of column c at w * T + c
@@ -525,7 +695,8 @@ __global__ void __launch_bounds__(EV_THREADS) k_eval(const __grid_constant__ Eva
             __syncwarp();
             // ---- phase 1: every pair of the tile; lane = row, loop over the
             // columns; each lane collects the kept columns of its rows in a bit mask
-            exam += diag ? (unsigned long long)nr * (nr - 1) / 2 : (unsigned long long)nr * nc;
+            exam += pn ? (unsigned long long)(nr / pn) * (pn * (pn - 1) / 2)
+                       : diag ? (unsigned long long)nr * (nr - 1) / 2 : (unsigned long long)nr * nc;
             // The equality keys of the owner MD hold for every pair of its block;
             // only the other keys (okeys) vary.  With at most 4 of them, lane l
             // works out, for the l-th combination of other-key matches, whether
@@ -560,44 +731,62 @@ __global__ void __launch_bounds__(EV_THREADS) k_eval(const __grid_constant__ Eva
             // condition; any other owned pair goes on as it is
             const bool filt = !LOG && nbase != 255;
             Mask kmask[R];
-            // fast path: at most 3 varying keys and at most one filter
-            const bool fast = ko <= 3 && (!filt || nbase == 1);
+            const bool fast = ko <= 3 && (MULTI || !filt || nbase == 1);
             if (fast) {
                 const uint32_t own8 = ownmask & 0xffu;
-                const uint32_t kfail = filt ? (own8 & ~basemask) : own8;
-                const uint32_t pk = own8 | (kfail << 8) | (own8 << 16);
-                const uint32_t pkn = kfail | (kfail << 8) | (own8 << 16);
+                const uint32_t kf8 = filt ? (own8 & ~basemask) : own8;
                 const int fk = !filt ? F_NONE : op0.kind == OP_ABS ? F_ABS : F_RANGE;
-                const bool ownc = own8 == 0u || own8 == (1u << (1 << ko)) - 1u;   // owned alike for every combination
 #pragma unroll
                 for (int rr = 0; rr < R; rr++) {
                     const int r = rr * 32 + lane;
-                    Mask km = 0, om = 0;
                     const uint32_t *hr = hrows + r * HWP;
+                    const Mask vm = valid_cols<Mask>(r, nr, nc, diag, pn);
+                    Mask km = 0;
+                    unsigned ow = 0;
+                    if (MULTI && filt && nbase != 1) {
+                        Mask em[3];
+                        switch (ko) {
+                        case 0: p1_keys<0, T>(hr, hcols, nc, okey, em); break;
+                        case 1: p1_keys<1, T>(hr, hcols, nc, okey, em); break;
+                        case 2: p1_keys<2, T>(hr, hcols, nc, okey, em); break;
+                        default: p1_keys<3, T>(hr, hcols, nc, okey, em); break;
+                        }
+                        Mask fm = 0;
+                        for (int i = 0; i < nbase; i++) {
+                            const Op &op = P.ops[P.base_op[m][i]];
+                            fm |= op.kind == OP_ABS ? p1_filter<F_ABS, T, Mask>(hr, hcols, nc, op)
+                                                    : p1_filter<F_RANGE, T, Mask>(hr, hcols, nc, op);
+                        }
+                        switch (ko) {
+                        case 0: km = p1_combine<0, Mask>(em, fm, own8, kf8, vm, ow); break;
+                        case 1: km = p1_combine<1, Mask>(em, fm, own8, kf8, vm, ow); break;
+                        case 2: km = p1_combine<2, Mask>(em, fm, own8, kf8, vm, ow); break;
+                        default: km = p1_combine<3, Mask>(em, fm, own8, kf8, vm, ow); break;
+                        }
+                    } else
                     switch (ko * 3 + fk) {
-                    case 0: p1_row<0, F_NONE, T>(hr, hcols, nc, okey, op0, pk, pkn, km, om); break;
-                    case 1: p1_row<0, F_RANGE, T>(hr, hcols, nc, okey, op0, pk, pkn, km, om); break;
-                    case 2: p1_row<0, F_ABS, T>(hr, hcols, nc, okey, op0, pk, pkn, km, om); break;
-                    case 3: p1_row<1, F_NONE, T>(hr, hcols, nc, okey, op0, pk, pkn, km, om); break;
-                    case 4: p1_row<1, F_RANGE, T>(hr, hcols, nc, okey, op0, pk, pkn, km, om); break;
-                    case 5: p1_row<1, F_ABS, T>(hr, hcols, nc, okey, op0, pk, pkn, km, om); break;
-                    case 6: p1_row<2, F_NONE, T>(hr, hcols, nc, okey, op0, pk, pkn, km, om); break;
-                    case 7: p1_row<2, F_RANGE, T>(hr, hcols, nc, okey, op0, pk, pkn, km, om); break;
-                    case 8: p1_row<2, F_ABS, T>(hr, hcols, nc, okey, op0, pk, pkn, km, om); break;
-                    case 9: p1_row<3, F_NONE, T>(hr, hcols, nc, okey, op0, pk, pkn, km, om); break;
-                    case 10: p1_row<3, F_RANGE, T>(hr, hcols, nc, okey, op0, pk, pkn, km, om); break;
-                    default: p1_row<3, F_ABS, T>(hr, hcols, nc, okey, op0, pk, pkn, km, om); break;
+                    case 0: p1_row<0, F_NONE, T>(hr, hcols, nc, okey, op0, own8, kf8, vm, km, ow); break;
+                    case 1: p1_row<0, F_RANGE, T>(hr, hcols, nc, okey, op0, own8, kf8, vm, km, ow); break;
+                    case 2: p1_row<0, F_ABS, T>(hr, hcols, nc, okey, op0, own8, kf8, vm, km, ow); break;
+                    case 3: p1_row<1, F_NONE, T>(hr, hcols, nc, okey, op0, own8, kf8, vm, km, ow); break;
+                    case 4: p1_row<1, F_RANGE, T>(hr, hcols, nc, okey, op0, own8, kf8, vm, km, ow); break;
+                    case 5: p1_row<1, F_ABS, T>(hr, hcols, nc, okey, op0, own8, kf8, vm, km, ow); break;
+                    case 6: p1_row<2, F_NONE, T>(hr, hcols, nc, okey, op0, own8, kf8, vm, km, ow); break;
+                    case 7: p1_row<2, F_RANGE, T>(hr, hcols, nc, okey, op0, own8, kf8, vm, km, ow); break;
+                    case 8: p1_row<2, F_ABS, T>(hr, hcols, nc, okey, op0, own8, kf8, vm, km, ow); break;
+                    case 9: p1_row<3, F_NONE, T>(hr, hcols, nc, okey, op0, own8, kf8, vm, km, ow); break;
+                    case 10: p1_row<3, F_RANGE, T>(hr, hcols, nc, okey, op0, own8, kf8, vm, km, ow); break;
+                    default: p1_row<3, F_ABS, T>(hr, hcols, nc, okey, op0, own8, kf8, vm, km, ow); break;
                     }
-                    const Mask vm = valid_cols<Mask>(r, nr, nc, diag);
-                    kmask[rr] = km & vm;
-                    cand += ownc ? (own8 ? (unsigned)pop(vm) : 0u) : (unsigned)pop(om & vm);
+                    kmask[rr] = km;
+                    cand += ow;
                 }
             } else {
 #pragma unroll
                 for (int rr = 0; rr < R; rr++) {
                     const int r = rr * 32 + lane;
                     const uint32_t *hr = hrows + r * HWP;
-                    const Mask vm = valid_cols<Mask>(r, nr, nc, diag);
+                    const Mask vm = valid_cols<Mask>(r, nr, nc, diag, pn);
                     Mask km = 0;
                     for (int c = 0; c < nc; c++) {
                         const uint32_t *hc = hcols + c;
@@ -662,45 +851,96 @@ __global__ void __launch_bounds__(EV_THREADS) k_eval(const __grid_constant__ Eva
                 }
             }
             __syncwarp();
-            // ---- phase 2: the survivors, one per lane
+            if constexpr (!RING) {
+                // ---- phase 2 per tile: the survivors, one per lane
+                for (int s0 = 0; s0 < cnt; s0 += 32) {
+                    const int s = s0 + lane;
+                    uint32_t E = 0, ra = 0, cb = 0;
+                    if (s < cnt) {
+                        const uint32_t e16 = surv[s];
+                        const int r = (int)(e16 >> 6), c = (int)(e16 & 63u);
+                        const uint32_t *hr = hrows + r * HWP, *hc = hcols + c;
+                        E = P.eqset[m];
+                        for (uint32_t ok = okeys; ok; ok &= ok - 1) {
+                            const int e = __ffs(ok) - 1;
+                            const uint32_t x = hr[e];
+                            E |= (x == hc[e * T] && x < NOMATCH_CODE) ? (1u << e) : 0u;
+                        }
+                        ra = rid_s[r];
+                        cb = cid_s[c];
+                    }
+                    phase2<LOG>(P, lut, s < cnt, ra, cb, E, rec_c, W, lane, lt, lg);
+                }
+            } else {
+            // ---- phase 1b: the survivors, 32 at a time (shared memory only): the
+            // equality-match bits, then, unless an MD without non-equality
+            // predicates is alive, the staged necessary conditions of each alive
+            // MD's first two predicates; a survivor that every alive MD fails is
+            // dropped, the others join the warp's ring.  Phase 2 runs whenever
+            // the ring holds 32, so that every lane of it has a pair.
             for (int s0 = 0; s0 < cnt; s0 += 32) {
                 const int s = s0 + lane;
-                bool hit = false;
-                uint32_t ra = 0, cb = 0;
+                bool keep = false;
+                uint32_t E = 0, ra = 0, cb = 0;
                 if (s < cnt) {
                     const uint32_t e16 = surv[s];
                     const int r = (int)(e16 >> 6), c = (int)(e16 & 63u);
-                    ra = rid_s[r];
-                    cb = cid_s[c];
                     const uint32_t *hr = hrows + r * HWP, *hc = hcols + c;
-                    uint32_t E = P.eqset[m];
+                    E = P.eqset[m];
                     for (uint32_t ok = okeys; ok; ok &= ok - 1) {
                         const int e = __ffs(ok) - 1;
                         const uint32_t x = hr[e];
                         E |= (x == hc[e * T] && x < NOMATCH_CODE) ? (1u << e) : 0u;
                     }
-                    const uint64_t alive = alive_of(P, lut, E);
-                    hit = run_program<LOG>(P, alive, P.rec_r + (size_t)ra * W, rec_c + (size_t)cb * W, lg);
-                }
-                const unsigned hm = __ballot_sync(0xffffffffu, hit);
-                if (hm) {
-                    unsigned long long base = 0;
-                    if (lane == 0) base = atomicAdd(P.out_count, (unsigned long long)__popc(hm));
-                    base = __shfl_sync(0xffffffffu, base, 0);
-                    if (hit) {
-                        const unsigned long long idx = base + __popc(hm & lt);
-                        uint64_t key;
-                        if (P.self_join) {
-                            const uint32_t lo2 = ra < cb ? ra : cb, hi2 = ra < cb ? cb : ra;
-                            key = ((uint64_t)lo2 << P.key_bits_s) | (uint64_t)hi2;
-                        } else {
-                            key = ((uint64_t)(ra + P.row_base) << P.key_bits_s) | (uint64_t)(cb + P.col_base);
+                    keep = true;
+                    {
+                        const uint64_t alive = alive_of(P, lut, E);
+                        keep = (alive & P.eqonly) != 0;
+                        for (uint64_t a = alive; a && !keep; a &= a - 1) {
+                            const int j = __ffsll((long long)a) - 1;
+                            const int o0 = P.screen_op[j][0], o1 = P.screen_op[j][1];
+                            keep = (o0 == 255 || screen(P.ops[o0], hr, hc, T)) &&
+                                   (o1 == 255 || screen(P.ops[o1], hr, hc, T));
                         }
-                        if (idx < P.out_cap) P.out[idx] = key;
                     }
+                    ra = rid_s[r];
+                    cb = cid_s[c];
                 }
+                const unsigned km = __ballot_sync(0xffffffffu, keep);
+                if (keep) {
+                    const int q = pend + __popc(km & lt);
+                    ring_ra[q] = ra;
+                    ring_cb[q] = cb;
+                    ring_e[q] = E;
+                }
+                pend += __popc(km);
+                if (pend >= 32) {
+                    __syncwarp();
+                    phase2<LOG>(P, lut, true, ring_ra[lane], ring_cb[lane], ring_e[lane], rec_c, W, lane, lt, lg);
+                    const int rest = pend - 32;
+                    uint32_t xa = 0, xb = 0, xe = 0;
+                    if (lane < rest) {
+                        xa = ring_ra[32 + lane];
+                        xb = ring_cb[32 + lane];
+                        xe = ring_e[32 + lane];
+                    }
+                    __syncwarp();
+                    if (lane < rest) {
+                        ring_ra[lane] = xa;
+                        ring_cb[lane] = xb;
+                        ring_e[lane] = xe;
+                    }
+                    pend = rest;
+                }
+                __syncwarp();
+            }
             }
         }
+    }
+    // the last survivors of this warp
+    if (RING && pend > 0) {
+        __syncwarp();
+        phase2<LOG>(P, lut, lane < pend, ring_ra[lane], ring_cb[lane], ring_e[lane], rec_c, W, lane, lt, lg);
     }
     for (int o = 16; o > 0; o >>= 1) cand += __shfl_xor_sync(0xffffffffu, cand, o);
     if (lane == 0 && cand) atomicAdd(P.cand_count, cand);
@@ -727,14 +967,23 @@ __global__ void k_pack_pairs(const uint64_t *keys, int64_t n, int key_bits_s, hb
 size_t eval_smem_bytes(int HW, int n_eq, int use_lut, int tile) {
     const size_t T = (size_t)tile;
     size_t lut = use_lut ? (size_t)8 << n_eq : 0;
-    return lut + (size_t)EV_WARPS * (2 * T * (HW + 1) + 2 * T + T * T / 2) * 4;
+    return lut + (size_t)EV_WARPS * (T * (HW + 1) + T * HW + 2 * T + T * T / 2 + 3 * RING_SLOTS) * 4;
 }
 
+template <int R, bool LOG, bool MULTI, bool RING>
+static int occupancy1(size_t smem) {
+    int nb = 0;
+    cudaFuncSetAttribute(k_eval<R, LOG, MULTI, RING>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_eval<R, LOG, MULTI, RING>, EV_THREADS, smem);
+    return nb;
+}
+
+// the smallest occupancy over the instantiations a launch may pick
 template <int R, bool LOG>
 static int occupancy(size_t smem) {
-    int nb = 0;
-    cudaFuncSetAttribute(k_eval<R, LOG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_eval<R, LOG>, EV_THREADS, smem);
+    int nb = std::min(occupancy1<R, LOG, false, false>(smem), occupancy1<R, LOG, true, false>(smem));
+    if constexpr (!LOG)
+        nb = std::min(nb, std::min(occupancy1<R, LOG, false, true>(smem), occupancy1<R, LOG, true, true>(smem)));
     return nb;
 }
 
@@ -743,14 +992,28 @@ int eval_blocks_per_sm(int tile, int logging, size_t smem) {
     return logging ? occupancy<1, true>(smem) : occupancy<1, false>(smem);
 }
 
+template <int R, bool LOG>
+static void launch(const EvalParams &p, bool multi, bool ring, int grid, size_t smem, cudaStream_t s) {
+    if constexpr (LOG) {
+        if (multi) k_eval<R, true, true, false><<<grid, EV_THREADS, smem, s>>>(p);
+        else k_eval<R, true, false, false><<<grid, EV_THREADS, smem, s>>>(p);
+    } else {
+        if (multi && ring) k_eval<R, false, true, true><<<grid, EV_THREADS, smem, s>>>(p);
+        else if (multi) k_eval<R, false, true, false><<<grid, EV_THREADS, smem, s>>>(p);
+        else if (ring) k_eval<R, false, false, true><<<grid, EV_THREADS, smem, s>>>(p);
+        else k_eval<R, false, false, false><<<grid, EV_THREADS, smem, s>>>(p);
+    }
+}
+
 cudaError_t launch_eval(const EvalParams &p, int grid, size_t smem, int logging, cudaStream_t s) {
     HB_LAUNCHED(1);
+    const bool multi = p.multi != 0, ring = p.refine != 0;
     if (p.tile == 64) {
-        if (logging) k_eval<2, true><<<grid, EV_THREADS, smem, s>>>(p);
-        else k_eval<2, false><<<grid, EV_THREADS, smem, s>>>(p);
+        if (logging) launch<2, true>(p, multi, ring, grid, smem, s);
+        else launch<2, false>(p, multi, ring, grid, smem, s);
     } else {
-        if (logging) k_eval<1, true><<<grid, EV_THREADS, smem, s>>>(p);
-        else k_eval<1, false><<<grid, EV_THREADS, smem, s>>>(p);
+        if (logging) launch<1, true>(p, multi, ring, grid, smem, s);
+        else launch<1, false>(p, multi, ring, grid, smem, s);
     }
     return cudaGetLastError();
 }

@@ -183,6 +183,35 @@ def _columns(cols):
     return arr, keep
 
 
+class PinnedColumn:
+    """A column whose arrays live in page-locked host memory."""
+
+    def __init__(self, col, keep):
+        self.type = col.type
+        self.data = _pin(col.data, keep)
+        self.offsets = _pin(getattr(col, "offsets", None), keep)
+        self.valid = _pin(getattr(col, "valid", None), keep)
+        self._keep = keep
+
+
+def _pin(a, keep):
+    if a is None:
+        return None
+    import torch
+    a = np.ascontiguousarray(a)
+    t = torch.empty(max(a.nbytes, 1), dtype=torch.uint8, pin_memory=True)
+    keep.append(t)
+    v = t.numpy()[:a.nbytes].view(a.dtype).reshape(a.shape)
+    v[...] = a
+    return v
+
+
+def pin_columns(columns):
+    """Copies of host columns in page-locked memory (torch pin_memory): hb_load_table
+    and hb_block_stream DMA such arrays directly instead of staging them."""
+    return [PinnedColumn(c, []) for c in columns]
+
+
 def _preds(md):
     arr = (hb_predicate * len(md))()
     for i, p in enumerate(md):

@@ -50,3 +50,37 @@ def test_stream_equals_resident_r_x_s():
             ctx.add_md(md)
         res = ctx.block()
     assert np.array_equal(got, res)
+
+
+@pytest.mark.parametrize("chunk_bytes", [0, 40_000])
+def test_stream_from_page_locked_memory(chunk_bytes):
+    """S in page-locked host memory is DMA'd per array instead of packed: same pairs."""
+    r, s, mds = synth.config3(n_r=3000, n_s=9000, cards=(15, 150, 1500))
+    locked = hb.pin_columns(s.columns)
+    with hb.Context(device=0, chunk_bytes=chunk_bytes) as ctx:
+        ctx.load_table(0, r.n_rows, r.columns)
+        for md in mds:
+            ctx.add_md(md)
+        got = ctx.block_stream(s.n_rows, locked)
+        pageable = ctx.block_stream(s.n_rows, s.columns)
+        again = ctx.block_stream(s.n_rows, locked)
+    want, _ = oracle.block_hash(r, mds, S=s)
+    assert np.array_equal(got, want)
+    assert np.array_equal(pageable, want)
+    assert np.array_equal(again, want)
+
+
+def test_load_table_from_page_locked_memory():
+    """hb_load_table of page-locked host columns (one DMA per array) equals the staged upload."""
+    r = synth.random_small(seed=61, n=1500, null_rate=0.1)
+    from synth import absdiff, ed, eq, jac
+    mds = [[eq(2), ed(0, 2)], [eq(3), jac(1, 1, 2)], [eq(2), absdiff(4, 0.3)]]
+    res = []
+    for cols in (r.columns, hb.pin_columns(r.columns)):
+        with hb.Context(device=0, chunk_bytes=16_384) as ctx:
+            ctx.load_table(0, r.n_rows, cols)
+            for md in mds:
+                ctx.add_md(md)
+            res.append(ctx.block())
+    assert np.array_equal(res[0], res[1])
+    assert np.array_equal(res[0], oracle.block_literal(r, mds))
