@@ -1057,8 +1057,13 @@ EvalParams make_params(hb_ctx *c, const uint32_t *rec_r, const uint32_t *rec_s, 
         }
         P.base_nops[m] = filterable ? (uint8_t)nb : 255;
     }
+    // the general phase 1: some active MD's blocks have 2..4 distinct base
+    // filters or 4 varying equality keys
     P.multi = 0;
-    for (int m : c->active) P.multi |= (P.base_nops[m] >= 2 && P.base_nops[m] <= 4) ? 1 : 0;
+    for (int m : c->active) {
+        const int ko = c->n_eq_total - __builtin_popcount((unsigned)c->eqset[m]);
+        P.multi |= ((P.base_nops[m] >= 2 && P.base_nops[m] <= 4) || ko == 4) ? 1 : 0;
+    }
     memset(P.screen_op, 255, sizeof(P.screen_op));
     P.refine = 0;
     for (int m = 0; m < (int)c->md_preds.size(); m++) {

@@ -95,7 +95,7 @@ struct EvalParams {
     // (when some screen holds more than phase 1's filter) and batches phase 2
     uint8_t screen_op[MAX_MD][2];
     int32_t refine;
-    int32_t multi;          // some active MD's blocks have 2..4 distinct base filters
+    int32_t multi;          // general phase 1 (2..4 distinct base filters or 4 varying keys in some block)
     int32_t HW;             // hot-record words (multiple of 4): keys, filter operands, bins
     const uint32_t *hot_r;
     const uint32_t *hot_s;

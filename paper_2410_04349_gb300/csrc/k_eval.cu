@@ -594,8 +594,8 @@ __device__ __forceinline__ void phase2(const EvalParams &P, const uint64_t *lut,
     }
 }
 
-// MULTI: tiles whose block has 2..4 distinct base filters take the multi-pass
-// phase 1 (instantiated only for rule sets that have such blocks).  RING: the
+// MULTI: the general phase 1 for rule sets that need it: blocks with 2..4
+// distinct base filters (multi-pass) or 4 varying equality keys.  RING: the
 // survivors are screened (phase 1b) and batched through the warp's ring;
 // otherwise phase 2 runs per tile.
 template <int R, bool LOG, bool MULTI, bool RING>
@@ -731,9 +731,10 @@ __global__ void __launch_bounds__(EV_THREADS, 4) k_eval(const __grid_constant__ 
             // condition; any other owned pair goes on as it is
             const bool filt = !LOG && nbase != 255;
             Mask kmask[R];
-            const bool fast = ko <= 3 && (MULTI || !filt || nbase == 1);
+            // fast path: at most 4 varying keys, and at most one base filter unless MULTI
+            const bool fast = ko <= (MULTI ? 4 : 3) && (MULTI || !filt || nbase == 1);
             if (fast) {
-                const uint32_t own8 = ownmask & 0xffu;
+                const uint32_t own8 = ownmask & 0xffffu;   // bit cb: key-match combination cb is owned
                 const uint32_t kf8 = filt ? (own8 & ~basemask) : own8;
                 const int fk = !filt ? F_NONE : op0.kind == OP_ABS ? F_ABS : F_RANGE;
 #pragma unroll
@@ -743,28 +744,41 @@ __global__ void __launch_bounds__(EV_THREADS, 4) k_eval(const __grid_constant__ 
                     const Mask vm = valid_cols<Mask>(r, nr, nc, diag, pn);
                     Mask km = 0;
                     unsigned ow = 0;
-                    if (MULTI && filt && nbase != 1) {
-                        Mask em[3];
-                        switch (ko) {
-                        case 0: p1_keys<0, T>(hr, hcols, nc, okey, em); break;
-                        case 1: p1_keys<1, T>(hr, hcols, nc, okey, em); break;
-                        case 2: p1_keys<2, T>(hr, hcols, nc, okey, em); break;
-                        default: p1_keys<3, T>(hr, hcols, nc, okey, em); break;
+                    bool done = false;
+                    if constexpr (MULTI) {
+                        if (filt && nbase != 1) {
+                            Mask em[4];
+                            switch (ko) {
+                            case 0: p1_keys<0, T>(hr, hcols, nc, okey, em); break;
+                            case 1: p1_keys<1, T>(hr, hcols, nc, okey, em); break;
+                            case 2: p1_keys<2, T>(hr, hcols, nc, okey, em); break;
+                            case 3: p1_keys<3, T>(hr, hcols, nc, okey, em); break;
+                            default: p1_keys<4, T>(hr, hcols, nc, okey, em); break;
+                            }
+                            Mask fm = 0;
+                            for (int i = 0; i < nbase; i++) {
+                                const Op &op = P.ops[P.base_op[m][i]];
+                                fm |= op.kind == OP_ABS ? p1_filter<F_ABS, T, Mask>(hr, hcols, nc, op)
+                                                        : p1_filter<F_RANGE, T, Mask>(hr, hcols, nc, op);
+                            }
+                            switch (ko) {
+                            case 0: km = p1_combine<0, Mask>(em, fm, own8, kf8, vm, ow); break;
+                            case 1: km = p1_combine<1, Mask>(em, fm, own8, kf8, vm, ow); break;
+                            case 2: km = p1_combine<2, Mask>(em, fm, own8, kf8, vm, ow); break;
+                            case 3: km = p1_combine<3, Mask>(em, fm, own8, kf8, vm, ow); break;
+                            default: km = p1_combine<4, Mask>(em, fm, own8, kf8, vm, ow); break;
+                            }
+                            done = true;
+                        } else if (ko == 4) {
+                            switch (fk) {
+                            case F_NONE: p1_row<4, F_NONE, T>(hr, hcols, nc, okey, op0, own8, kf8, vm, km, ow); break;
+                            case F_RANGE: p1_row<4, F_RANGE, T>(hr, hcols, nc, okey, op0, own8, kf8, vm, km, ow); break;
+                            default: p1_row<4, F_ABS, T>(hr, hcols, nc, okey, op0, own8, kf8, vm, km, ow); break;
+                            }
+                            done = true;
                         }
-                        Mask fm = 0;
-                        for (int i = 0; i < nbase; i++) {
-                            const Op &op = P.ops[P.base_op[m][i]];
-                            fm |= op.kind == OP_ABS ? p1_filter<F_ABS, T, Mask>(hr, hcols, nc, op)
-                                                    : p1_filter<F_RANGE, T, Mask>(hr, hcols, nc, op);
-                        }
-                        switch (ko) {
-                        case 0: km = p1_combine<0, Mask>(em, fm, own8, kf8, vm, ow); break;
-                        case 1: km = p1_combine<1, Mask>(em, fm, own8, kf8, vm, ow); break;
-                        case 2: km = p1_combine<2, Mask>(em, fm, own8, kf8, vm, ow); break;
-                        default: km = p1_combine<3, Mask>(em, fm, own8, kf8, vm, ow); break;
-                        }
-                    } else
-                    switch (ko * 3 + fk) {
+                    }
+                    if (!done) switch (ko * 3 + fk) {
                     case 0: p1_row<0, F_NONE, T>(hr, hcols, nc, okey, op0, own8, kf8, vm, km, ow); break;
                     case 1: p1_row<0, F_RANGE, T>(hr, hcols, nc, okey, op0, own8, kf8, vm, km, ow); break;
                     case 2: p1_row<0, F_ABS, T>(hr, hcols, nc, okey, op0, own8, kf8, vm, km, ow); break;
