@@ -189,6 +189,7 @@ __device__ __forceinline__ uint32_t gram_at(const uint8_t *p, uint32_t k, int q)
 __device__ __forceinline__ uint32_t gram_bin(uint32_t g) { return (g * 0x9E3779B1u) >> 27; }
 
 constexpr int QG_SHORT = 64;       // grams per string handled by one thread
+constexpr int QG_MID = 256;        // grams per string handled by one warp
 constexpr int QG_THREADS = 128;
 constexpr int QG_LONG_MAX = 8192;  // grams per string handled by one block
 
@@ -267,14 +268,71 @@ __device__ void write_gram_feature(uint32_t *r, uint32_t ucount, uint32_t start,
     for (int k = 0; k < 8; k++) r[2 + k] = sig[k];
 }
 
-// Strings with up to 64 grams: one thread sorts its grams in shared memory
-// (insertion sort), removes duplicates and writes them at the string's slot.
+// bitonic sorting network over N registers (every index is a compile-time
+// constant once the loops are unrolled)
+template <int N>
+__device__ __forceinline__ void sort_net(uint32_t (&v)[N]) {
+#pragma unroll
+    for (int size = 2; size <= N; size <<= 1)
+#pragma unroll
+        for (int stride = size / 2; stride > 0; stride >>= 1)
+#pragma unroll
+            for (int i = 0; i < N; i++) {
+                const int j = i ^ stride;
+                if (j > i) {
+                    const bool up = (i & size) == 0;
+                    const uint32_t a = v[i], b = v[j];
+                    const uint32_t lo = min(a, b), hi = max(a, b);
+                    v[i] = up ? lo : hi;
+                    v[j] = up ? hi : lo;
+                }
+            }
+}
+
+// The g (<= N) grams of one string in registers (a rolling window: the gram at
+// k is bytes k .. k+q-1, packed big-endian), padded with 0xFFFFFFFF, sorted by
+// the network; the unique ones are written at dst and counted in 32 bins.
+template <int N>
+__device__ __forceinline__ void grams_sorted(const uint8_t *p, uint32_t g, int q, uint32_t *dst, uint32_t *r,
+                                             uint32_t start) {
+    const uint32_t gmask = q >= 4 ? 0xFFFFFFFFu : ((1u << (8 * q)) - 1u);
+    uint32_t win = 0;
+    if (g > 0)
+        for (int t0 = 0; t0 < q - 1; t0++) win = (win << 8) | p[t0];
+    uint32_t v[N];
+#pragma unroll
+    for (int k = 0; k < N; k++) {
+        if ((uint32_t)k < g) win = ((win << 8) | p[k + q - 1]) & gmask;
+        v[k] = (uint32_t)k < g ? win : 0xFFFFFFFFu;
+    }
+    sort_net<N>(v);
+    uint32_t u = 0;
+    uint32_t sig[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+#pragma unroll
+    for (int k = 0; k < N; k++) {
+        if ((uint32_t)k < g && (k == 0 || v[k] != v[k > 0 ? k - 1 : 0])) {
+            dst[u++] = v[k];
+            const uint32_t bin = gram_bin(v[k]);
+            const uint32_t word = bin >> 2, sh = (bin & 3u) * 8u;
+            const uint32_t cur = (sig[word] >> sh) & 255u;
+            if (cur < 255u) sig[word] += 1u << sh;
+        }
+    }
+    r[0] = u;
+    r[1] = start;
+#pragma unroll
+    for (int k = 0; k < 8; k++) r[2 + k] = sig[k];
+}
+
+// Strings with up to 64 grams: one thread per string sorts its grams in
+// registers with the smallest network that holds them (strings arrive ordered
+// by gram count, so a warp's threads take the same network).
 __global__ void __launch_bounds__(QG_THREADS) k_grams_short(const uint8_t *bytes, const uint32_t *off,
                                                            const uint8_t *valid, int64_t n, int q,
                                                            const uint32_t *order, const uint32_t *gstart,
                                                            uint32_t *grams, uint32_t *rec, int W, int feat,
+                                                           uint32_t *mid_list, unsigned int *n_mid,
                                                            uint32_t *long_list, unsigned int *n_long) {
-    __shared__ uint32_t buf[QG_SHORT][QG_THREADS];
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= n) return;
     const int64_t i = order[t];
@@ -285,47 +343,84 @@ __global__ void __launch_bounds__(QG_THREADS) k_grams_short(const uint8_t *bytes
         for (int k = 0; k < 8; k++) r[2 + k] = 0;
         return;
     }
-    uint32_t a = off[i], len = off[i + 1] - a;
-    uint32_t g = len >= (uint32_t)q ? len - (uint32_t)q + 1u : 0u;
+    const uint32_t a = off[i], len = off[i + 1] - a;
+    const uint32_t g = len >= (uint32_t)q ? len - (uint32_t)q + 1u : 0u;
     if (g > (uint32_t)QG_SHORT) {
-        unsigned int slot = atomicAdd(n_long, 1u);
-        long_list[slot] = (uint32_t)i;
+        if (g <= (uint32_t)QG_MID) mid_list[atomicAdd(n_mid, 1u)] = (uint32_t)i;
+        else long_list[atomicAdd(n_long, 1u)] = (uint32_t)i;
         return;
     }
     const uint8_t *p = bytes + a;
-    uint32_t *s = &buf[0][threadIdx.x];
-    // rolling window: the gram at k is bytes k .. k+q-1, packed big-endian
-    const uint32_t gmask = q >= 4 ? 0xFFFFFFFFu : ((1u << (8 * q)) - 1u);
-    uint32_t win = 0;
-    if (g > 0)
-        for (int t0 = 0; t0 < q - 1; t0++) win = (win << 8) | p[t0];
-    for (uint32_t k = 0; k < g; k++) {
-        win = ((win << 8) | p[k + q - 1]) & gmask;
-        const uint32_t x = win;
-        uint32_t j = k;
-        while (j > 0 && s[(j - 1) * QG_THREADS] > x) {
-            s[j * QG_THREADS] = s[(j - 1) * QG_THREADS];
-            j--;
-        }
-        s[j * QG_THREADS] = x;
-    }
-    uint32_t u = 0;
     uint32_t *dst = grams + gstart[i];
-    uint32_t sig[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    for (uint32_t k = 0; k < g; k++) {
-        uint32_t x = s[k * QG_THREADS];
-        if (k == 0 || x != s[(k - 1) * QG_THREADS]) {
-            dst[u++] = x;
-            uint32_t bin = gram_bin(x);
-            uint32_t word = bin >> 2, sh = (bin & 3u) * 8u;
-            uint32_t cur = (sig[word] >> sh) & 255u;
-            if (cur < 255u) sig[word] += 1u << sh;
+    if (g <= 8) grams_sorted<8>(p, g, q, dst, r, gstart[i]);
+    else if (g <= 16) grams_sorted<16>(p, g, q, dst, r, gstart[i]);
+    else if (g <= 32) grams_sorted<32>(p, g, q, dst, r, gstart[i]);
+    else grams_sorted<64>(p, g, q, dst, r, gstart[i]);
+}
+
+// Strings with 65..256 grams: one warp per string, bitonic sort in the warp's
+// shared memory, the unique grams compacted with warp ballots and counted in
+// 32 bins with shared-memory atomics.
+__global__ void __launch_bounds__(256) k_grams_mid(const uint8_t *bytes, const uint32_t *off, int q,
+                                                  const uint32_t *gstart, uint32_t *grams, uint32_t *rec, int W,
+                                                  int feat, const uint32_t *mid_list, const unsigned int *n_mid) {
+    __shared__ uint32_t sm[8][QG_MID];
+    __shared__ uint32_t bins[8][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+    uint32_t *s = sm[w];
+    const unsigned int nm = *n_mid;
+    for (unsigned int li = blockIdx.x * 8u + (unsigned)w; li < nm; li += gridDim.x * 8u) {
+        const int64_t i = mid_list[li];
+        const uint32_t a = off[i], len = off[i + 1] - a;
+        const uint32_t g = len - (uint32_t)q + 1u;   // 65 .. QG_MID
+        const uint32_t P2 = g <= 128u ? 128u : 256u;
+        const uint8_t *p = bytes + a;
+        for (uint32_t k = lane; k < P2; k += 32) s[k] = k < g ? gram_at(p, k, q) : 0xFFFFFFFFu;
+        bins[w][lane] = 0;
+        __syncwarp();
+        for (uint32_t size = 2; size <= P2; size <<= 1) {
+            for (uint32_t stride = size >> 1; stride > 0; stride >>= 1) {
+                for (uint32_t k = lane; k < P2; k += 32) {
+                    const uint32_t partner = k ^ stride;
+                    if (partner > k) {
+                        const bool up = (k & size) == 0;
+                        const uint32_t x = s[k], y = s[partner];
+                        if ((x > y) == up) {
+                            s[k] = y;
+                            s[partner] = x;
+                        }
+                    }
+                }
+                __syncwarp();
+            }
         }
-    }
-    r[0] = u;
-    r[1] = gstart[i];
+        uint32_t *dst = grams + gstart[i];
+        uint32_t base = 0;
+        for (uint32_t c0 = 0; c0 < g; c0 += 32) {
+            const uint32_t k = c0 + lane;
+            const bool keep = k < g && (k == 0 || s[k] != s[k - 1]);
+            const unsigned bal = __ballot_sync(0xffffffffu, keep);
+            if (keep) {
+                dst[base + __popc(bal & lt)] = s[k];
+                atomicAdd(&bins[w][gram_bin(s[k])], 1u);
+            }
+            base += __popc(bal);
+        }
+        __syncwarp();
+        uint32_t *r = rec + i * W + feat;
+        if (lane < 8) {
+            uint32_t word = 0;
 #pragma unroll
-    for (int k = 0; k < 8; k++) r[2 + k] = sig[k];
+            for (int j = 0; j < 4; j++) word |= min(bins[w][4 * lane + j], 255u) << (8 * j);
+            r[2 + lane] = word;
+        }
+        if (lane == 0) {
+            r[0] = base;
+            r[1] = gstart[i];
+        }
+        __syncwarp();
+    }
 }
 
 // Strings with more grams: one block per string, bitonic sort in shared memory.
@@ -452,7 +547,7 @@ void abs_feature(const DevCol &c, uint32_t *rec, int W, int feat, cudaStream_t s
 }
 
 size_t jac_scratch_bytes(int64_t n) {
-    return (size_t)(n + 1) * 4 * 4 + 2 * QG_BUCKETS * 4 + scan_tmp_bytes(n) + 4096;
+    return (size_t)(n + 1) * 4 * 5 + 2 * QG_BUCKETS * 4 + scan_tmp_bytes(n) + 4096;
 }
 
 // scratch: jac_scratch_bytes(n); grams: capacity >= nbytes of the column (one gram per byte at most)
@@ -464,19 +559,24 @@ void jac_features_impl(const DevCol &c, int q, uint32_t *rec, int W, int feat, u
     uint32_t *gstart = cnt + (n + 1);
     uint32_t *long_list = gstart + (n + 1);
     uint32_t *order = long_list + (n + 1);
-    uint32_t *bucket_count = order + (n + 1);
+    uint32_t *mid_list = order + (n + 1);
+    uint32_t *bucket_count = mid_list + (n + 1);
     uint32_t *bucket_cursor = bucket_count + QG_BUCKETS;
     unsigned int *n_long = bucket_cursor + QG_BUCKETS;
+    unsigned int *n_mid = n_long + 1;
     void *stmp = reinterpret_cast<void *>((reinterpret_cast<uintptr_t>(n_long + 4) + 255) & ~uintptr_t(255));
-    // n_long and the bucket counts are zeroed together
-    cudaMemsetAsync(bucket_count, 0, sizeof(uint32_t) * (2 * QG_BUCKETS + 1), s);
+    // n_long, n_mid and the bucket counts are zeroed together
+    cudaMemsetAsync(bucket_count, 0, sizeof(uint32_t) * (2 * QG_BUCKETS + 2), s);
     HB_LAUNCHED(4);
     k_gram_counts<<<blocks_for(n, ENC_THREADS), ENC_THREADS, 0, s>>>(c.off, c.valid, n, q, cnt, bucket_count);
     k_bucket_scan<<<1, 32, 0, s>>>(bucket_count, bucket_cursor);
     k_bucket_scatter<<<blocks_for(n, ENC_THREADS), ENC_THREADS, 0, s>>>(cnt, n, bucket_cursor, order);
     scan_exclusive_u32(cnt, gstart, n, nullptr, stmp, 0, s);
     k_grams_short<<<blocks_for(n, QG_THREADS), QG_THREADS, 0, s>>>(c.bytes, c.off, c.valid, n, q, order, gstart,
-                                                                  grams, rec, W, feat, long_list, n_long);
+                                                                  grams, rec, W, feat, mid_list, n_mid, long_list,
+                                                                  n_long);
+    HB_LAUNCHED(1);
+    k_grams_mid<<<(unsigned)(n_sm * 8), 256, 0, s>>>(c.bytes, c.off, q, gstart, grams, rec, W, feat, mid_list, n_mid);
     HB_LAUNCHED(1);
     k_grams_long<<<(unsigned)(n_sm * 4), 256, 0, s>>>(c.bytes, c.off, q, gstart, grams, rec, W, feat, long_list,
                                                       n_long, too_long);

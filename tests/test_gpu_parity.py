@@ -196,3 +196,25 @@ def test_edit_distance_across_pattern_words(k):
     want = oracle.block_literal(t, mds)
     assert 0 < len(want) < 20 * 21   # some in-group pairs pass, not all
     assert np.array_equal(got, want)
+
+
+@pytest.mark.parametrize("q", [2, 3, 4])
+def test_jaccard_across_gram_list_sizes(q):
+    """Gram lists sorted by one thread (<= 64 grams), one warp (65..256) and one
+    block (more), with near-duplicates around the threshold."""
+    rng = np.random.default_rng(23 + q)
+    alphabet = list("abcdefgh")
+    rows = []
+    group = 0
+    for length in (30, 66, 67, 120, 200, 258, 259, 300):
+        for rep in range(2):
+            base = "".join(rng.choice(alphabet, length))
+            for v in range(6):
+                rows.append((_edited(rng, base, int(rng.integers(0, length // 6 + 2)), alphabet), group))
+            group += 1
+    t = synth.table_from_rows(["s", "g"], ["string", "int32"], rows)
+    mds = [[eq(1), jac(0, 3, 4, q=q)]]
+    got, _, _ = run_gpu(t, mds)
+    want = oracle.block_literal(t, mds)
+    assert 0 < len(want) < 16 * 15
+    assert np.array_equal(got, want)
