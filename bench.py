@@ -164,7 +164,7 @@ def eval_kernel_traffic():
         sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
     except OSError:
         return None
-    vals = dict(line.split(":", 1) for line in text.splitlines() if ":" in line)
+    vals = dict(line.split(": ", 1) for line in text.splitlines() if ": " in line)
     if vals.get("k_eval.cu sha256[:16]", "").strip() != sha:
         return None
     try:

@@ -231,7 +231,7 @@ extern "C" void hb_destroy(hb_ctx *c) {
                    &c->w_start_s, &c->w_cursor, &c->w_members_r, &c->w_members_s, &c->w_blocks, &c->w_tiles,
                    &c->w_prefix, &c->w_scan, &c->w_out, &c->w_alt, &c->w_sort, &c->w_pairs, &c->w_counters,
                    &c->w_lut, &c->w_log, &c->w_jac, &c->w_jobrows, &c->w_jobcount, &c->w_joboff,
-                   &c->w_small, &c->w_small_meta};
+                   &c->w_small};
     for (Buf *b : bufs) free_buf(c, *b);
     for (int b = 0; b < 2; b++) {
         free_buf(c, c->w_chunk[b]);
@@ -242,6 +242,15 @@ extern "C" void hb_destroy(hb_ctx *c) {
         cudaStreamSynchronize(c->copy_stream);
         cudaStreamDestroy(c->copy_stream);
     }
+    for (hb_ctx::MdLane &L : c->md_lanes) {
+        if (L.stream) cudaStreamSynchronize(L.stream);
+        Buf *lb[] = {&L.table, &L.slot_r, &L.count_r, &L.start_r, &L.cursor, &L.slot_s, &L.count_s, &L.start_s,
+                     &L.scan, &L.meta};
+        for (Buf *b : lb) free_buf(c, *b);
+        if (L.done) cudaEventDestroy(L.done);
+        if (L.stream) cudaStreamDestroy(L.stream);
+    }
+    if (c->md_fork) cudaEventDestroy(c->md_fork);
     if (c->batch_exec) cudaGraphExecDestroy(c->batch_exec);
     if (c->batch_graph) cudaGraphDestroy(c->batch_graph);
     cudaStreamSynchronize(c->stream);
@@ -955,68 +964,85 @@ hb_status build_blocks(hb_ctx *c, const uint32_t *rec_r, int64_t n_r, const uint
     const uint64_t per_md = self ? (uint64_t)(n_r / 2 + 1) : (uint64_t)std::min<int64_t>(n_r, n_s) + 1;
     const uint64_t bc = std::min<uint64_t>(per_md * (uint64_t)std::max(na, 1), 0xFFFFFFF0ull);
     block_cap = (uint32_t)bc;
-    HB_TRY(grow(c, c->w_table, sizeof(uint64_t) * H));
-    HB_TRY(grow(c, c->w_slot_r, sizeof(uint32_t) * (size_t)(n_r + 1)));
-    HB_TRY(grow(c, c->w_count_r, sizeof(uint32_t) * (H + 1)));
-    HB_TRY(grow(c, c->w_start_r, sizeof(uint32_t) * (H + 1)));
-    HB_TRY(grow(c, c->w_cursor, sizeof(uint32_t) * (H + 1)));
     HB_TRY(grow(c, c->w_members_r, sizeof(uint32_t) * (size_t)std::max<int64_t>(n_r, 1) * std::max(na, 1)));
-    if (!self) {
-        HB_TRY(grow(c, c->w_slot_s, sizeof(uint32_t) * (size_t)(n_s + 1)));
-        HB_TRY(grow(c, c->w_count_s, sizeof(uint32_t) * (H + 1)));
-        HB_TRY(grow(c, c->w_start_s, sizeof(uint32_t) * (H + 1)));
+    if (!self)
         HB_TRY(grow(c, c->w_members_s, sizeof(uint32_t) * (size_t)std::max<int64_t>(n_s, 1) * std::max(na, 1)));
-    }
     HB_TRY(grow(c, c->w_blocks, sizeof(BlockDesc) * (size_t)bc));
     HB_TRY(grow(c, c->w_tiles, sizeof(uint64_t) * ((size_t)bc + 1)));
     HB_TRY(grow(c, c->w_prefix, sizeof(uint64_t) * ((size_t)bc + 1)));
-    HB_TRY(grow(c, c->w_scan, std::max(scan_tmp_bytes((int64_t)H + 1), scan_tmp_bytes((int64_t)bc + 1))));
+    HB_TRY(grow(c, c->w_scan, scan_tmp_bytes((int64_t)bc + 1)));
     uint32_t *n_blocks = reinterpret_cast<uint32_t *>(ctr + 3);
     unsigned int *overflow = reinterpret_cast<unsigned int *>(ctr + 4);
     uint32_t *n_packed = reinterpret_cast<uint32_t *>(ctr + 6);
-    if (self) {
-        HB_TRY(grow(c, c->w_small, sizeof(uint32_t) * (size_t)bc));
-        HB_TRY(grow(c, c->w_small_meta, sizeof(uint32_t) * SMALL_META_WORDS));
-        HB_CUDA(cudaMemsetAsync(c->w_small_meta.p, 0, sizeof(uint32_t) * SMALL_META_WORDS, c->stream));
+    uint32_t *small_total = reinterpret_cast<uint32_t *>(ctr + 7);
+    if (self) HB_TRY(grow(c, c->w_small, sizeof(uint32_t) * (size_t)bc));
+    // The MDs are independent: up to 4 lanes (side streams with scratch of their
+    // own) build them at once, forked from and joined to the context's stream;
+    // block descriptors, tile counts and small-block ranges are claimed with
+    // atomics.  MD a runs on lane a % lanes.
+    const int lanes = std::min(std::max(na, 1), MD_LANES);
+    if ((int)c->md_lanes.size() < lanes) c->md_lanes.resize(lanes);
+    if (!c->md_fork) HB_CUDA(cudaEventCreateWithFlags(&c->md_fork, cudaEventDisableTiming));
+    for (int l = 0; l < lanes; l++) {
+        hb_ctx::MdLane &L = c->md_lanes[l];
+        if (!L.stream) HB_CUDA(cudaStreamCreateWithFlags(&L.stream, cudaStreamNonBlocking));
+        if (!L.done) HB_CUDA(cudaEventCreateWithFlags(&L.done, cudaEventDisableTiming));
+        HB_TRY(grow(c, L.table, sizeof(uint64_t) * H));
+        HB_TRY(grow(c, L.slot_r, sizeof(uint32_t) * (size_t)(n_r + 1)));
+        HB_TRY(grow(c, L.count_r, sizeof(uint32_t) * (H + 1)));
+        HB_TRY(grow(c, L.start_r, sizeof(uint32_t) * (H + 1)));
+        HB_TRY(grow(c, L.cursor, sizeof(uint32_t) * (H + 1)));
+        HB_TRY(grow(c, L.scan, scan_tmp_bytes((int64_t)H + 1)));
+        if (self) HB_TRY(grow(c, L.meta, sizeof(uint32_t) * SMALL_META_WORDS));
+        if (!self) {
+            HB_TRY(grow(c, L.slot_s, sizeof(uint32_t) * (size_t)(n_s + 1)));
+            HB_TRY(grow(c, L.count_s, sizeof(uint32_t) * (H + 1)));
+            HB_TRY(grow(c, L.start_s, sizeof(uint32_t) * (H + 1)));
+        }
     }
+    HB_CUDA(cudaEventRecord(c->md_fork, c->stream));
+    for (int l = 0; l < lanes; l++) HB_CUDA(cudaStreamWaitEvent(c->md_lanes[l].stream, c->md_fork, 0));
     for (int a = 0; a < na; a++) {
         const int m = c->active[a];
+        hb_ctx::MdLane &L = c->md_lanes[a % lanes];
+        cudaStream_t st = L.stream;
         int32_t words[MAX_EQ];
         int nk = 0;
         for (int e = 0; e < c->n_eq_total; e++)
             if (c->eqset[m] & (1u << e)) words[nk++] = e;
-        group_build(rec_r, W, n_r, words, nk, as<uint64_t>(c->w_table), H, as<uint32_t>(c->w_slot_r), c->stream);
-        HB_CUDA(cudaMemsetAsync(c->w_count_r.p, 0, sizeof(uint32_t) * (H + 1), c->stream));
-        count_slots(as<uint32_t>(c->w_slot_r), n_r, as<uint32_t>(c->w_count_r), c->stream);
-        scan_exclusive_u32(as<uint32_t>(c->w_count_r), as<uint32_t>(c->w_start_r), (int64_t)H, nullptr, c->w_scan.p,
-                           c->w_scan.bytes, c->stream);
-        HB_CUDA(cudaMemsetAsync(c->w_cursor.p, 0, sizeof(uint32_t) * (H + 1), c->stream));
+        group_build(rec_r, W, n_r, words, nk, as<uint64_t>(L.table), H, as<uint32_t>(L.slot_r), st);
+        HB_CUDA(cudaMemsetAsync(L.count_r.p, 0, sizeof(uint32_t) * (H + 1), st));
+        count_slots(as<uint32_t>(L.slot_r), n_r, as<uint32_t>(L.count_r), st);
+        scan_exclusive_u32(as<uint32_t>(L.count_r), as<uint32_t>(L.start_r), (int64_t)H, nullptr, L.scan.p,
+                           L.scan.bytes, st);
+        HB_CUDA(cudaMemsetAsync(L.cursor.p, 0, sizeof(uint32_t) * (H + 1), st));
         uint32_t *mem_r = as<uint32_t>(c->w_members_r) + (size_t)a * (size_t)std::max<int64_t>(n_r, 1);
-        scatter_slots(as<uint32_t>(c->w_slot_r), n_r, as<uint32_t>(c->w_start_r), as<uint32_t>(c->w_cursor), mem_r,
-                      c->stream);
+        scatter_slots(as<uint32_t>(L.slot_r), n_r, as<uint32_t>(L.start_r), as<uint32_t>(L.cursor), mem_r, st);
         if (self) {
-            emit_blocks_packed(as<uint32_t>(c->w_count_r), as<uint32_t>(c->w_start_r), H, (uint32_t)m,
+            emit_blocks_packed(as<uint32_t>(L.count_r), as<uint32_t>(L.start_r), H, (uint32_t)m,
                                (uint32_t)((size_t)a * (size_t)std::max<int64_t>(n_r, 1)), c->tile,
                                as<BlockDesc>(c->w_blocks), as<uint64_t>(c->w_tiles), n_blocks, n_packed, block_cap,
-                               overflow, as<uint32_t>(c->w_small_meta), as<uint32_t>(c->w_small), block_cap,
-                               reinterpret_cast<uint32_t *>(ctr + 7), c->n_sm, c->stream);
+                               overflow, as<uint32_t>(L.meta), as<uint32_t>(c->w_small), block_cap, small_total,
+                               c->n_sm, st);
         } else {
-            group_probe(rec_s, n_s, rec_r, W, words, nk, as<uint64_t>(c->w_table), H, as<uint32_t>(c->w_slot_s),
-                        c->stream);
-            HB_CUDA(cudaMemsetAsync(c->w_count_s.p, 0, sizeof(uint32_t) * (H + 1), c->stream));
-            count_slots(as<uint32_t>(c->w_slot_s), n_s, as<uint32_t>(c->w_count_s), c->stream);
-            scan_exclusive_u32(as<uint32_t>(c->w_count_s), as<uint32_t>(c->w_start_s), (int64_t)H, nullptr,
-                               c->w_scan.p, c->w_scan.bytes, c->stream);
-            HB_CUDA(cudaMemsetAsync(c->w_cursor.p, 0, sizeof(uint32_t) * (H + 1), c->stream));
+            group_probe(rec_s, n_s, rec_r, W, words, nk, as<uint64_t>(L.table), H, as<uint32_t>(L.slot_s), st);
+            HB_CUDA(cudaMemsetAsync(L.count_s.p, 0, sizeof(uint32_t) * (H + 1), st));
+            count_slots(as<uint32_t>(L.slot_s), n_s, as<uint32_t>(L.count_s), st);
+            scan_exclusive_u32(as<uint32_t>(L.count_s), as<uint32_t>(L.start_s), (int64_t)H, nullptr, L.scan.p,
+                               L.scan.bytes, st);
+            HB_CUDA(cudaMemsetAsync(L.cursor.p, 0, sizeof(uint32_t) * (H + 1), st));
             uint32_t *mem_s = as<uint32_t>(c->w_members_s) + (size_t)a * (size_t)std::max<int64_t>(n_s, 1);
-            scatter_slots(as<uint32_t>(c->w_slot_s), n_s, as<uint32_t>(c->w_start_s), as<uint32_t>(c->w_cursor),
-                          mem_s, c->stream);
-            emit_blocks(as<uint32_t>(c->w_count_r), as<uint32_t>(c->w_start_r), as<uint32_t>(c->w_count_s),
-                        as<uint32_t>(c->w_start_s), H, (uint32_t)m, 0,
+            scatter_slots(as<uint32_t>(L.slot_s), n_s, as<uint32_t>(L.start_s), as<uint32_t>(L.cursor), mem_s, st);
+            emit_blocks(as<uint32_t>(L.count_r), as<uint32_t>(L.start_r), as<uint32_t>(L.count_s),
+                        as<uint32_t>(L.start_s), H, (uint32_t)m, 0,
                         (uint32_t)((size_t)a * (size_t)std::max<int64_t>(n_r, 1)),
                         (uint32_t)((size_t)a * (size_t)std::max<int64_t>(n_s, 1)), c->tile, as<BlockDesc>(c->w_blocks),
-                        as<uint64_t>(c->w_tiles), n_blocks, block_cap, overflow, c->stream);
+                        as<uint64_t>(c->w_tiles), n_blocks, block_cap, overflow, st);
         }
+    }
+    for (int l = 0; l < lanes; l++) {
+        HB_CUDA(cudaEventRecord(c->md_lanes[l].done, c->md_lanes[l].stream));
+        HB_CUDA(cudaStreamWaitEvent(c->stream, c->md_lanes[l].done, 0));
     }
     clamp_blocks(n_blocks, block_cap, c->stream);
     scan_exclusive_u64(as<uint64_t>(c->w_tiles), as<uint64_t>(c->w_prefix), (int64_t)bc, n_blocks, c->w_scan.p,

@@ -89,6 +89,11 @@ static std::vector<int64_t> graph_key(hb_ctx *c, int n_jobs) {
                          &c->w_blocks, &c->w_tiles, &c->w_prefix, &c->w_scan, &c->w_out, &c->w_alt, &c->w_sort,
                          &c->w_pairs, &c->w_counters, &c->w_lut, &c->w_jobrows, &c->w_jobcount, &c->w_joboff};
     for (const Buf *b : bufs) k.push_back((int64_t)(uintptr_t)b->p);
+    k.push_back((int64_t)(uintptr_t)c->w_small.p);
+    for (const hb_ctx::MdLane &L : c->md_lanes) {
+        const Buf *lb[] = {&L.table, &L.slot_r, &L.count_r, &L.start_r, &L.cursor, &L.scan, &L.meta};
+        for (const Buf *b : lb) k.push_back((int64_t)(uintptr_t)b->p);
+    }
     for (const Op &op : c->ops) k.push_back((int64_t)op.need ^ ((int64_t)op.cp << 1) ^ op.kind);
     return k;
 }

@@ -137,7 +137,15 @@ struct hb_ctx {
     cudaGraphExec_t batch_exec = nullptr;
     std::vector<int64_t> batch_graph_key;
     Buf w_jobrows, w_jobcount, w_joboff;
-    Buf w_small, w_small_meta;   // member starts of packed small blocks, packing metadata
+    Buf w_small;   // member starts of packed small blocks
+    // block building of several MDs at once: per-lane scratch, side streams, events
+    struct MdLane {
+        Buf table, slot_r, count_r, start_r, cursor, slot_s, count_s, start_s, scan, meta;
+        cudaStream_t stream = nullptr;
+        cudaEvent_t done = nullptr;
+    };
+    std::vector<MdLane> md_lanes;
+    cudaEvent_t md_fork = nullptr;
     // autotuner cache: job-size signature -> (tile, claim)
     std::vector<std::pair<std::vector<int64_t>, std::pair<int, int>>> tune_cache;
     int claim = 8;

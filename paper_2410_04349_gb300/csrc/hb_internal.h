@@ -26,6 +26,7 @@ constexpr int MAX_MD = 64;
 constexpr int LUT_MAX_EQ = 10; // equality-match -> MD-mask lookup table up to 2^10 entries
 constexpr int SMALL_MAX = 16;  // self-join blocks of 2..SMALL_MAX tuples are packed several to a tile
 constexpr int SMALL_META_WORDS = 160;
+constexpr int MD_LANES = 4;    // MDs whose blocks are built at once (side streams)
 // hot-record words beyond which only the mandatory words (keys, first-predicate
 // filter operands) are staged: 12 keeps four 256-thread evaluation CTAs of
 // 32-tuple tiles resident per SM

@@ -187,7 +187,6 @@ struct SmallMeta {
     static constexpr int OFF = 32;      // [n]: first entry of size class n in the start list
     static constexpr int CURSOR = 64;   // [n]: entries written so far
     static constexpr int TILES = 96;    // [n]: first packed tile of class n; [SMALL_MAX + 1]: this MD's total
-    static constexpr int TOTAL = 128;   // entries of the start list used by all MDs so far
 };
 
 __global__ void k_small_hist(const uint32_t *count, uint64_t cap, uint32_t *meta) {
@@ -204,10 +203,18 @@ __global__ void k_small_hist(const uint32_t *count, uint64_t cap, uint32_t *meta
         if (h[t]) atomicAdd(&meta[SmallMeta::COUNT + t], h[t]);
 }
 
-// one thread: class regions in the start list and packed-tile ranges
+// one thread: this MD's range of the start list (claimed with an atomic, so
+// that MDs built at once get disjoint ranges), its class regions and
+// packed-tile ranges
 __global__ void k_small_plan(uint32_t *meta, int tile, uint32_t small_cap, unsigned int *overflow,
                              uint32_t *small_total) {
-    uint32_t base = meta[SmallMeta::TOTAL], tp = 0;
+    uint32_t md_total = 0, tp = 0;
+    for (int n = 2; n <= SMALL_MAX; n++) md_total += meta[SmallMeta::COUNT + n];
+    uint32_t base = atomicAdd(small_total, md_total);
+    if ((uint64_t)base + md_total > small_cap) {
+        atomicExch(overflow, 1u);
+        base = small_cap;   // every tile of this MD then fails the range check of k_emit_packed
+    }
     for (int n = 2; n <= SMALL_MAX; n++) {
         const uint32_t cnt = meta[SmallMeta::COUNT + n];
         const uint32_t per = (uint32_t)(tile / n);
@@ -218,12 +225,6 @@ __global__ void k_small_plan(uint32_t *meta, int tile, uint32_t small_cap, unsig
         tp += (cnt + per - 1) / per;
     }
     meta[SmallMeta::TILES + SMALL_MAX + 1] = tp;
-    if (base > small_cap) {
-        atomicExch(overflow, 1u);
-        base = small_cap;
-    }
-    meta[SmallMeta::TOTAL] = base;
-    *small_total = base;
 }
 
 __global__ void k_small_scatter(const uint32_t *count, const uint32_t *start, uint64_t cap, uint32_t member_base,
