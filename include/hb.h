@@ -162,7 +162,9 @@ HB_API const char *hb_version(void);
  * one through pinned staging chunks of chunk_bytes; on_device = 1: pointers
  * are device memory of this context's device, copied device to device.  The
  * call returns once every host array has been read.  Replaces any previous
- * table of that side.
+ * table of that side.  HB_ERR_ARG when string offsets do not start at 0, end
+ * at data_bytes or never decrease (host arrays; the last is checked on the
+ * device after the copy, and the side is then left empty).
  */
 HB_API hb_status hb_load_table(hb_ctx *ctx, int32_t side, int64_t n_rows, int32_t n_cols, const hb_column *cols,
                         int32_t on_device);

@@ -168,6 +168,13 @@ hb_status sync_direct(hb_ctx *c) {
     return HB_OK;
 }
 
+// offsets of a string column must not decrease: bad[0] = the first row i with
+// off[i + 1] < off[i] (0xFFFFFFFF when none)
+__global__ void k_check_offsets(const uint32_t *off, int64_t n, unsigned int *bad) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        if (off[i + 1] < off[i]) atomicMin(bad, (unsigned int)i);
+}
+
 static hb_status copy_in(hb_ctx *c, void *dst, const void *src, size_t bytes, bool on_device) {
     if (bytes == 0) return HB_OK;
     if (on_device) {
@@ -231,7 +238,7 @@ extern "C" void hb_destroy(hb_ctx *c) {
                    &c->w_start_s, &c->w_cursor, &c->w_members_r, &c->w_members_s, &c->w_blocks, &c->w_tiles,
                    &c->w_prefix, &c->w_scan, &c->w_out, &c->w_alt, &c->w_sort, &c->w_pairs, &c->w_counters,
                    &c->w_lut, &c->w_log, &c->w_jac, &c->w_jobrows, &c->w_jobcount, &c->w_joboff,
-                   &c->w_small};
+                   &c->w_small, &c->w_check};
     for (Buf *b : bufs) free_buf(c, *b);
     for (int b = 0; b < 2; b++) {
         free_buf(c, c->w_chunk[b]);
@@ -278,13 +285,9 @@ extern "C" hb_status hb_load_table(hb_ctx *c, int32_t side, int64_t n_rows, int3
         if (col.type == HB_COL_STRING) {
             if (!col.offsets) return fail(HB_ERR_ARG, "hb_load_table: string column " + std::to_string(k) + " has no offsets");
             if (!on_device) {
+                // the ends here; that the offsets never decrease is checked on the
+                // device once they are there (k_check_offsets)
                 if (col.offsets[0] != 0) return fail(HB_ERR_ARG, "hb_load_table: offsets[0] must be 0");
-                // branch-free scan first (vectorises); the row is located only on failure
-                uint32_t dec = 0;
-                for (int64_t i = 0; i < n_rows; i++) dec |= col.offsets[i + 1] < col.offsets[i] ? 1u : 0u;
-                for (int64_t i = 0; dec && i < n_rows; i++)
-                    if (col.offsets[i + 1] < col.offsets[i])
-                        return fail(HB_ERR_ARG, "hb_load_table: offsets of column " + std::to_string(k) + " decrease at row " + std::to_string(i));
                 if ((uint64_t)col.offsets[n_rows] != col.data_bytes)
                     return fail(HB_ERR_ARG, "hb_load_table: data_bytes != offsets[n] in column " + std::to_string(k));
             }
@@ -296,6 +299,11 @@ extern "C" hb_status hb_load_table(hb_ctx *c, int32_t side, int64_t n_rows, int3
     c->planned = false;
     S.n = n_rows;
     S.cols.resize(n_cols);
+    const bool check = !on_device && n_cols > 0 && n_rows > 0;
+    if (check) {
+        HB_TRY(grow(c, c->w_check, sizeof(unsigned int) * (size_t)n_cols));
+        HB_CUDA(cudaMemsetAsync(c->w_check.p, 0xFF, sizeof(unsigned int) * (size_t)n_cols, c->stream));
+    }
     for (int k = 0; k < n_cols; k++) {
         const hb_column &col = cols[k];
         DevCol &d = S.cols[k];
@@ -312,6 +320,11 @@ extern "C" hb_status hb_load_table(hb_ctx *c, int32_t side, int64_t n_rows, int3
             S.allocs.push_back(p);
             d.off = static_cast<uint32_t *>(p);
             HB_TRY(copy_in(c, d.off, col.offsets, sizeof(uint32_t) * (n_rows + 1), on_device));
+            if (check) {
+                HB_LAUNCHED(1);
+                k_check_offsets<<<(unsigned)std::min<int64_t>((n_rows + 255) / 256, 4 * c->n_sm), 256, 0, c->stream>>>(
+                    d.off, n_rows, as<unsigned int>(c->w_check) + k);
+            }
         } else {
             HB_TRY(dmalloc(c, &p, 4 * (size_t)n_rows + 16));
             S.allocs.push_back(p);
@@ -324,6 +337,20 @@ extern "C" hb_status hb_load_table(hb_ctx *c, int32_t side, int64_t n_rows, int3
             d.valid = static_cast<uint8_t *>(p);
             HB_TRY(copy_in(c, d.valid, col.valid, (size_t)n_rows, on_device));
         }
+    }
+    if (check) {
+        std::vector<unsigned int> bad(n_cols);
+        HB_CUDA(cudaMemcpyAsync(bad.data(), c->w_check.p, sizeof(unsigned int) * (size_t)n_cols, cudaMemcpyDeviceToHost,
+                                c->stream));
+        HB_CUDA(cudaStreamSynchronize(c->stream));
+        c->direct_pending = false;
+        for (int k = 0; k < n_cols; k++)
+            if (bad[k] != 0xFFFFFFFFu) {
+                free_side(c, S);
+                S.n = 0;
+                return fail(HB_ERR_ARG, "hb_load_table: offsets of column " + std::to_string(k) + " decrease at row " +
+                                            std::to_string(bad[k]));
+            }
     }
     HB_TRY(sync_direct(c));
     if (side == 0) c->stats.n_rows_r = n_rows;

@@ -138,6 +138,7 @@ struct hb_ctx {
     std::vector<int64_t> batch_graph_key;
     Buf w_jobrows, w_jobcount, w_joboff;
     Buf w_small;   // member starts of packed small blocks
+    Buf w_check;   // per column: first row whose string offsets decrease (hb_load_table)
     // block building of several MDs at once: per-lane scratch, side streams, events
     struct MdLane {
         Buf table, slot_r, count_r, start_r, cursor, slot_s, count_s, start_s, scan, meta;
