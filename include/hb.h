@@ -198,9 +198,11 @@ HB_API hb_status hb_block_device(hb_ctx *ctx, hb_pair **dev_pairs_out, int64_t *
 /*
  * R x S with S streamed from host memory: R must be loaded (side 0); S's
  * columns (host pointers, same column order as used by the MDs' col_s) are
- * copied in chunks of chunk_bytes through pinned buffers, and every chunk is
- * encoded, blocked and evaluated while the next one is in flight.  Output as
- * hb_block (tid2 indexes S as given).
+ * copied in chunks of at most chunk_bytes (straight from the caller's arrays
+ * when all of them are page-locked, else through two pinned staging buffers),
+ * and every chunk is encoded, blocked and evaluated while the next one is in
+ * flight.  The call returns after the last chunk.  Output as hb_block (tid2
+ * indexes S as given).
  */
 HB_API hb_status hb_block_stream(hb_ctx *ctx, int64_t n_rows_s, int32_t n_cols, const hb_column *cols_s,
                           hb_pair **pairs_out, int64_t *n_out);

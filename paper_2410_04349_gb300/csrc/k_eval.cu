@@ -1,14 +1,16 @@
 // Pair evaluation: the hot loop of blocking.
 //
 // Work items are tiles of a block's pair space (T x T tuples, the upper
-// triangle for a self-join).  A persistent grid of warps claims tiles from one
-// atomic counter (task stealing in the form of a shared queue, Section 5.2).
-// Each warp works on one tile at a time in two phases:
+// triangle for a self-join), or packed tiles holding several small self-join
+// blocks side by side.  A persistent grid of warps claims tiles (8 per claim)
+// from one atomic counter (task stealing in the form of a shared queue,
+// Section 5.2).  Each warp works on one tile at a time:
 //
 //  phase 1 (every pair, branch-light): the warp stages the tile's "hot"
-//    records (equality codes and the filter operand of each MD's first
-//    predicate) in shared memory, rows tuple-major and columns word-major;
-//    lane = row, loop over the columns 8 at a time.  For every pair:
+//    records (equality codes, the filter operand of each MD's first predicate
+//    and, within a word budget, bins and second-predicate operands) in shared
+//    memory, rows tuple-major and columns word-major; lane = row, loop over
+//    the columns 8 at a time.  For every pair:
 //      - equality keys: bit e of E is set when both tuples hold the same
 //        present code of key e; the MDs whose keys are all in E are alive;
 //      - owner check: the pair is handled only in the block of the lowest
@@ -17,10 +19,15 @@
 //        block, the cheap necessary condition of each one's first predicate
 //        (length / size filter, or the |a-b| test itself) rejects most pairs
 //        at once: a pair survives if one of them passes;
-//    the owner / keep decisions come from per-tile bit masks indexed by the
-//    combination of other-key matches, and the filter is a per-row interval
-//    test; each lane collects its kept columns in a bit mask, and one warp
-//    prefix sum per tile turns the masks into a per-warp survivor list.
+//    the owner / keep decisions come from per-tile tables indexed by the
+//    combination of other-key matches, applied to per-row match masks, and a
+//    filter is a per-row interval test; each lane collects its kept columns
+//    in a bit mask, and one warp prefix sum per tile turns the masks into a
+//    per-warp survivor list.
+//  phase 1b (when the hot record holds more than phase 1 used): each survivor
+//    is screened with the staged necessary conditions of every alive MD's
+//    first two predicates (shared memory only) and the rest join a per-warp
+//    ring spanning tiles, so phase 2 always runs 32 pairs at a time.
 //  phase 2 (survivors, 32 at a time, all lanes busy): the sequential execution
 //    path of Section 5.1 on the full records: non-equality predicates in plan
 //    order, each evaluated once per pair and its result applied to every MD
