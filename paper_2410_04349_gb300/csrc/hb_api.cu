@@ -745,8 +745,12 @@ static hb_status finish_plan(hb_ctx *c, int mode, const std::vector<double> &sp,
         }
         c->ops.push_back(op);
     }
-    // hot record: keys, first-op filter operands, then within HOT_BUDGET the
-    // bins of first ops, second-op filter operands and their bins
+    // hot record (what phases 1 and 1b of the evaluation read from shared
+    // memory): the equality codes and the filter operand (length, gram count
+    // or value) of each MD's first program predicate; then, while the record
+    // stays within HOT_BUDGET words, the character / gram bins of those
+    // predicates, the filter operands of each MD's second predicate and their
+    // bins (MDs by decreasing estimated pass rate of their first predicate)
     c->hot_map.clear();
     for (int e = 0; e < c->n_eq_total; e++) c->hot_map.push_back(e);
     std::vector<int> hot_word(c->groups.size(), -1), hot_bins(c->groups.size(), -1);
@@ -773,9 +777,16 @@ static hb_status finish_plan(hb_ctx *c, int mode, const std::vector<double> &sp,
         hot_bins[g] = (int)c->hot_map.size();
         for (int w = 0; w < nb; w++) c->hot_map.push_back(G.word + 2 + w);
     };
-    for (int m = 0; m < n_md; m++)
+    // the optional words go first to the MDs whose first predicate lets the
+    // most pairs through (largest estimated pass rate sp): their survivors
+    // gain the most from a screen in shared memory
+    std::vector<int> by_pass(n_md);
+    std::iota(by_pass.begin(), by_pass.end(), 0);
+    auto pass_of = [&](int m) { return (mdops[m][0] >= 0 && !sp.empty()) ? sp[program[mdops[m][0]]] : 0.0; };
+    std::stable_sort(by_pass.begin(), by_pass.end(), [&](int x, int y) { return pass_of(x) > pass_of(y); });
+    for (int m : by_pass)
         if (mdops[m][0] >= 0) add_bins(mdops[m][0]);
-    for (int m = 0; m < n_md; m++) {
+    for (int m : by_pass) {
         if (mdops[m][1] < 0) continue;
         const int g = group_of(mdops[m][1]);
         if (hot_word[g] < 0 && (int)c->hot_map.size() + 1 <= HOT_BUDGET) {
@@ -783,7 +794,7 @@ static hb_status finish_plan(hb_ctx *c, int mode, const std::vector<double> &sp,
             c->hot_map.push_back(c->groups[g].word);
         }
     }
-    for (int m = 0; m < n_md; m++)
+    for (int m : by_pass)
         if (mdops[m][1] >= 0) add_bins(mdops[m][1]);
     while (c->hot_map.size() % 4) c->hot_map.push_back(-1);
     c->HW = (int)c->hot_map.size();
