@@ -234,7 +234,7 @@ extern "C" void hb_destroy(hb_ctx *c) {
     free_side(c, c->side[0]);
     free_side(c, c->side[1]);
     free_dicts(c);
-    Buf *bufs[] = {&c->w_table, &c->w_slot_r, &c->w_slot_s, &c->w_count_r, &c->w_count_s, &c->w_start_r,
+    Buf *bufs[] = {&c->w_slot_r, &c->w_slot_s, &c->w_count_s,
                    &c->w_start_s, &c->w_cursor, &c->w_members_r, &c->w_members_s, &c->w_blocks, &c->w_tiles,
                    &c->w_prefix, &c->w_scan, &c->w_out, &c->w_alt, &c->w_sort, &c->w_pairs, &c->w_counters,
                    &c->w_lut, &c->w_log, &c->w_jac, &c->w_jobrows, &c->w_jobcount, &c->w_joboff,
@@ -1335,10 +1335,16 @@ extern "C" hb_status hb_get_stats(const hb_ctx *c, hb_stats *out) {
         for (auto &col : c->side[s].cols) tot += col.nbytes + (col.off ? 4 * (col.n + 1) : 0) + (col.vals ? 4 * col.n : 0);
         if (c->side[s].rec) tot += (size_t)4 * c->W * c->side[s].n;
     }
-    const Buf *bufs[] = {&c->w_table, &c->w_slot_r, &c->w_slot_s, &c->w_count_r, &c->w_count_s, &c->w_start_r,
-                         &c->w_start_s, &c->w_cursor, &c->w_members_r, &c->w_members_s, &c->w_blocks, &c->w_tiles,
-                         &c->w_prefix, &c->w_scan, &c->w_out, &c->w_alt, &c->w_sort, &c->w_pairs};
+    const Buf *bufs[] = {&c->w_slot_r, &c->w_slot_s, &c->w_count_s, &c->w_start_s, &c->w_cursor, &c->w_members_r,
+                         &c->w_members_s, &c->w_blocks, &c->w_tiles, &c->w_prefix, &c->w_scan, &c->w_out,
+                         &c->w_alt, &c->w_sort, &c->w_pairs, &c->w_small, &c->w_jac, &c->w_lut, &c->w_log,
+                         &c->w_chunk[0], &c->w_chunk[1]};
     for (const Buf *b : bufs) tot += b->bytes;
+    for (const hb_ctx::MdLane &L : c->md_lanes) {
+        const Buf *lb[] = {&L.table, &L.slot_r, &L.count_r, &L.start_r, &L.cursor, &L.slot_s, &L.count_s,
+                           &L.start_s, &L.scan, &L.meta};
+        for (const Buf *b : lb) tot += b->bytes;
+    }
     out->device_bytes = (int64_t)tot;
     out->kernel_launches = (int64_t)g_kernel_launches.load();
     return HB_OK;

@@ -85,7 +85,7 @@ static std::vector<int64_t> graph_key(hb_ctx *c, int n_jobs) {
     std::vector<int64_t> k = {c->side[0].n, n_jobs, c->out_cap, c->tile, c->claim, c->W, c->HW,
                               (int64_t)c->ops.size(), (int64_t)(uintptr_t)c->side[0].rec,
                               (int64_t)(uintptr_t)c->side[0].hot};
-    const Buf *bufs[] = {&c->w_table, &c->w_slot_r, &c->w_count_r, &c->w_start_r, &c->w_cursor, &c->w_members_r,
+    const Buf *bufs[] = {&c->w_members_r,
                          &c->w_blocks, &c->w_tiles, &c->w_prefix, &c->w_scan, &c->w_out, &c->w_alt, &c->w_sort,
                          &c->w_pairs, &c->w_counters, &c->w_lut, &c->w_jobrows, &c->w_jobcount, &c->w_joboff};
     for (const Buf *b : bufs) k.push_back((int64_t)(uintptr_t)b->p);

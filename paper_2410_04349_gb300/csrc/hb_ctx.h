@@ -112,7 +112,7 @@ struct hb_ctx {
     std::vector<uint64_t *> dict;
     std::vector<uint64_t> dict_cap;
     // work buffers
-    Buf w_table, w_slot_r, w_slot_s, w_count_r, w_count_s, w_start_r, w_start_s, w_cursor, w_members_r,
+    Buf w_slot_r, w_slot_s, w_count_s, w_start_s, w_cursor, w_members_r,
         w_members_s, w_blocks, w_tiles, w_prefix, w_scan, w_out, w_alt, w_sort, w_pairs, w_counters, w_lut, w_log,
         w_jac;
     int64_t out_cap = 0;
