@@ -7,7 +7,8 @@ never import it, and it imports nothing from them.
 Contents:
   * hb_oracle.cpp   - the blocking definition of Section 2 ("Semantics",
                       "Blocking") as a literal nested loop, a grouped variant,
-                      per-pair checks and the single predicates;
+                      per-pair checks, the single predicates and an
+                      owner-rule pass for the benchmark's full sizes;
   * plan.py         - the execution-plan generator of Section 4.2 (ordering by
                       cost-effectiveness, execution tree, witness probability,
                       edge scores, DFS order) and its flattening into the
@@ -74,6 +75,8 @@ def lib():
         L.or_block_literal.argtypes = [i64, i32, P, i64, i32, P, i32, P, P, P, i64]
         L.or_block_hash.restype = i64
         L.or_block_hash.argtypes = [i64, i32, P, i64, i32, P, i32, P, P, i32, P, i64, P, i32]
+        L.or_block_owned.restype = i64
+        L.or_block_owned.argtypes = [i64, i32, P, i64, i32, P, i32, P, P, i32, i32, P, i64, P]
         L.or_check_pairs.restype = None
         L.or_check_pairs.argtypes = [i64, i32, P, i64, i32, P, i32, P, P, P, i64, P]
         L.or_pred_verdicts.restype = None
@@ -186,6 +189,29 @@ def block_hash(R, mds, S=None, threads=None, count_candidates=True):
     buf = np.zeros(max(n, 1), np.uint64)
     lib().or_block_hash(*a, len(mds), starts.ctypes.data, preds, threads, buf.ctypes.data, n, None, 0)
     return _unpack(buf, n), int(cand[0])
+
+
+def block_owned(R, mds, S=None, threads=None, evaluate=True):
+    """(pairs [n,2] ascending, candidate count) by the owner rule: each pair
+    that agrees on some MD's equality predicates is looked at once, in the
+    group of the lowest such MD; for relations of the benchmark's full sizes.
+    evaluate=False only counts the candidates (pairs is then empty)."""
+    r, s, a = _args(R, S)
+    starts, preds = _rules(mds)
+    threads = threads or os.cpu_count() or 1
+    cand = np.zeros(1, np.int64)
+    if not evaluate:
+        lib().or_block_owned(*a, len(mds), starts.ctypes.data, preds, threads, 0, None, 0, cand.ctypes.data)
+        return np.zeros((0, 2), np.int64), int(cand[0])
+    # one pass: the result is written into a buffer grown until it fits
+    cap = 1 << 20
+    while True:
+        buf = np.zeros(cap, np.uint64)
+        n = lib().or_block_owned(*a, len(mds), starts.ctypes.data, preds, threads, 1, buf.ctypes.data, cap,
+                                 cand.ctypes.data)
+        if n <= cap:
+            return _unpack(buf, n), int(cand[0])
+        cap = int(n)
 
 
 def check_pairs(R, mds, pairs, S=None) -> np.ndarray:

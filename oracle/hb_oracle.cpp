@@ -190,6 +190,122 @@ int64_t emit(const std::vector<uint64_t> &v, uint64_t *out, int64_t cap) {
 
 }  // namespace
 
+namespace {
+
+struct GramSets { int side, col, q; std::vector<std::vector<std::string>> rows; };
+
+void group_ids(const or_pred *preds, int32_t lo, int32_t hi, const Rel &R, const Rel *S,
+               std::vector<int64_t> &gr, std::vector<int64_t> &gs, std::vector<std::vector<int64_t>> &left,
+               std::vector<std::vector<int64_t>> &right) {
+    bool has_eq = false;
+    for (int32_t k = lo; k < hi; k++) has_eq = has_eq || is_equality(preds[k]);
+    gr.assign((size_t)R.n, -1);
+    if (S) gs.assign((size_t)S->n, -2);
+    left.clear();
+    right.clear();
+    if (!has_eq) {
+        left.emplace_back();
+        for (int64_t i = 0; i < R.n; i++) { gr[(size_t)i] = 0; left[0].push_back(i); }
+        if (S) {
+            right.emplace_back();
+            for (int64_t j = 0; j < S->n; j++) { gs[(size_t)j] = 0; right[0].push_back(j); }
+        }
+        return;
+    }
+    std::unordered_map<std::string, int64_t> index;
+    std::string key;
+    for (int64_t i = 0; i < R.n; i++) {
+        if (!group_key(preds, lo, hi, R, i, true, key)) continue;
+        auto it = index.find(key);
+        if (it == index.end()) {
+            it = index.emplace(key, (int64_t)left.size()).first;
+            left.emplace_back();
+        }
+        gr[(size_t)i] = it->second;
+        left[(size_t)it->second].push_back(i);
+    }
+    if (!S) return;
+    right.resize(left.size());
+    for (int64_t j = 0; j < S->n; j++) {
+        if (!group_key(preds, lo, hi, *S, j, false, key)) { gs[(size_t)j] = -1; continue; }
+        auto it = index.find(key);
+        if (it == index.end()) continue;
+        gs[(size_t)j] = it->second;
+        right[(size_t)it->second].push_back(j);
+    }
+}
+
+/* the q-gram set of every row of one string column, as sorted unique substrings */
+void gram_rows(const Rel &T, int col, int q, int n_threads, std::vector<std::vector<std::string>> &rows) {
+    rows.assign((size_t)T.n, {});
+    const or_col &c = T.cols[col];
+    std::atomic<int64_t> next{0};
+    auto work = [&]() {
+        for (;;) {
+            int64_t i0 = next.fetch_add(4096);
+            if (i0 >= T.n) break;
+            for (int64_t i = i0; i < std::min(T.n, i0 + 4096); i++) {
+                if (!present(c, i)) continue;
+                std::set<std::string> g = qgrams(bytes_of(c, i), q);
+                rows[(size_t)i].assign(g.begin(), g.end());
+            }
+        }
+    };
+    std::vector<std::thread> th;
+    for (int t = 1; t < std::max(n_threads, 1); t++) th.emplace_back(work);
+    work();
+    for (auto &x : th) x.join();
+}
+
+/* |A n B| of two sorted unique lists */
+uint64_t common(const std::vector<std::string> &A, const std::vector<std::string> &B) {
+    size_t a = 0, b = 0;
+    uint64_t I = 0;
+    while (a < A.size() && b < B.size()) {
+        if (A[a] < B[b]) a++;
+        else if (B[b] < A[a]) b++;
+        else { I++; a++; b++; }
+    }
+    return I;
+}
+
+struct Owned {
+    int n_md;
+    const int32_t *md_start;
+    const or_pred *preds;
+    const Rel &R, &S;
+    const std::vector<GramSets> &grams;
+    bool self;
+
+    const std::vector<std::vector<std::string>> *gram_of(int side, int col, int q) const {
+        if (self) side = 0;   /* a self-join reads both tuples from R */
+        for (const GramSets &g : grams)
+            if (g.side == side && g.col == col && g.q == q) return &g.rows;
+        return nullptr;
+    }
+
+    bool holds_p(const or_pred &p, int64_t i, int64_t j) const {
+        if (p.kind != 3) return holds(p, R, i, S, j);
+        if (!present(R.cols[p.col_t], i) || !present(S.cols[p.col_s], j)) return false;
+        const auto *A = gram_of(0, p.col_t, p.q), *B = gram_of(1, p.col_s, p.q);
+        if (!A || !B) return holds(p, R, i, S, j);
+        const std::vector<std::string> &a = (*A)[(size_t)i], &b = (*B)[(size_t)j];
+        const uint64_t I = common(a, b), U = a.size() + b.size() - I;
+        return I * (uint64_t)p.den >= (uint64_t)p.num * U;
+    }
+
+    bool dnf(int64_t i, int64_t j) const {
+        for (int m = 0; m < n_md; m++) {
+            bool all = true;
+            for (int32_t k = md_start[m]; k < md_start[m + 1] && all; k++) all = holds_p(preds[k], i, j);
+            if (all) return true;
+        }
+        return false;
+    }
+};
+
+}  // namespace
+
 extern "C" {
 
 int64_t or_edit_distance(const uint8_t *a, int64_t la, const uint8_t *b, int64_t lb) {
@@ -314,6 +430,117 @@ int64_t or_block_hash(int64_t nR, int32_t ncR, const or_col *R, int64_t nS, int3
             *n_candidates = -1;
         }
     }
+    return emit(all, out, cap);
+}
+
+/*
+ * Same result as or_block_hash, for relations too large for it (the
+ * benchmark's full sizes), in two plain steps:
+ *
+ *  1. every tuple gets, per MD, the id of its group of equal values of that
+ *     MD's equality predicates (-1 when one of them is missing; an MD without
+ *     equality predicates puts every tuple in group 0; an S tuple whose values
+ *     no R tuple holds gets -2);
+ *  2. a pair that agrees on some MD's equality predicates is looked at once,
+ *     in the group of the lowest-numbered such MD (two tuples agree on MD m'
+ *     iff their group ids of m' are equal and not negative), counted as a
+ *     candidate, and the whole disjunction is evaluated for it.
+ *
+ * Large groups are cut into ranges of their first tuple so that all threads
+ * stay busy.  The q-gram set of each string a Jaccard predicate reads is
+ * built once per row (the same set of substrings as qgrams(), kept sorted),
+ * because the full sizes evaluate it billions of times.  evaluate = 0 only
+ * counts the candidates (out may then be NULL).
+ */
+int64_t or_block_owned(int64_t nR, int32_t ncR, const or_col *R, int64_t nS, int32_t ncS, const or_col *S,
+                       int32_t n_md, const int32_t *md_start, const or_pred *preds, int32_t n_threads,
+                       int32_t evaluate, uint64_t *out, int64_t cap, int64_t *n_candidates) {
+    Rel r{nR, ncR, R};
+    Rel s = S ? Rel{nS, ncS, S} : r;
+    const bool self = (S == nullptr);
+    const int nt = std::max(n_threads, 1);
+    // 1. group ids per MD
+    std::vector<std::vector<int64_t>> gid_r((size_t)n_md), gid_s((size_t)n_md);
+    std::vector<std::vector<std::vector<int64_t>>> left((size_t)n_md), right((size_t)n_md);
+    for (int m = 0; m < n_md; m++)
+        group_ids(preds, md_start[m], md_start[m + 1], r, self ? nullptr : &s, gid_r[(size_t)m], gid_s[(size_t)m],
+                  left[(size_t)m], right[(size_t)m]);
+    const std::vector<std::vector<int64_t>> &gid_c = self ? gid_r : gid_s;
+    // q-gram sets of the string columns Jaccard predicates read
+    std::vector<GramSets> grams;
+    if (evaluate) {
+        for (int32_t k = 0; k < md_start[n_md]; k++) {
+            const or_pred &p = preds[k];
+            if (p.kind != 3) continue;
+            for (int side = 0; side < (self ? 1 : 2); side++) {
+                const int col = side == 0 ? p.col_t : p.col_s;
+                bool have = false;
+                for (const GramSets &g : grams) have = have || (g.side == side && g.col == col && g.q == p.q);
+                if (have) continue;
+                grams.push_back(GramSets{side, col, p.q, {}});
+                gram_rows(side == 0 ? r : s, col, p.q, nt, grams.back().rows);
+            }
+        }
+    }
+    // 2. work units: (MD, group, range of the first tuple's position) of at most ~2^21 pairs
+    struct Unit { int m; int64_t g, a0, a1; };
+    std::vector<Unit> units;
+    for (int m = 0; m < n_md; m++) {
+        for (size_t g = 0; g < left[(size_t)m].size(); g++) {
+            const int64_t nl = (int64_t)left[(size_t)m][g].size();
+            const int64_t nrt = self ? nl : (int64_t)right[(size_t)m][g].size();
+            if (nl == 0 || nrt == 0 || (self && nl < 2)) continue;
+            int64_t a = 0;
+            while (a < nl) {
+                int64_t b = a, pairs = 0;
+                while (b < nl && pairs < (1 << 21)) { pairs += self ? (nl - 1 - b) : nrt; b++; }
+                units.push_back(Unit{m, (int64_t)g, a, b});
+                a = b;
+            }
+        }
+    }
+    Owned ev{n_md, md_start, preds, r, s, grams, self};
+    std::atomic<size_t> next{0};
+    std::vector<std::vector<uint64_t>> res((size_t)nt);
+    std::vector<int64_t> cand((size_t)nt, 0);
+    auto owner_is = [&](int m, int64_t i, int64_t j) {
+        for (int mm = 0; mm < m; mm++) {
+            const int64_t x = gid_r[(size_t)mm][(size_t)i];
+            if (x >= 0 && x == gid_c[(size_t)mm][(size_t)j]) return false;
+        }
+        return true;
+    };
+    auto work = [&](int t) {
+        for (;;) {
+            const size_t u = next.fetch_add(1);
+            if (u >= units.size()) break;
+            const Unit &U = units[u];
+            const std::vector<int64_t> &L = left[(size_t)U.m][(size_t)U.g];
+            const std::vector<int64_t> &Rt = self ? L : right[(size_t)U.m][(size_t)U.g];
+            for (int64_t a = U.a0; a < U.a1; a++) {
+                for (int64_t b = self ? a + 1 : 0; b < (int64_t)Rt.size(); b++) {
+                    int64_t i = L[(size_t)a], j = Rt[(size_t)b];
+                    if (self && i > j) std::swap(i, j);
+                    if (!owner_is(U.m, i, j)) continue;
+                    cand[(size_t)t]++;
+                    if (evaluate && ev.dnf(i, j)) res[(size_t)t].push_back(((uint64_t)i << 32) | (uint64_t)j);
+                }
+            }
+        }
+    };
+    std::vector<std::thread> th;
+    for (int t = 1; t < nt; t++) th.emplace_back(work, t);
+    work(0);
+    for (auto &x : th) x.join();
+    std::vector<uint64_t> all;
+    int64_t c = 0;
+    for (int t = 0; t < nt; t++) {
+        c += cand[(size_t)t];
+        all.insert(all.end(), res[(size_t)t].begin(), res[(size_t)t].end());
+    }
+    std::sort(all.begin(), all.end());
+    all.erase(std::unique(all.begin(), all.end()), all.end());
+    if (n_candidates) *n_candidates = c;
     return emit(all, out, cap);
 }
 

@@ -184,3 +184,42 @@ def test_config1_literal_equals_hash():
     h, cand = oracle.block_hash(t, mds)
     assert np.array_equal(lit, h)
     assert len(lit) > 0 and cand >= len(lit)
+
+
+@pytest.mark.parametrize("null_rate", [0.0, 0.15])
+def test_owner_pass_matches_python_loop(null_rate):
+    """The owner-rule pass (each candidate looked at once, big groups split
+    over threads, q-gram sets built once per row) gives the nested loop's
+    pairs and the brute-force candidate count, self-join and R x S."""
+    t = synth.random_small(seed=41, n=90, null_rate=null_rate)
+    mds = small_mds()
+    py = py_block(t, mds)
+    for threads in (1, 3):
+        got, cand = oracle.block_owned(t, mds, threads=threads)
+        assert np.array_equal(got, py)
+        assert cand == py_candidates(t, mds)
+    assert oracle.block_owned(t, mds, evaluate=False)[1] == cand
+    r = synth.random_small(seed=43, n=40, null_rate=null_rate)
+    s = synth.random_small(seed=44, n=55, null_rate=null_rate)
+    got, cand = oracle.block_owned(r, mds, S=s, threads=2)
+    assert np.array_equal(got, py_block(r, mds, S=s))
+    assert cand == py_candidates(r, mds, S=s)
+
+
+def test_owner_pass_rule_without_equality_and_big_groups():
+    # one key value for every row: one group of 2,200 rows is cut into many
+    # work ranges; an MD without equality owns the pairs the others miss
+    t = synth.random_small(seed=47, n=2200)
+    t.columns[2].data[:] = 3
+    mds = [[eq(2), eq(3), ed(0, 1)], [jac(1, 7, 10)], [eq(2), absdiff(4, 0.05)]]
+    want, cand_h = oracle.block_hash(t, mds)
+    got, cand = oracle.block_owned(t, mds, threads=4)
+    assert np.array_equal(got, want)
+    assert cand == cand_h == 2200 * 2199 // 2
+
+
+def test_owner_pass_config1_equals_literal():
+    t, mds = synth.config1()
+    got, cand = oracle.block_owned(t, mds)
+    assert np.array_equal(got, oracle.block_literal(t, mds))
+    assert cand == oracle.block_hash(t, mds)[1]
