@@ -84,8 +84,10 @@ typedef struct {
     int32_t kind;             /* hb_pkind */
     int32_t col_t;            /* column of the left tuple (relation R) */
     int32_t col_s;            /* column of the right tuple (S; = col_t for a self-join) */
-    int32_t k;                /* ED_LE: max distance (>= 0); EQ_PREFIX: prefix length (>= 1) */
-    int32_t q;                /* JACCARD_GE: gram length, 1..4 */
+    int32_t k;                /* ED_LE: max distance, 0..31 (larger: HB_ERR_ARG);
+                                 EQ_PREFIX: prefix length (>= 1) */
+    int32_t q;                /* JACCARD_GE: gram length, 1..4; a compared string may hold at most
+                                 8192 grams (a longer one makes hb_plan / hb_block return HB_ERR_ARG) */
     uint32_t num, den;        /* JACCARD_GE: threshold num/den, 0 <= num <= den, den >= 1 */
     float delta;              /* ABSDIFF_LE: threshold (>= 0) */
 } hb_predicate;
@@ -169,7 +171,15 @@ HB_API const char *hb_version(void);
 HB_API hb_status hb_load_table(hb_ctx *ctx, int32_t side, int64_t n_rows, int32_t n_cols, const hb_column *cols,
                         int32_t on_device);
 
-/* Add one MD with 1..10 predicates; *md_id_out (optional) receives its id (0, 1, ...). */
+/*
+ * Add one MD (Section 2, "Rules": phi = X -> t.eid = s.eid, X a conjunction
+ * of predicates; the default parameters of Section 6 cap an MD at ten) with
+ * 1..10 predicates; *md_id_out (optional) receives its id (0, 1, ...).
+ * Checks each predicate's parameters (HB_ERR_ARG: unknown kind, negative
+ * column, ED threshold outside 0..31, Jaccard q outside 1..4 or num > den,
+ * prefix length < 1, delta < 0 or NaN); columns are checked against the
+ * tables by hb_plan.
+ */
 HB_API hb_status hb_add_md(hb_ctx *ctx, int32_t n_pred, const hb_predicate *preds, int32_t *md_id_out);
 HB_API hb_status hb_clear_mds(hb_ctx *ctx);
 
@@ -196,7 +206,10 @@ HB_API hb_status hb_block(hb_ctx *ctx, hb_pair **pairs_out, int64_t *n_out);
 HB_API hb_status hb_block_device(hb_ctx *ctx, hb_pair **dev_pairs_out, int64_t *n_out);
 
 /*
- * R x S with S streamed from host memory: R must be loaded (side 0); S's
+ * Section 5.3 ("Data transfer between host and devices"): partitions are read
+ * into device memory while in-device ones are evaluated (CUDA streams overlap
+ * transfer and compute).  This call is that pipeline for R x S, with S
+ * streamed from host memory: R must be loaded (side 0); S's
  * columns (host pointers, same column order as used by the MDs' col_s) are
  * copied in chunks of at most chunk_bytes (straight from the caller's arrays
  * when all of them are page-locked, else through two pinned staging buffers),
@@ -208,8 +221,10 @@ HB_API hb_status hb_block_stream(hb_ctx *ctx, int64_t n_rows_s, int32_t n_cols, 
                           hb_pair **pairs_out, int64_t *n_out);
 
 /*
- * Batched form: the loaded R holds n_jobs independent relations stacked by
- * rows; job j is rows [job_rows[j], job_rows[j+1]).  Every job is blocked
+ * Build addition: the paper blocks the partitions P1..Pm of its problem
+ * statement (Section 2) one after another; this blocks many independent
+ * relations in one launch sequence.  The loaded R holds n_jobs independent
+ * relations stacked by rows; job j is rows [job_rows[j], job_rows[j+1]).  Every job is blocked
  * with the context's MDs in one persistent work-queue launch sequence (replayed
  * from a CUDA graph when the shapes repeat).  Pairs use job-local row ids;
  * job j's pairs are (*pairs_out)[job_pairs_out[j] .. job_pairs_out[j+1]),
@@ -309,7 +324,10 @@ HB_API hb_status hb_mlp_backward(const float *X, const float *t, int32_t n, cons
  * (about 4.2 MB, held on every GPU that loads the library until exit).  The
  * first call on a device looks up that array's address (call it once before
  * any stream capture); every call shares the array, so calls that overlap on
- * the GPU race.  No state carries over between calls.
+ * the GPU race.  No state carries over between calls.  The array's address
+ * is kept per device with the CUDA context it was found in; do not call this
+ * across a device reset (cudaDeviceReset) whose new context could reuse the
+ * old handle.
  */
 HB_API hb_status hb_mlp_backward_noalloc(const float *X, const float *t, int32_t n, const float *params,
                                          float *grad, void *stream);

@@ -1000,7 +1000,7 @@ hb_status build_blocks(hb_ctx *c, const uint32_t *rec_r, int64_t n_r, const uint
     const uint64_t H = pow2_at_least(std::max<uint64_t>(2 * (uint64_t)std::max<int64_t>(n_r, 1), 1024));
     const int na = (int)c->active.size();
     // member lists of all active MDs side by side, addressed with 32 bits
-    if ((uint64_t)std::max(na, 1) * (uint64_t)std::max<int64_t>(std::max(n_r, n_s), 1) >= (1ull << 32))
+    if (!member_addressing_fits(na, std::max(n_r, n_s)))
         return fail(HB_ERR_ARG, "rows x active MDs exceed the 32-bit member addressing");
     const uint64_t per_md = self ? (uint64_t)(n_r / 2 + 1) : (uint64_t)std::min<int64_t>(n_r, n_s) + 1;
     const uint64_t bc = std::min<uint64_t>(per_md * (uint64_t)std::max(na, 1), 0xFFFFFFF0ull);

@@ -296,6 +296,8 @@ extern "C" hb_status hb_block_batch(hb_ctx *c, int32_t n_jobs, const int64_t *jo
         HB_CUDA(cudaStreamSynchronize(c->stream));
         if (h[4]) return fail(HB_ERR_INTERNAL, "block list overflow");
         const int64_t n_out = (int64_t)h[1];
+        // job offsets are 32-bit on the device
+        if (n_out >= (int64_t)(1ll << 32)) return fail(HB_ERR_OVERFLOW, "hb_block_batch: 2^32 or more result pairs");
         if (n_out > c->out_cap) {
             c->out_cap = n_out + n_out / 8 + 1024;
             drop_graph(c);

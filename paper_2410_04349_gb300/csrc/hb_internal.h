@@ -32,6 +32,13 @@ constexpr int MD_LANES = 4;    // MDs whose blocks are built at once (side strea
 // 32-tuple tiles resident per SM
 constexpr int HOT_BUDGET = 12;
 
+// The member lists of all active MDs lie side by side and are addressed with
+// 32 bits: the block build needs (active MDs) x (rows) < 2^32.
+inline bool member_addressing_fits(int64_t n_active, int64_t rows) {
+    const uint64_t a = (uint64_t)(n_active > 1 ? n_active : 1), r = (uint64_t)(rows > 1 ? rows : 1);
+    return a * r < (1ull << 32);
+}
+
 // ---- device-side column of one relation ----
 struct DevCol {
     int32_t type = 0;

@@ -229,6 +229,9 @@ extern "C" hb_status hb_block_stream(hb_ctx *c, int64_t n_rows_s, int32_t n_cols
     }
     if (max_buf > chunk_bytes && K > 0 && max_rows > 1)
         return fail(HB_ERR_ARG, "hb_block_stream: a chunk exceeds chunk_bytes");
+    // R's member lists and a chunk's are addressed with 32 bits per active MD
+    if (!member_addressing_fits((int64_t)c->active.size(), std::max<int64_t>(c->side[0].n, max_rows)))
+        return fail(HB_ERR_ARG, "hb_block_stream: rows x active MDs exceed the 32-bit member addressing");
 
     // staging: two device chunk buffers and a copy stream kept by the context;
     // page-locked S arrays are copied straight from the caller's memory, any

@@ -180,7 +180,10 @@ cudaError_t mlp_backward(const float *X, const float *t, int n, const float *par
     float *dz2 = dy + n;   // n * D2
     HB_LAUNCHED(1);
     k_mlp_fwd<false><<<g, 64, 0, s>>>(X, n, params, y, z1, z2);
-    cudaMemcpyAsync(dz2, z2, sizeof(float) * (size_t)n * D2, cudaMemcpyDeviceToDevice, s);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    e = cudaMemcpyAsync(dz2, z2, sizeof(float) * (size_t)n * D2, cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return e;
     HB_LAUNCHED(1);
     k_mlp_bwd_rows<<<g, 64, 0, s>>>(y, t, n, params, z1, dz2, dz1, dy);
     HB_LAUNCHED(1);
@@ -215,7 +218,11 @@ cudaError_t adam_step(float *params, const float *grad, float *m, float *v, int 
 // Host code cannot use the array's name as a device address, so the address
 // is looked up once per device with cudaGetSymbolAddress (with that device
 // current) the first time the entry point runs on it; make that first call
-// before any stream capture.  Every call shares the one array: calls that
+// before any stream capture.  The address is kept together with the CUDA
+// context it was found in and looked up again when the device's current
+// context is another one (after cudaDeviceReset the module is loaded anew);
+// a reset that hands out a new context at the very same handle cannot be told
+// apart, so do not call the entry point across a device reset.  Every call shares the one array: calls that
 // overlap on the GPU (different streams, threads or devices' contexts racing
 // on the same device) race on it.  Nothing needs clearing between calls:
 // each call writes every scratch word it later reads, for its own rows.
@@ -230,6 +237,25 @@ namespace {
 constexpr int NOALLOC_MAX_DEVICES = 64;
 std::mutex g_noalloc_mu;
 float *g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {};
+void *g_noalloc_ctx[NOALLOC_MAX_DEVICES] = {};   // the context each address was looked up in
+
+// the calling thread's current CUDA context (driver cuCtxGetCurrent, reached
+// through the runtime so that the library needs no link to libcuda); NULL
+// when it cannot be read
+void *current_context() {
+    using get_fn = int (*)(void **);
+    static get_fn fn = []() -> get_fn {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            return nullptr;
+        return reinterpret_cast<get_fn>(f);
+    }();
+    void *ctx = nullptr;
+    if (!fn || fn(&ctx) != 0) return nullptr;
+    return ctx;
+}
 }  // namespace
 
 }  // namespace hb
@@ -248,12 +274,14 @@ extern "C" hb_status hb_mlp_backward_noalloc(const float *X, const float *t, int
     float *work = nullptr;
     {
         std::lock_guard<std::mutex> lock(g_noalloc_mu);
-        if (!g_noalloc_ptr[dev]) {
+        void *ctx = current_context();
+        if (!g_noalloc_ptr[dev] || ctx != g_noalloc_ctx[dev]) {
             void *p = nullptr;
             e = cudaGetSymbolAddress(&p, g_backward_scratch);
             if (e != cudaSuccess)
                 return fail(HB_ERR_CUDA, std::string("hb_mlp_backward_noalloc: cudaGetSymbolAddress: ") + cudaGetErrorString(e));
             g_noalloc_ptr[dev] = static_cast<float *>(p);
+            g_noalloc_ctx[dev] = current_context();   // the lookup made the device's context current
         }
         work = g_noalloc_ptr[dev];
     }
