@@ -77,6 +77,8 @@ def lib():
         L.or_block_hash.argtypes = [i64, i32, P, i64, i32, P, i32, P, P, i32, P, i64, P, i32]
         L.or_block_owned.restype = i64
         L.or_block_owned.argtypes = [i64, i32, P, i64, i32, P, i32, P, P, i32, i32, P, i64, P]
+        L.or_plan_units.restype = i64
+        L.or_plan_units.argtypes = [i64, i32, P, i64, i32, P, i32, P, P, i32, i32, i32, P, P, P, P]
         L.or_check_pairs.restype = None
         L.or_check_pairs.argtypes = [i64, i32, P, i64, i32, P, i32, P, P, P, i64, P]
         L.or_pred_verdicts.restype = None
@@ -212,6 +214,72 @@ def block_owned(R, mds, S=None, threads=None, evaluate=True):
         if n <= cap:
             return _unpack(buf, n), int(cand[0])
         cap = int(n)
+
+
+def _norm_pred(p):
+    """A predicate with only the parameters its kind uses (a Jaccard threshold
+    as a reduced fraction): two predicates are the same iff these are equal."""
+    kind, ct, cs, k, q, num, den, delta = p
+    if kind == "eq":
+        return (kind, ct, cs)
+    if kind in ("eq_prefix", "ed"):
+        return (kind, ct, cs, k)
+    if kind == "jaccard":
+        from math import gcd
+        g = gcd(num, den) or 1
+        return (kind, ct, cs, q, num // g, den // g)
+    return (kind, ct, cs, float(np.float32(delta)))
+
+
+def distinct_predicates(mds):
+    """Distinct predicates in order of first appearance over the MDs (MD order,
+    then written order): the numbering of Section 4.2's per-predicate
+    quantities and of the plan's program."""
+    out = []
+    for md in mds:
+        for p in md:
+            if _norm_pred(p) not in [_norm_pred(x) for x in out]:
+                out.append(p)
+    return out
+
+
+UNIT_NAMES = ("eq", "owner", "absdiff", "ed", "jaccard")
+
+
+def plan_units(R, mds, program, S=None, threads=None):
+    """Algorithmic work of replaying a plan on every candidate pair: a dict of
+    units per class (see or_plan_units), 'candidates', and 'total'.  program
+    lists the distinct non-equality predicates (tuples) in plan order."""
+    r, s, a = _args(R, S)
+    starts, preds = _rules(mds)
+    flat = [p for md in mds for p in md]
+    key = [_norm_pred(p) for p in flat]
+    prog, need = [], []
+    for p in program:
+        kp = _norm_pred(p)
+        prog.append(key.index(kp))
+        need.append(sum(1 << m for m, md in enumerate(mds) if any(_norm_pred(x) == kp for x in md)))
+    cp = []
+    for md in mds:
+        steps = [i for i, p in enumerate(program) if any(_norm_pred(x) == _norm_pred(p) for x in md)]
+        others = [x for x in md if x[0] not in ("eq", "eq_prefix")]
+        if len({_norm_pred(x) for x in others}) != len(steps):
+            raise ValueError("program misses a non-equality predicate of an MD")
+        cp.append(max(steps, default=-1))
+    n_eq = len({_norm_pred(x) for x in flat if x[0] in ("eq", "eq_prefix")})
+    prog_a = np.array(prog or [0], np.int32)
+    need_a = np.array(need or [0], np.uint64)
+    cp_a = np.array(cp, np.int32)
+    out = np.zeros(7, np.int64)
+    threads = threads or os.cpu_count() or 1
+    lib().or_plan_units(*a, len(mds), starts.ctypes.data, preds, threads, n_eq, len(prog), prog_a.ctypes.data,
+                        need_a.ctypes.data, cp_a.ctypes.data, out.ctypes.data)
+    if out[6]:
+        raise AssertionError(f"plan replay disagrees with the disjunction on {out[6]} pairs")
+    d = {n: int(v) for n, v in zip(UNIT_NAMES, out[:5])}
+    d["candidates"] = int(out[5])
+    d["total"] = int(out[:5].sum())
+    return d
 
 
 def check_pairs(R, mds, pairs, S=None) -> np.ndarray:

@@ -36,6 +36,7 @@
  * paper's Table 1 / Examples 3 and "(t1, t5)").
  */
 #include <algorithm>
+#include <array>
 #include <atomic>
 #include <cmath>
 #include <cstdint>
@@ -542,6 +543,149 @@ int64_t or_block_owned(int64_t nR, int32_t ncR, const or_col *R, int64_t nS, int
     all.erase(std::unique(all.begin(), all.end()), all.end());
     if (n_candidates) *n_candidates = c;
     return emit(all, out, cap);
+}
+
+/*
+ * Algorithmic work of an execution plan, counted by replaying it (Section 5.1,
+ * "Tree traversal on GPUs": the sequential path with a checkpoint per rule,
+ * each distinct predicate evaluated once per pair and its result reused) on
+ * every candidate pair, enumerated as in or_block_owned.  For a pair:
+ *
+ *   alive = the MDs whose equality predicates all hold; an alive MD without
+ *   other predicates is a witness at once.  Then for each step k of prog
+ *   (a predicate index into preds, one per distinct non-equality predicate,
+ *   in plan order) whose MD set need[k] meets alive: evaluate it, and drop
+ *   need[k] from alive when it fails; stop with a witness once an alive MD
+ *   has its checkpoint at k (cp_step[m] == k, its last predicate), or with
+ *   none once alive is empty.
+ *
+ * Units added (units_out, int64[7]): [0] n_eq_keys compares per candidate
+ * pair; [1] n_md compares (owner check) per candidate pair; [2] 3 per
+ * |a - b| <= delta; [3] edit distance: 3 for the length filter, and when
+ * |la - lb| <= k also ceil(min(la, lb) / 64) * max(la, lb) * 16 (bit-parallel
+ * distance over 64-bit words); [4] Jaccard: 3 for the size filter, and when
+ * min(|A|,|B|) * den >= num * max(|A|,|B|) also (|A| + |B|) * 4 (merge
+ * intersection); a missing operand costs the filter only.  [5] candidate
+ * pairs; [6] pairs where the replayed verdict differs from the disjunction
+ * (must be 0: the plan does not change the result).  Returns units_out[6].
+ */
+int64_t or_plan_units(int64_t nR, int32_t ncR, const or_col *R, int64_t nS, int32_t ncS, const or_col *S,
+                      int32_t n_md, const int32_t *md_start, const or_pred *preds, int32_t n_threads,
+                      int32_t n_eq_keys, int32_t n_prog, const int32_t *prog, const uint64_t *need,
+                      const int32_t *cp_step, int64_t *units_out) {
+    Rel r{nR, ncR, R};
+    Rel s = S ? Rel{nS, ncS, S} : r;
+    const bool self = (S == nullptr);
+    const int nt = std::max(n_threads, 1);
+    std::vector<std::vector<int64_t>> gid_r((size_t)n_md), gid_s((size_t)n_md);
+    std::vector<std::vector<std::vector<int64_t>>> left((size_t)n_md), right((size_t)n_md);
+    for (int m = 0; m < n_md; m++)
+        group_ids(preds, md_start[m], md_start[m + 1], r, self ? nullptr : &s, gid_r[(size_t)m], gid_s[(size_t)m],
+                  left[(size_t)m], right[(size_t)m]);
+    const std::vector<std::vector<int64_t>> &gid_c = self ? gid_r : gid_s;
+    std::vector<GramSets> grams;
+    for (int k = 0; k < n_prog; k++) {
+        const or_pred &p = preds[prog[k]];
+        if (p.kind != 3) continue;
+        for (int side = 0; side < (self ? 1 : 2); side++) {
+            const int col = side == 0 ? p.col_t : p.col_s;
+            bool have = false;
+            for (const GramSets &g : grams) have = have || (g.side == side && g.col == col && g.q == p.q);
+            if (have) continue;
+            grams.push_back(GramSets{side, col, p.q, {}});
+            gram_rows(side == 0 ? r : s, col, p.q, nt, grams.back().rows);
+        }
+    }
+    Owned ev{n_md, md_start, preds, r, s, grams, self};
+    struct Unit { int m; int64_t g, a0, a1; };
+    std::vector<Unit> units;
+    for (int m = 0; m < n_md; m++)
+        for (size_t g = 0; g < left[(size_t)m].size(); g++) {
+            const int64_t nl = (int64_t)left[(size_t)m][g].size();
+            const int64_t nrt = self ? nl : (int64_t)right[(size_t)m][g].size();
+            if (nl == 0 || nrt == 0 || (self && nl < 2)) continue;
+            for (int64_t a = 0; a < nl;) {
+                int64_t b = a, pairs = 0;
+                while (b < nl && pairs < (1 << 20)) { pairs += self ? (nl - 1 - b) : nrt; b++; }
+                units.push_back(Unit{m, (int64_t)g, a, b});
+                a = b;
+            }
+        }
+    std::vector<int64_t> eqonly((size_t)n_md);   /* MD has no non-equality predicate */
+    for (int m = 0; m < n_md; m++) {
+        eqonly[(size_t)m] = 1;
+        for (int32_t k = md_start[m]; k < md_start[m + 1]; k++) if (!is_equality(preds[k])) eqonly[(size_t)m] = 0;
+    }
+    auto filter_and_work = [&](const or_pred &p, int64_t i, int64_t j) -> int64_t {
+        const or_col &a = r.cols[p.col_t], &b = s.cols[p.col_s];
+        if (!present(a, i) || !present(b, j)) return 3;
+        if (p.kind == 2) {
+            const int64_t la = (int64_t)(a.off[i + 1] - a.off[i]), lb = (int64_t)(b.off[j + 1] - b.off[j]);
+            if (std::llabs(la - lb) > (int64_t)p.k) return 3;
+            return 3 + ((std::min(la, lb) + 63) / 64) * std::max(la, lb) * 16;
+        }
+        const auto *A = ev.gram_of(0, p.col_t, p.q), *B = ev.gram_of(1, p.col_s, p.q);
+        const int64_t na = (int64_t)(*A)[(size_t)i].size(), nb = (int64_t)(*B)[(size_t)j].size();
+        if ((uint64_t)std::min(na, nb) * p.den < (uint64_t)p.num * (uint64_t)std::max(na, nb)) return 3;
+        return 3 + (na + nb) * 4;
+    };
+    std::atomic<size_t> next{0};
+    std::vector<std::array<int64_t, 7>> acc((size_t)nt);
+    for (auto &x : acc) x.fill(0);
+    auto work = [&](int t) {
+        std::array<int64_t, 7> &u = acc[(size_t)t];
+        for (;;) {
+            const size_t w = next.fetch_add(1);
+            if (w >= units.size()) break;
+            const Unit &U = units[w];
+            const std::vector<int64_t> &L = left[(size_t)U.m][(size_t)U.g];
+            const std::vector<int64_t> &Rt = self ? L : right[(size_t)U.m][(size_t)U.g];
+            for (int64_t a = U.a0; a < U.a1; a++)
+                for (int64_t b = self ? a + 1 : 0; b < (int64_t)Rt.size(); b++) {
+                    int64_t i = L[(size_t)a], j = Rt[(size_t)b];
+                    if (self && i > j) std::swap(i, j);
+                    bool owned = true;
+                    for (int mm = 0; mm < U.m && owned; mm++) {
+                        const int64_t x = gid_r[(size_t)mm][(size_t)i];
+                        owned = !(x >= 0 && x == gid_c[(size_t)mm][(size_t)j]);
+                    }
+                    if (!owned) continue;
+                    u[5]++;
+                    u[0] += n_eq_keys;
+                    u[1] += n_md;
+                    uint64_t alive = 0;
+                    bool hit = false;
+                    for (int m = 0; m < n_md; m++) {
+                        bool all = true;
+                        for (int32_t k = md_start[m]; k < md_start[m + 1] && all; k++)
+                            if (is_equality(preds[k])) all = holds(preds[k], r, i, s, j);
+                        if (all) {
+                            alive |= 1ull << m;
+                            hit = hit || eqonly[(size_t)m];
+                        }
+                    }
+                    for (int k = 0; k < n_prog && !hit && alive; k++) {
+                        if (!(alive & need[k])) continue;
+                        const or_pred &p = preds[prog[k]];
+                        if (p.kind == 4) u[2] += 3;
+                        else u[p.kind == 2 ? 3 : 4] += filter_and_work(p, i, j);
+                        if (!ev.holds_p(p, i, j)) alive &= ~need[k];
+                        for (int m = 0; m < n_md && !hit; m++)
+                            hit = ((alive >> m) & 1ull) && cp_step[m] == k;
+                    }
+                    if (hit != ev.dnf(i, j)) u[6]++;
+                }
+        }
+    };
+    std::vector<std::thread> th;
+    for (int t = 1; t < nt; t++) th.emplace_back(work, t);
+    work(0);
+    for (auto &x : th) x.join();
+    for (int f = 0; f < 7; f++) {
+        units_out[f] = 0;
+        for (int t = 0; t < nt; t++) units_out[f] += acc[(size_t)t][(size_t)f];
+    }
+    return units_out[6];
 }
 
 /* Disjunction verdict for given pairs (i << 32 | j); used for sampled checks at full size. */
