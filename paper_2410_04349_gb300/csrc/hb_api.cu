@@ -748,9 +748,9 @@ static hb_status finish_plan(hb_ctx *c, int mode, const std::vector<double> &sp,
     // hot record (what phases 1 and 1b of the evaluation read from shared
     // memory): the equality codes and the filter operand (length, gram count
     // or value) of each MD's first program predicate; then, while the record
-    // stays within HOT_BUDGET words, the character / gram bins of those
-    // predicates, the filter operands of each MD's second predicate and their
-    // bins (MDs by decreasing estimated pass rate of their first predicate)
+    // stays within HOT_BUDGET words, the signature words of those predicates,
+    // the filter operands of each MD's second predicate and their signatures
+    // (MDs by decreasing estimated pass rate of their first predicate)
     c->hot_map.clear();
     for (int e = 0; e < c->n_eq_total; e++) c->hot_map.push_back(e);
     std::vector<int> hot_word(c->groups.size(), -1), hot_bins(c->groups.size(), -1);
@@ -769,13 +769,16 @@ static hb_status finish_plan(hb_ctx *c, int mode, const std::vector<double> &sp,
             c->hot_map.push_back(c->groups[g].word);
         }
     }
+    // the signature words of a predicate: one for edit distance (8 character
+    // bins), two for Jaccard (64-bit gram presence mask)
     auto add_bins = [&](int k) {
         const int g = group_of(k);
         const FeatGroup &G = c->groups[g];
-        const int nb = G.kind == OP_ED ? 4 : G.kind == OP_JAC ? 8 : 0;
+        const int nb = G.kind == OP_ED ? 1 : G.kind == OP_JAC ? 2 : 0;
+        const int w0 = G.kind == OP_ED ? FEAT_ED_SIG : FEAT_JAC_MASK;
         if (nb == 0 || hot_word[g] < 0 || hot_bins[g] >= 0 || (int)c->hot_map.size() + nb > HOT_BUDGET) return;
         hot_bins[g] = (int)c->hot_map.size();
-        for (int w = 0; w < nb; w++) c->hot_map.push_back(G.word + 2 + w);
+        for (int w = 0; w < nb; w++) c->hot_map.push_back(G.word + w0 + w);
     };
     // the optional words go first to the MDs whose first predicate lets the
     // most pairs through (largest estimated pass rate sp): their survivors
@@ -823,6 +826,8 @@ static hb_status finish_plan(hb_ctx *c, int mode, const std::vector<double> &sp,
     int tile = c->opt.tile ? c->opt.tile : 32;
     c->tile = tile;
     I.tile = tile;
+    I.record_words = c->W;
+    I.hot_words = c->HW;
     c->planned = true;
     return HB_OK;
 }

@@ -28,9 +28,9 @@ constexpr int SMALL_MAX = 16;  // self-join blocks of 2..SMALL_MAX tuples are pa
 constexpr int SMALL_META_WORDS = 160;
 constexpr int MD_LANES = 4;    // MDs whose blocks are built at once (side streams)
 // hot-record words beyond which only the mandatory words (keys, first-predicate
-// filter operands) are staged: 12 keeps four 256-thread evaluation CTAs of
+// filter operands) are staged: 16 keeps four 256-thread evaluation CTAs of
 // 32-tuple tiles resident per SM
-constexpr int HOT_BUDGET = 12;
+constexpr int HOT_BUDGET = 16;
 
 // The member lists of all active MDs lie side by side and are addressed with
 // 32 bits: the block build needs (active MDs) x (rows) < 2^32.
@@ -67,8 +67,12 @@ struct Op {
 };
 
 // feature group sizes (record words)
-constexpr int FEAT_ED_WORDS = 6;   // len, byte offset, 16 x 8-bit character-bin counts
-constexpr int FEAT_JAC_WORDS = 10; // unique gram count, gram offset, 32 x 8-bit gram-bin counts
+constexpr int FEAT_ED_WORDS = 7;   // len, byte offset, 16 x 8-bit character-bin counts (byte & 15),
+                                   // signature: 8 x 4-bit character-bin counts (byte & 7, saturating at 15)
+constexpr int FEAT_JAC_WORDS = 12; // unique gram count, gram offset, 32 x 8-bit gram-bin counts,
+                                   // 64-bit presence mask of the grams' 6-bit hash bins (low word first)
+constexpr int FEAT_ED_SIG = 6;     // word of the ED signature in its group
+constexpr int FEAT_JAC_MASK = 10;  // first word of the Jaccard presence mask in its group
 constexpr int FEAT_ABS_WORDS = 1;  // fp32 value bits (NaN when missing)
 
 struct BlockDesc {

@@ -155,16 +155,20 @@ __global__ void k_ed_features(const uint8_t *bytes, const uint32_t *off, const u
     if (valid && !valid[i]) {
         r[0] = NULL_LEN;
         r[1] = 0;
-        r[2] = r[3] = r[4] = r[5] = 0;
+        r[2] = r[3] = r[4] = r[5] = r[6] = 0;
         return;
     }
     uint32_t a = off[i], b = off[i + 1];
     uint32_t cnt[4] = {0, 0, 0, 0};
+    uint32_t sig = 0;   // 8 nibbles: counts of bytes with (byte & 7) == nibble index, saturating at 15
     for (uint32_t k = a; k < b; k++) {
-        uint32_t bin = bytes[k] & 15u;
+        const uint32_t by = bytes[k];
+        uint32_t bin = by & 15u;
         uint32_t word = bin >> 2, sh = (bin & 3u) * 8u;
         uint32_t cur = (cnt[word] >> sh) & 255u;
         if (cur < 255u) cnt[word] += 1u << sh;
+        const uint32_t ns = (by & 7u) * 4u;
+        if (((sig >> ns) & 15u) < 15u) sig += 1u << ns;
     }
     r[0] = b - a;
     r[1] = a;
@@ -172,6 +176,7 @@ __global__ void k_ed_features(const uint8_t *bytes, const uint32_t *off, const u
     r[3] = cnt[1];
     r[4] = cnt[2];
     r[5] = cnt[3];
+    r[FEAT_ED_SIG] = sig;
 }
 
 __global__ void k_abs_feature(const float *vals, const uint8_t *valid, int64_t n, uint32_t *rec, int W, int feat) {
@@ -187,6 +192,8 @@ __device__ __forceinline__ uint32_t gram_at(const uint8_t *p, uint32_t k, int q)
 }
 
 __device__ __forceinline__ uint32_t gram_bin(uint32_t g) { return (g * 0x9E3779B1u) >> 27; }
+// 6-bit hash bin of a gram for the 64-bit presence mask
+__device__ __forceinline__ uint32_t gram_bit(uint32_t g) { return (g * 0x9E3779B1u) >> 26; }
 
 constexpr int QG_SHORT = 64;       // grams per string handled by one thread
 constexpr int QG_MID = 256;        // grams per string handled by one warp
@@ -262,10 +269,14 @@ __device__ void write_gram_feature(uint32_t *r, uint32_t ucount, uint32_t start,
         uint32_t cur = (sig[word] >> sh) & 255u;
         if (cur < 255u) sig[word] += 1u << sh;
     }
+    uint64_t mask = 0;
+    for (uint32_t k = 0; k < ucount; k++) mask |= 1ull << gram_bit(g[k]);
     r[0] = ucount;
     r[1] = start;
 #pragma unroll
     for (int k = 0; k < 8; k++) r[2 + k] = sig[k];
+    r[FEAT_JAC_MASK] = (uint32_t)mask;
+    r[FEAT_JAC_MASK + 1] = (uint32_t)(mask >> 32);
 }
 
 // bitonic sorting network over N registers (every index is a compile-time
@@ -308,6 +319,7 @@ __device__ __forceinline__ void grams_sorted(const uint8_t *p, uint32_t g, int q
     sort_net<N>(v);
     uint32_t u = 0;
     uint32_t sig[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    uint64_t mask = 0;
 #pragma unroll
     for (int k = 0; k < N; k++) {
         if ((uint32_t)k < g && (k == 0 || v[k] != v[k > 0 ? k - 1 : 0])) {
@@ -316,12 +328,15 @@ __device__ __forceinline__ void grams_sorted(const uint8_t *p, uint32_t g, int q
             const uint32_t word = bin >> 2, sh = (bin & 3u) * 8u;
             const uint32_t cur = (sig[word] >> sh) & 255u;
             if (cur < 255u) sig[word] += 1u << sh;
+            mask |= 1ull << gram_bit(v[k]);
         }
     }
     r[0] = u;
     r[1] = start;
 #pragma unroll
     for (int k = 0; k < 8; k++) r[2 + k] = sig[k];
+    r[FEAT_JAC_MASK] = (uint32_t)mask;
+    r[FEAT_JAC_MASK + 1] = (uint32_t)(mask >> 32);
 }
 
 // Strings with up to 64 grams: one thread per string sorts its grams in
@@ -340,7 +355,7 @@ __global__ void __launch_bounds__(QG_THREADS) k_grams_short(const uint8_t *bytes
     if (valid && !valid[i]) {
         r[0] = NULL_LEN;
         r[1] = 0;
-        for (int k = 0; k < 8; k++) r[2 + k] = 0;
+        for (int k = 2; k < FEAT_JAC_WORDS; k++) r[k] = 0;
         return;
     }
     const uint32_t a = off[i], len = off[i + 1] - a;
@@ -397,6 +412,7 @@ __global__ void __launch_bounds__(256) k_grams_mid(const uint8_t *bytes, const u
         }
         uint32_t *dst = grams + gstart[i];
         uint32_t base = 0;
+        uint64_t mask = 0;
         for (uint32_t c0 = 0; c0 < g; c0 += 32) {
             const uint32_t k = c0 + lane;
             const bool keep = k < g && (k == 0 || s[k] != s[k - 1]);
@@ -404,9 +420,12 @@ __global__ void __launch_bounds__(256) k_grams_mid(const uint8_t *bytes, const u
             if (keep) {
                 dst[base + __popc(bal & lt)] = s[k];
                 atomicAdd(&bins[w][gram_bin(s[k])], 1u);
+                mask |= 1ull << gram_bit(s[k]);
             }
             base += __popc(bal);
         }
+        const uint32_t mlo = __reduce_or_sync(0xffffffffu, (uint32_t)mask);
+        const uint32_t mhi = __reduce_or_sync(0xffffffffu, (uint32_t)(mask >> 32));
         __syncwarp();
         uint32_t *r = rec + i * W + feat;
         if (lane < 8) {
@@ -418,6 +437,8 @@ __global__ void __launch_bounds__(256) k_grams_mid(const uint8_t *bytes, const u
         if (lane == 0) {
             r[0] = base;
             r[1] = gstart[i];
+            r[FEAT_JAC_MASK] = mlo;
+            r[FEAT_JAC_MASK + 1] = mhi;
         }
         __syncwarp();
     }
