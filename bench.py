@@ -42,15 +42,7 @@ UNIT = "pairs/s"
 WORKLOAD = ("single table, 1,000,000 tuples x 8 attributes (2 strings 8-60 chars, 3 Zipf(1.1) keys over "
             "1e3/1e4/1e5 values, 2 fp32), 10% near-duplicates, 4 MDs")
 
-# algorithmic integer operations per unit of work ("Roofline")
-OPS_EXAMINED_PER_KEY = 3      # compare, mask missing, merge into the match vector
-OPS_EXAMINED_FIXED = 3        # match vector -> alive MDs, owner test
-OPS = {  # kind: (per evaluation, per stage-1 pass, per stage-2 pass, per core unit)
-    "absdiff": (3, 0, 0, 0),   # subtract, absolute value, compare
-    "ed": (4, 18, 0, 5),       # length filter; 16-bin bag distance; banded DP cell
-    "jaccard": (7, 18, 0, 6),  # size filter; 32-bin count bound; merge step
-}
-KIND_NAMES = {2: "ed", 3: "jaccard", 4: "absdiff"}
+GOLDEN = os.path.join(ROOT, "tests", "golden")
 
 
 def parse():
@@ -63,6 +55,8 @@ def parse():
     ap.add_argument("--cpu-sample-rows", type=int, default=80_000)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the learned-vs-plain (10M tuples) and batched-vs-per-job (10,000 jobs) comparisons")
     ap.add_argument("--workload", choices=["c2", "c3", "c4", "c5"], default="c2",
                     help="c2 (default): the single-table step above; c3: R x S with S streamed from host in pinned "
                          "chunks; c4: 10,000 jobs batched vs one launch sequence per job; c5: learned vs rule- and "
@@ -173,12 +167,53 @@ def eval_kernel_traffic():
         return None
 
 
-def algorithmic_ops(logs, examined, n_eq):
-    total = examined * (OPS_EXAMINED_PER_KEY * n_eq + OPS_EXAMINED_FIXED)
-    for L in logs:
-        base, s1, s2, core = OPS[KIND_NAMES[L["kind"]]]
-        total += L["evaluated"] * base + L["stage1"] * s1 + L["stage2"] * s2 + L["core"] * core
-    return float(total)
+def plan_units(info, n_md):
+    """Algorithmic integer work of one evaluation launch under the plan in use:
+    the oracle's exact plan-replay count over every candidate pair of the
+    full-size relation, stored by tests/golden/make_plan_units.py (committed
+    data; nothing of the oracle runs here).  None when it was counted for
+    another plan."""
+    try:
+        d = json.load(open(os.path.join(GOLDEN, "plan_units_c2.json")))
+    except (OSError, ValueError):
+        return None
+    program = [int(x) for x in info.op_pred[:info.n_ops]]
+    if d.get("program_ids") != program:
+        return None
+    return d
+
+
+def algorithmic_bytes(table, mds, stats, q=3):
+    """HBM bytes the encoder, the block build and the sort must move at least
+    (the output each stage produces from the data it reads):
+      encode: every column a rule reads, plus the dictionary code of each
+        equality key (4 B a row), the q-gram lists of the Jaccard columns
+        (4 B a gram, |s| - q + 1 grams for a string of |s| bytes) and their
+        offsets (4 B a row);
+      block build: per MD that builds blocks, its key codes read (4 B a key a
+        row) and one member id written (4 B a row);
+      sort: one read and one write of each 8-byte pair key per 8-bit radix pass
+        over the used key bits."""
+    n = table.n_rows
+    used = sorted({p[1] for md in mds for p in md})
+    read = 0
+    for ci in used:
+        c = table.columns[ci]
+        read += c.data.nbytes + (0 if c.offsets is None else c.offsets.nbytes) + (0 if c.valid is None else c.valid.nbytes)
+    eq_keys = {(p[0], p[1], p[3] if p[0] == "eq_prefix" else 0) for md in mds for p in md if p[0] in ("eq", "eq_prefix")}
+    jac_cols = {(p[1], p[4]) for md in mds for p in md if p[0] == "jaccard"}
+    grams = 0
+    for ci, qq in jac_cols:
+        lens = np.diff(table.columns[ci].offsets.astype(np.int64))
+        grams += int(np.maximum(lens - qq + 1, 0).sum())
+    enc = read + 4 * n * len(eq_keys) + 4 * grams + 4 * (n + 1) * len(jac_cols)
+    eqsets = [frozenset((p[0], p[1], p[3] if p[0] == "eq_prefix" else 0) for p in md if p[0] in ("eq", "eq_prefix"))
+              for md in mds]
+    active = [m for m, e in enumerate(eqsets) if not any(eqsets[j] <= e for j in range(m))]
+    blk = sum(4 * n * len(eqsets[m]) + 4 * n for m in active)
+    bits = 2 * max(1, int(n - 1).bit_length())
+    srt = 2 * 8 * stats["emitted_pairs"] * ((bits + 7) // 8)
+    return {"encode": enc, "block_build": blk, "sort": srt}
 
 
 def device_columns(table, device):
@@ -285,8 +320,10 @@ def run_c3(args):
     return 0
 
 
-def run_c4(args):
-    """10,000 independent jobs: one batched launch (graph replay) vs one launch sequence per job."""
+def compare_c4(args):
+    """10,000 independent jobs: one batched launch sequence (replayed from a
+    CUDA graph, autotuned tile shape) vs one launch sequence per job, with the
+    pair sets compared."""
     import torch
     import synth
     from paper_2410_04349_gb300 import hb
@@ -311,64 +348,40 @@ def run_c4(args):
     tb, stb, pb, ob, lb = res["batched"]
     tp, stp, pp, op_, lp = res["per_job"]
     identical = bool(np.array_equal(pb, pp) and np.array_equal(ob, op_))
-    line = _line(METRIC, stb["candidate_pairs"] / tb, UNIT, args, tb * 1e3,
-                 f"10,000 independent jobs of {t.n_rows} tuples in total (lognormal sizes in [50, 20000]), C2 schema "
-                 f"and rules; one persistent launch replayed from a CUDA graph",
-                 candidate_pairs_per_step=stb["candidate_pairs"], emitted_pairs_per_step=len(pb),
-                 tile=stb["tile"], gpu_launches=lb,
-                 per_job={"ms_per_step": tp * 1e3, "value": stp["candidate_pairs"] / tp, "gpu_launches": lp},
-                 speedup_vs_per_job=tp / tb, identical_pair_sets=identical)
+    return {"workload": f"10,000 independent jobs, {t.n_rows} tuples in all (lognormal sizes in [50, 20000]), "
+                        "C2 schema and rules, host-resident tables",
+            "candidate_pairs": stb["candidate_pairs"], "emitted_pairs": int(len(pb)),
+            "batched": {"ms_per_step": tb * 1e3, "value": stb["candidate_pairs"] / tb, "gpu_launches": lb,
+                        "tile": stb["tile"], "steps": args.steps},
+            "per_job": {"ms_per_step": tp * 1e3, "value": stp["candidate_pairs"] / tp, "gpu_launches": lp, "steps": 1},
+            "speedup": tp / tb, "identical_pair_sets": identical, "unit": UNIT,
+            "timing": "wall clock around each hb_block_batch call (host tables in, pairs out), median"}
+
+
+def run_c4(args):
+    d = compare_c4(args)
+    line = _line(METRIC, d["batched"]["value"], UNIT, args, d["batched"]["ms_per_step"], d["workload"],
+                 batched_vs_per_job=d, gpu_launches=d["batched"]["gpu_launches"])
     print(json.dumps(line), flush=True)
-    return 0 if identical else 1
+    return 0 if d["identical_pair_sets"] else 1
 
 
-def c5_training_rows(ctx_factory):
-    """Training rows of the cost model from logs of configs 2-4 under the given
-    rules and seeded random rule sets."""
-    import synth
-    from paper_2410_04349_gb300 import learn
-    Xs, ycs, yss = [], [], []
-
-    def rows(table, sets, S=None):
-        with ctx_factory() as ctx:
-            ctx.load_table(0, table.n_rows, table.columns)
-            if S is not None:
-                ctx.load_table(1, S.n_rows, S.columns)
-            for mds in sets:
-                ctx.clear_mds()
-                for md in mds:
-                    ctx.add_md(md)
-                ctx.plan("rule_data")
-                X, yc, ys = learn.collect(ctx)
-                Xs.append(X)
-                ycs.append(yc)
-                yss.append(ys)
-
-    t2, m2 = synth.config2()
-    rows(t2, [m2] + [synth.random_rule_set(100 + i, 4, [2, 3, 4], [0, 1], [5, 6]) for i in range(16)])
-    r3, s3, m3 = synth.config3()
-    rows(r3, [m3] + [synth.random_rule_set(200 + i, 4, [2, 3, 4], [0, 1], [5, 6]) for i in range(8)], S=s3)
-    sizes = [20000, 16000, 12000, 9000, 7000, 5000, 4000, 3000]
-    t4, m4 = synth.config4(n_jobs=len(sizes), sizes=sizes)
-    for j in range(len(sizes)):
-        sub = t4.slice(t4.job_offsets[j], t4.job_offsets[j + 1])
-        rows(sub, [m4] + [synth.random_rule_set(300 + 10 * j + i, 4, [2, 3, 4], [0, 1], [5, 6], n_keys=(1, 2))
-                          for i in range(3)])
-    return np.concatenate(Xs), np.concatenate(ycs), np.concatenate(yss)
+MODEL_PATH = os.path.join(ROOT, "paper_2410_04349_gb300", "cost_model.npy")
 
 
-def run_c5(args):
-    """Learned cost model (trained on logs of configs 2-4) vs the rule- and
-    data-aware plan on 10M tuples x 12 attributes with 16 MDs."""
+def cost_model():
+    """The committed cost model (two 32-64-64-1 networks trained on the blocker's
+    logs of the C2-C4 workloads by paper_2410_04349_gb300/train_cost_model.py)."""
+    return np.load(MODEL_PATH).astype(np.float32)
+
+
+def compare_c5(args):
+    """Learned plan (the committed cost model) vs the rule- and data-aware plan
+    on 10M tuples x 12 attributes with 16 MDs; identical pair sets required."""
     import torch
     import synth
-    from paper_2410_04349_gb300 import hb, learn
-    t0 = time.perf_counter()
-    X, yc, ys = c5_training_rows(lambda: hb.Context(device=0))
-    with hb.Context(device=0) as ctx:
-        loss = learn.train(ctx, X, yc, ys)
-        model = ctx.get_cost_model()
-    train_s = time.perf_counter() - t0
+    from paper_2410_04349_gb300 import hb
+    model = cost_model()
     t, mds = synth.config5()
     res = {}
     with hb.Context(device=0) as ctx:
@@ -377,7 +390,9 @@ def run_c5(args):
             ctx.add_md(md)
         ctx.set_cost_model(model)
         for mode in ("rule_data", "learned"):
+            tp0 = time.perf_counter()
             info = ctx.plan(mode)
+            plan_s = time.perf_counter() - tp0
             for _ in range(max(args.warmup, 3)):
                 pairs = ctx.block()
             ev, tot = [], []
@@ -388,23 +403,33 @@ def run_c5(args):
                 tot.append(time.perf_counter() - s0)
                 ev.append(ctx.stats()["ms_eval"])
             st = ctx.stats()
-            res[mode] = (statistics.median(tot), statistics.median(ev), st, pairs, info.mode,
-                         list(info.op_pred[:info.n_ops]))
-    identical = bool(np.array_equal(res["rule_data"][3], res["learned"][3]))
-    tl, el, stl, pl, applied, opl = res["learned"]
-    tp, ep, stp, pp, _, opp = res["rule_data"]
-    line = _line(METRIC, stl["candidate_pairs"] / (el / 1e3), UNIT, args, tl * 1e3,
-                 "single table, 10,000,000 tuples x 12 attributes (4 strings 8-80 chars, 5 Zipf(1.1) keys, 3 fp32), "
-                 "10% near-duplicates, 16 MDs; learned plan",
-                 candidate_pairs_per_step=stl["candidate_pairs"], emitted_pairs_per_step=len(pl),
-                 learned={"eval_ms": el, "step_ms": tl * 1e3, "plan_mode_applied": applied, "program": opl},
-                 rule_data={"eval_ms": ep, "step_ms": tp * 1e3, "program": opp},
-                 eval_speedup_learned_vs_plain=ep / el, step_speedup_learned_vs_plain=tp / tl,
-                 identical_pair_sets=identical,
-                 training={"rows": int(len(X)), "loss_cost": float(loss[0]), "loss_sel": float(loss[1]),
-                           "seconds_incl_logging": train_s})
+            res[mode] = {"eval_ms": statistics.median(ev), "step_ms": 1e3 * statistics.median(tot),
+                         "plan_ms": plan_s * 1e3, "plan_mode_applied": int(info.mode), "tile": int(info.tile),
+                         "program": [int(x) for x in info.op_pred[:info.n_ops]], "pairs": pairs, "st": st}
+    L, Rd = res["learned"], res["rule_data"]
+    identical = bool(np.array_equal(L["pairs"], Rd["pairs"]))
+    cand = L["st"]["candidate_pairs"]
+    out = {"workload": "single table, 10,000,000 tuples x 12 attributes (4 strings 8-80 chars, 5 Zipf(1.1) keys, "
+                       "3 fp32), 10% near-duplicates, 16 MDs",
+           "candidate_pairs": cand, "emitted_pairs": int(len(L["pairs"])), "unit": UNIT,
+           "identical_pair_sets": identical,
+           "eval_speedup_learned_vs_plain": Rd["eval_ms"] / L["eval_ms"],
+           "step_speedup_learned_vs_plain": Rd["step_ms"] / L["step_ms"],
+           "model": "paper_2410_04349_gb300/cost_model.npy",
+           "timing": "eval_ms: CUDA events around the evaluation kernel; step_ms: wall clock around hb_block "
+                     "(host tables already loaded), medians"}
+    for k, v in (("learned", L), ("rule_data", Rd)):
+        out[k] = {x: v[x] for x in ("eval_ms", "step_ms", "plan_ms", "plan_mode_applied", "tile", "program")}
+        out[k]["value"] = cand / (v["eval_ms"] / 1e3)
+    return out
+
+
+def run_c5(args):
+    d = compare_c5(args)
+    line = _line(METRIC, d["learned"]["value"], UNIT, args, d["learned"]["step_ms"], d["workload"],
+                 learned_vs_plain=d)
     print(json.dumps(line), flush=True)
-    return 0 if identical else 1
+    return 0 if d["identical_pair_sets"] else 1
 
 
 def main():
@@ -426,7 +451,8 @@ def main():
         dist.init_process_group("nccl")
     device = torch.device("cuda", local)
     torch.cuda.set_device(device)
-    table, mds = synth.config2(seed=synth.BASE_SEED + 2 + 1000 * rank, n=args.rows)
+    seed_offset = 1000 * rank   # every rank blocks its own seeded table (independent problems)
+    table, mds = synth.config2(seed=synth.BASE_SEED + 2 + seed_offset, n=args.rows)
     dev_cols = device_columns(table, device)
     stream = torch.cuda.current_stream(device)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=device)
@@ -443,11 +469,16 @@ def main():
     for _ in range(max(args.warmup, 3)):
         step()
     torch.cuda.synchronize()
+    # the integer issue-rate ceiling of this GPU, measured by the library's probe
+    probe_ops, _ = hb.probe_int_issue(stream=stream.cuda_stream)
+    probe_mhz = None
+    torch.cuda.synchronize()
     launches0 = ctx.stats()["kernel_launches"]
     if world > 1:
         torch.distributed.barrier()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     eval_ms, cands, outs = [], [], []
+    stage_hist = {"ms_encode": [], "ms_block_build": [], "ms_sort": []}
     with ClockSampler(local) as clk:
         torch.cuda.synchronize()
         for i in range(args.steps):
@@ -457,6 +488,8 @@ def main():
             ev[i][1].record(stream)
             st = ctx.stats()
             eval_ms.append(st["ms_eval"])
+            for k in stage_hist:
+                stage_hist[k].append(st[k])
             cands.append(st["candidate_pairs"])
             outs.append(n_out)
         torch.cuda.synchronize()
@@ -469,23 +502,48 @@ def main():
     value = units / secs
     st = ctx.stats()
 
-    # roofline of the evaluation kernel: algorithmic integer ops / its launch time
-    logs = ctx.log_predicates(profile=False)
-    ex = ctx.stats()["examined_pairs"]
+    # roofline of the evaluation kernel: algorithmic integer operations per
+    # launch (the oracle's plan-replay count for the plan in use) over the
+    # library's measured integer issue rate; its staged bytes against HBM
     info = ctx.plan("rule_data")
-    n_eq = info.n_eq
-    alg = algorithmic_ops(logs, ex, n_eq)
     clocks = clk.summary()
     sm_mhz = clocks["sm_mhz"] or measured_peaks().get("clocks_under_load", {}).get("sm_mhz_median", 1440.0)
     n_sm = torch.cuda.get_device_properties(device).multi_processor_count
-    peak_ops = n_sm * 4 * 32 * sm_mhz * 1e6          # one 32-lane integer warp instruction per SMSP per clock
+    derived_ops = n_sm * 4 * 32 * sm_mhz * 1e6      # one 32-lane warp instruction per SMSP per clock
     eval_s = statistics.median(eval_ms) / 1e3
-    achieved = alg / eval_s
-    roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12, "unit": "Tops/s",
-                "frac": achieved / peak_ops, "traffic": eval_kernel_traffic(), "kernel": "k_eval",
-                "ops_per_launch": alg, "launch_ms": eval_s * 1e3,
-                "peak_basis": f"{n_sm} SMs x 4 SMSPs x 32 lanes x {sm_mhz:.0f} MHz (median SM clock sampled during "
-                              f"the timed region)"}
+    pu = plan_units(info, len(mds)) if args.rows == 1_000_000 and seed_offset == 0 else None
+    hbm = measured_peaks().get("hbm_gbs", 6800.0) * 1e9
+    hw_bytes = 4 * info.hot_words
+    staged = float(st["tiles"]) * 2 * (32 * info.tile // 32) * hw_bytes + 8.0 * outs[-1]
+    roofline = {"bound": "alu", "kernel": "k_eval", "unit": "Tops/s", "launch_ms": eval_s * 1e3,
+                "peak": probe_ops / 1e12,
+                "peak_basis": f"measured by hb_probe_int_issue (8 independent add/shift/logic chains per thread, "
+                              f"8 x 256-thread blocks per SM): {probe_ops / 1e12:.1f} T int ops/s at "
+                              f"{probe_mhz or sm_mhz:.0f} MHz; derived {n_sm} SMs x 4 SMSPs x 32 lanes x clock = "
+                              f"{derived_ops / 1e12:.1f} T",
+                "traffic": eval_kernel_traffic(),
+                "alg_bytes_per_launch": staged,
+                "alg_bytes_basis": "hot records of both sides of every tile (tiles x 2 x 32 x hot-record bytes) "
+                                   "+ 8 B per emitted pair",
+                "hbm_frac": (staged / hbm) / eval_s}
+    if pu is not None:
+        ops = float(pu["units"]["total"])
+        roofline.update({"achieved": ops / eval_s / 1e12, "frac": ops / eval_s / probe_ops,
+                         "ops_per_launch": ops, "ops_basis": "oracle plan replay over all "
+                         f"{pu['units']['candidates']} candidate pairs (tests/golden/plan_units_c2.json): "
+                         + ", ".join(f"{k} {pu['units'][k]:.3g}" for k in ("eq", "owner", "absdiff", "ed", "jaccard"))})
+    else:
+        roofline.update({"achieved": None, "frac": None, "ops_per_launch": None,
+                         "ops_basis": "no plan-replay count for this plan or size"})
+    alg = algorithmic_bytes(table, mds, st)
+    stage_ms = {k: st[k] for k in ("ms_encode", "ms_plan", "ms_block_build", "ms_eval", "ms_sort", "ms_d2h")}
+    stages = {}
+    for name, key in (("encode", "ms_encode"), ("block_build", "ms_block_build"), ("sort", "ms_sort")):
+        t_s = statistics.median(stage_hist[key]) / 1e3
+        stages[name] = {"bound": "hbm", "alg_bytes": alg[name], "ms": t_s * 1e3,
+                        "achieved_gbs": alg[name] / t_s / 1e9 if t_s > 0 else None,
+                        "frac": (alg[name] / hbm) / t_s if t_s > 0 else None}
+    stages["eval"] = {"bound": "alu", "ms": eval_s * 1e3, "frac": roofline["frac"]}
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -494,20 +552,22 @@ def main():
         "config": {"workload": WORKLOAD, "n_tuples": table.n_rows, "n_mds": len(mds), "parallelism": f"dp{world}",
                    "l2": "flushed (256 MiB write) before every timed step", "inputs": "raw columns resident in HBM"},
         "candidate_pairs_per_step": cands[-1], "emitted_pairs_per_step": outs[-1],
-        "examined_pairs_per_step": ex,
+        "examined_pairs_per_step": st["examined_pairs"],
         "eval_kernel_pairs_per_s": cands[-1] / eval_s,
-        "stage_ms": {k: st[k] for k in ("ms_encode", "ms_plan", "ms_block_build", "ms_eval", "ms_sort", "ms_d2h")},
+        "stage_ms": stage_ms,
+        "stage_roofline": stages,
         "gpu_launches": launches,
         "clocks": {"sm_mhz": clocks["sm_mhz"], "sm_max_mhz": clocks["sm_max_mhz"], "reasons": clocks["reasons"]},
         "roofline": roofline,
     }
 
     if not args.no_e2e:
-        # the caller's columns in page-locked host memory; every step copies them in
+        # the caller's columns in page-locked host memory; every step copies them
+        # in and reads the sorted pairs back, over as many steps as the device-timed loop
         host_cols = hb.pin_columns(table.columns)
         h2d = table.nbytes()
         times, last_n = [], 0
-        for i in range(1 + min(args.steps, 5)):
+        for i in range(max(args.warmup, 3) + args.steps):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             ctx.load_table(0, table.n_rows, host_cols, on_device=False)
@@ -515,13 +575,19 @@ def main():
             pairs = ctx.block()
             dt = time.perf_counter() - t0
             last_n = len(pairs)
-            if i > 0:
+            if i >= max(args.warmup, 3):
                 times.append(dt)
         e2e_units, e2e_s = aggregate(float(cands[-1]) * len(times), sum(times), world)
         line["e2e"] = {"value": e2e_units / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
-                       "d2h_bytes_per_step": last_n * 8, "ms_per_step": 1e3 * e2e_s / len(times)}
+                       "d2h_bytes_per_step": last_n * 8, "ms_per_step": 1e3 * e2e_s / len(times),
+                       "steps": len(times)}
     ctx.close()
 
+    if rank == 0 and world == 1 and not args.no_extra:
+        # the metric's other halves: learned vs plain plan (10M tuples) and the
+        # batched form vs one launch sequence per job (10,000 jobs)
+        line["learned_vs_plain"] = compare_c5(args)
+        line["batched_vs_per_job"] = compare_c4(args)
     if rank == 0 and world == 1 and not args.no_cpu:
         rate, dt, cand, threads = cpu_oracle_rate(table, mds, args.cpu_sample_rows)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",

@@ -135,6 +135,8 @@ typedef struct {
     int32_t pred_md[HB_MAX_PREDS];    /* first MD that holds each distinct predicate */
     int32_t tile;                     /* tile side chosen for evaluation */
     int32_t n_mds;
+    int32_t record_words;             /* 32-bit words of a tuple's packed record (codes and features) */
+    int32_t hot_words;                /* 32-bit words of a tuple's hot record (what every pair's first test reads) */
 } hb_plan_info;
 
 typedef struct {
@@ -333,6 +335,18 @@ HB_API hb_status hb_mlp_backward_noalloc(const float *X, const float *t, int32_t
                                          float *grad, void *stream);
 HB_API hb_status hb_adam_step(float *params, const float *grad, float *m, float *v, int32_t n_params, int32_t step,
                        float lr, float beta1, float beta2, float eps, void *stream);
+
+/*
+ * Measurement aid (no counterpart in the paper): the integer issue rate of the
+ * current device.  Launches 8 resident 256-thread blocks per SM whose threads
+ * run 8 independent chains of three integer instructions (three-input add,
+ * shift, three-input logic) for `iters` steps, timed with CUDA events on
+ * `stream` (NULL = default stream) after one short warm-up launch.  Writes
+ * integer operations per second to *ops_per_s and the timed launch's
+ * milliseconds to *ms_out (optional).  Allocates and frees a small result
+ * array on `stream`.  HB_ERR_ARG when iters < 1 or ops_per_s is NULL.
+ */
+HB_API hb_status hb_probe_int_issue(int32_t iters, double *ops_per_s, double *ms_out, void *stream);
 
 #ifdef __cplusplus
 }

@@ -15,7 +15,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libhb.so")
 
 SOURCES = ["hb_api.cu", "hb_learn.cu", "k_sort.cu", "k_encode.cu", "k_block.cu", "k_eval.cu", "k_stats.cu",
-           "k_mlp.cu", "planner.cpp", "hb_batch.cu", "hb_stream.cu"]
+           "k_mlp.cu", "planner.cpp", "hb_batch.cu", "hb_stream.cu", "k_probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -64,7 +64,8 @@ class hb_plan_info(ctypes.Structure):
                 ("n_eq", ctypes.c_int32), ("op_pred", ctypes.c_int32 * MAX_PREDS),
                 ("md_order", ctypes.c_int32 * MAX_MDS), ("sp", ctypes.c_double * MAX_PREDS),
                 ("cost", ctypes.c_double * MAX_PREDS), ("pred_md", ctypes.c_int32 * MAX_PREDS),
-                ("tile", ctypes.c_int32), ("n_mds", ctypes.c_int32)]
+                ("tile", ctypes.c_int32), ("n_mds", ctypes.c_int32), ("record_words", ctypes.c_int32),
+                ("hot_words", ctypes.c_int32)]
 
 
 class hb_stats(ctypes.Structure):
@@ -96,7 +97,7 @@ EXPORTS = ["hb_create", "hb_destroy", "hb_last_error", "hb_version", "hb_load_ta
            "hb_plan", "hb_block", "hb_block_device", "hb_block_stream", "hb_block_batch", "hb_free_pairs",
            "hb_get_stats", "hb_plan_order", "hb_log_predicates", "hb_predicate_features", "hb_train_cost_model",
            "hb_get_cost_model", "hb_set_cost_model", "hb_mlp_forward", "hb_mlp_forward_bf16", "hb_mlp_backward",
-           "hb_mlp_backward_noalloc", "hb_adam_step"]
+           "hb_mlp_backward_noalloc", "hb_adam_step", "hb_probe_int_issue"]
 
 _lib = None
 
@@ -125,6 +126,7 @@ def lib():
         "hb_mlp_backward": (st, [P, P, i32, P, P, P]), "hb_mlp_backward_noalloc": (st, [P, P, i32, P, P, P]),
         "hb_adam_step": (st, [P, P, P, P, i32, i32, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                               P]),
+        "hb_probe_int_issue": (st, [i32, P, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -396,3 +398,12 @@ def mlp_backward_noalloc(X, t, params, grad, stream=None):
 def adam_step(params, grad, m, v, step, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
     _check(lib().hb_adam_step(_ptr(params), _ptr(grad), _ptr(m), _ptr(v), params.numel(), step, lr, beta1, beta2,
                               eps, stream), "hb_adam_step")
+
+
+def probe_int_issue(iters=4096, stream=None):
+    """(integer operations per second, launch ms) of the library's issue-rate
+    probe on the current device."""
+    ops = ctypes.c_double()
+    ms = ctypes.c_double()
+    _check(lib().hb_probe_int_issue(iters, ctypes.byref(ops), ctypes.byref(ms), stream), "hb_probe_int_issue")
+    return ops.value, ms.value

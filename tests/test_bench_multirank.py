@@ -46,9 +46,36 @@ def test_aggregate_single_rank_is_identity():
     assert bench.aggregate(5.0, 2.0, 1) == (5.0, 2.0)
 
 
-def test_algorithmic_ops_formula():
+def test_algorithmic_bytes_formula():
+    """Encoder, block-build and sort bytes of the stage rooflines, on a
+    hand-sized table: 3 rows, a string column of 4, 5 and 0 bytes read by a
+    Jaccard (q = 3) predicate and an int32 key."""
     import bench
-    logs = [{"kind": 2, "evaluated": 10, "stage1": 4, "stage2": 1, "core": 50},
-            {"kind": 4, "evaluated": 7, "stage1": 0, "stage2": 0, "core": 0}]
-    got = bench.algorithmic_ops(logs, examined=100, n_eq=3)
-    assert got == 100 * (3 * 3 + 3) + 10 * 4 + 4 * 18 + 50 * 5 + 7 * 3
+    import synth
+    t = synth.table_from_rows(["s", "k"], ["string", "int32"], [("abcd", 1), ("abcde", 2), ("", 1)])
+    mds = [[synth.eq(1), synth.jac(0, 1, 2)]]
+    got = bench.algorithmic_bytes(t, mds, {"emitted_pairs": 5})
+    read = 9 + 4 * 4 + 3 * 4                 # string bytes + offsets, int32 keys
+    grams = 2 + 3 + 0                        # |s| - 2 grams per string
+    assert got["encode"] == read + 4 * 3 * 1 + 4 * grams + 4 * 4
+    assert got["block_build"] == 4 * 3 * 1 + 4 * 3
+    assert got["sort"] == 2 * 8 * 5 * 1      # 2 bits per row id, two ids: one 8-bit pass
+
+
+class _Info:
+    def __init__(self, prog):
+        self.op_pred = prog + [0] * (128 - len(prog))
+        self.n_ops = len(prog)
+
+
+def test_plan_units_only_for_the_plan_they_were_counted_for():
+    import json
+    import os
+    import bench
+    path = os.path.join(bench.GOLDEN, "plan_units_c2.json")
+    if not os.path.exists(path):
+        assert bench.plan_units(_Info([2, 8]), 4) is None
+        return
+    d = json.load(open(path))
+    assert bench.plan_units(_Info(list(d["program_ids"])), 4)["units"]["total"] == d["units"]["total"]
+    assert bench.plan_units(_Info(list(reversed(d["program_ids"]))), 4) is None
