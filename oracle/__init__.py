@@ -28,7 +28,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SO = os.path.join(_HERE, "liboracle.so")
 
-KINDS = {"eq": 0, "eq_prefix": 1, "ed": 2, "jaccard": 3, "absdiff": 4}
+KINDS = {"eq": 0, "eq_prefix": 1, "ed": 2, "jaccard": 3, "absdiff": 4, "const_eq": 5, "contain": 6, "tjaccard": 7}
 
 
 class OrCol(ctypes.Structure):
@@ -39,7 +39,22 @@ class OrCol(ctypes.Structure):
 class OrPred(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("col_t", ctypes.c_int32), ("col_s", ctypes.c_int32),
                 ("k", ctypes.c_int32), ("q", ctypes.c_int32), ("num", ctypes.c_uint32), ("den", ctypes.c_uint32),
-                ("delta", ctypes.c_float)]
+                ("delta", ctypes.c_float), ("side", ctypes.c_int32), ("value_len", ctypes.c_uint32),
+                ("value", ctypes.c_void_p)]
+
+
+_CONSTS = []   # constant bytes referenced by marshalled predicates (kept alive)
+
+
+def _const_bytes(v):
+    """A constant as the oracle reads it: bytes of a string, or an int32's 4 bytes."""
+    if isinstance(v, (bytes, bytearray, str)):
+        b = v.encode() if isinstance(v, str) else bytes(v)
+    else:
+        b = np.array([v], np.int32).tobytes()
+    buf = ctypes.create_string_buffer(b, max(len(b), 1))
+    _CONSTS.append(buf)
+    return buf, len(b)
 
 
 def build(force: bool = False) -> str:
@@ -153,8 +168,14 @@ def _rules(mds):
         starts[m + 1] = len(flat)
     arr = (OrPred * max(len(flat), 1))()
     for i, p in enumerate(flat):
-        kind, ct, cs, k, q, num, den, delta = p
-        arr[i] = OrPred(KINDS[kind], ct, cs, k, q, num, den, delta)
+        kind, ct, cs, k, q, num, den, delta = p[:8]
+        side = p[8] if len(p) > 8 else 0
+        op = OrPred(KINDS[kind], ct, cs, k, q, num, den, delta, side, 0, None)
+        if kind == "const_eq":
+            buf, n = _const_bytes(p[9])
+            op.value = ctypes.cast(buf, ctypes.c_void_p)
+            op.value_len = n
+        arr[i] = op
     return starts, arr
 
 
@@ -219,7 +240,18 @@ def block_owned(R, mds, S=None, threads=None, evaluate=True):
 def _norm_pred(p):
     """A predicate with only the parameters its kind uses (a Jaccard threshold
     as a reduced fraction): two predicates are the same iff these are equal."""
-    kind, ct, cs, k, q, num, den, delta = p
+    kind, ct, cs, k, q, num, den, delta = p[:8]
+    side = p[8] if len(p) > 8 else 0
+    if kind == "const_eq":
+        return (kind, ct, cs, side, p[9])
+    if kind == "contain":
+        from math import gcd
+        g = gcd(num, den) or 1
+        return (kind, ct, cs, q, num // g, den // g, side)
+    if kind == "tjaccard":
+        from math import gcd
+        g = gcd(num, den) or 1
+        return (kind, ct, cs, num // g, den // g)
     if kind == "eq":
         return (kind, ct, cs)
     if kind in ("eq_prefix", "ed"):

@@ -59,12 +59,16 @@ struct or_col {
 };
 
 struct or_pred {
-    int32_t kind;            /* 0 eq, 1 eq_prefix, 2 ed, 3 jaccard, 4 absdiff */
+    int32_t kind;            /* 0 eq, 1 eq_prefix, 2 ed, 3 jaccard, 4 absdiff, 5 const_eq, 6 contain,
+                                7 token jaccard */
     int32_t col_t, col_s;    /* column of the left tuple (R) and of the right tuple (S) */
     int32_t k;               /* ed: max distance; eq_prefix: prefix length */
-    int32_t q;               /* jaccard: gram length */
-    uint32_t num, den;       /* jaccard: threshold num/den */
+    int32_t q;               /* jaccard, contain: gram length */
+    uint32_t num, den;       /* jaccard, contain, token jaccard: threshold num/den */
     float delta;             /* absdiff */
+    int32_t side;            /* const_eq: 0 = t.A = c, 1 = s.A = c; contain: whose set divides, 0 = t, 1 = s */
+    uint32_t value_len;      /* const_eq: constant bytes (string column) or 4 (int32 column) */
+    const void *value;       /* const_eq: the constant */
 };
 
 struct Rel {
@@ -105,6 +109,36 @@ std::set<std::string> qgrams(const std::string &s, int q) {
     return g;
 }
 
+/* word tokens: the maximal runs of bytes other than the space byte 0x20 */
+std::set<std::string> tokens(const std::string &s) {
+    std::set<std::string> t;
+    size_t i = 0;
+    while (i < s.size()) {
+        while (i < s.size() && s[i] == ' ') i++;
+        size_t j = i;
+        while (j < s.size() && s[j] != ' ') j++;
+        if (j > i) t.insert(s.substr(i, j - i));
+        i = j;
+    }
+    return t;
+}
+
+/* |A n B| * den >= num * |A u B| for two sets */
+bool set_jaccard_ge(const std::set<std::string> &A, const std::set<std::string> &B, uint32_t num, uint32_t den) {
+    std::vector<std::string> inter;
+    std::set_intersection(A.begin(), A.end(), B.begin(), B.end(), std::back_inserter(inter));
+    uint64_t I = inter.size();
+    uint64_t U = A.size() + B.size() - I;
+    return I * (uint64_t)den >= (uint64_t)num * U;
+}
+
+/* containment of D in the other set E: |D n E| * den >= num * |D| */
+bool contain_ge(const std::set<std::string> &D, const std::set<std::string> &E, uint32_t num, uint32_t den) {
+    std::vector<std::string> inter;
+    std::set_intersection(D.begin(), D.end(), E.begin(), E.end(), std::back_inserter(inter));
+    return (uint64_t)inter.size() * (uint64_t)den >= (uint64_t)num * (uint64_t)D.size();
+}
+
 bool jaccard_ge(const std::string &a, const std::string &b, int q, uint32_t num, uint32_t den) {
     std::set<std::string> A = qgrams(a, q), B = qgrams(b, q);
     std::vector<std::string> inter;
@@ -115,6 +149,17 @@ bool jaccard_ge(const std::string &a, const std::string &b, int q, uint32_t num,
 }
 
 bool holds(const or_pred &p, const Rel &R, int64_t i, const Rel &S, int64_t j) {
+    if (p.kind == 5) {   /* t.A = c (side 0: the left tuple) or s.A = c (side 1: the right tuple) */
+        const or_col &c = p.side == 0 ? R.cols[p.col_t] : S.cols[p.col_s];
+        const int64_t r = p.side == 0 ? i : j;
+        if (!present(c, r)) return false;
+        if (c.type == 1) {
+            int32_t want;
+            std::memcpy(&want, p.value, 4);
+            return static_cast<const int32_t *>(c.data)[r] == want;
+        }
+        return bytes_of(c, r) == std::string(static_cast<const char *>(p.value), p.value_len);
+    }
     const or_col &a = R.cols[p.col_t];
     const or_col &b = S.cols[p.col_s];
     if (!present(a, i) || !present(b, j)) return false;
@@ -139,6 +184,12 @@ bool holds(const or_pred &p, const Rel &R, int64_t i, const Rel &S, int64_t j) {
         volatile float d = x - y;
         return std::fabs((float)d) <= p.delta;
     }
+    case 6: {
+        std::set<std::string> A = qgrams(bytes_of(a, i), p.q), B = qgrams(bytes_of(b, j), p.q);
+        return p.side == 0 ? contain_ge(A, B, p.num, p.den) : contain_ge(B, A, p.num, p.den);
+    }
+    case 7:
+        return set_jaccard_ge(tokens(bytes_of(a, i)), tokens(bytes_of(b, j)), p.num, p.den);
     }
     return false;
 }
@@ -158,14 +209,40 @@ bool dnf_holds(int n_md, const int32_t *md_start, const or_pred *preds, const Re
     return false;
 }
 
+/* A self-join reports the unordered pair {i, j} when some MD is a witness at
+ * (t_i, t_j) or at (t_j, t_i); with symmetric predicates only the two
+ * valuations agree, so the second is evaluated only when some predicate is
+ * asymmetric (asym).  R x S pairs have one valuation, (r_i, s_j). */
+bool pair_holds(int n_md, const int32_t *md_start, const or_pred *preds, const Rel &R, int64_t i, const Rel &S,
+                int64_t j, bool self, bool asym) {
+    if (dnf_holds(n_md, md_start, preds, R, i, S, j)) return true;
+    return self && asym && dnf_holds(n_md, md_start, preds, R, j, S, i);
+}
+
 bool is_equality(const or_pred &p) { return p.kind == 0 || p.kind == 1; }
 
+/* A predicate whose verdict can change when the two tuples swap roles: a
+ * constant on one of them, containment, or two different columns. */
+bool asymmetric(const or_pred &p) { return p.kind == 5 || p.kind == 6 || p.col_t != p.col_s; }
+
+bool any_asymmetric(int n_md, const int32_t *md_start, const or_pred *preds) {
+    for (int32_t k = 0; k < md_start[n_md]; k++)
+        if (asymmetric(preds[k])) return true;
+    return false;
+}
+
+/* The equality predicates a group is keyed on: in a self-join, those that
+ * compare a column with itself (t.A = s.B with A != B relates two different
+ * columns of the pair's tuples and is checked per pair instead). */
+bool groups_on(const or_pred &p, bool self) { return is_equality(p) && (!self || p.col_t == p.col_s); }
+
 /* the grouping key of tuple i for the equality predicates of one MD; false if a value is missing */
-bool group_key(const or_pred *preds, int32_t lo, int32_t hi, const Rel &T, int64_t i, bool left, std::string &key) {
+bool group_key(const or_pred *preds, int32_t lo, int32_t hi, const Rel &T, int64_t i, bool left, std::string &key,
+               bool self) {
     key.clear();
     for (int32_t k = lo; k < hi; k++) {
         const or_pred &p = preds[k];
-        if (!is_equality(p)) continue;
+        if (!groups_on(p, self)) continue;
         const or_col &c = T.cols[left ? p.col_t : p.col_s];
         if (!present(c, i)) return false;
         std::string part;
@@ -199,7 +276,7 @@ void group_ids(const or_pred *preds, int32_t lo, int32_t hi, const Rel &R, const
                std::vector<int64_t> &gr, std::vector<int64_t> &gs, std::vector<std::vector<int64_t>> &left,
                std::vector<std::vector<int64_t>> &right) {
     bool has_eq = false;
-    for (int32_t k = lo; k < hi; k++) has_eq = has_eq || is_equality(preds[k]);
+    for (int32_t k = lo; k < hi; k++) has_eq = has_eq || groups_on(preds[k], S == nullptr);
     gr.assign((size_t)R.n, -1);
     if (S) gs.assign((size_t)S->n, -2);
     left.clear();
@@ -216,7 +293,7 @@ void group_ids(const or_pred *preds, int32_t lo, int32_t hi, const Rel &R, const
     std::unordered_map<std::string, int64_t> index;
     std::string key;
     for (int64_t i = 0; i < R.n; i++) {
-        if (!group_key(preds, lo, hi, R, i, true, key)) continue;
+        if (!group_key(preds, lo, hi, R, i, true, key, S == nullptr)) continue;
         auto it = index.find(key);
         if (it == index.end()) {
             it = index.emplace(key, (int64_t)left.size()).first;
@@ -228,7 +305,7 @@ void group_ids(const or_pred *preds, int32_t lo, int32_t hi, const Rel &R, const
     if (!S) return;
     right.resize(left.size());
     for (int64_t j = 0; j < S->n; j++) {
-        if (!group_key(preds, lo, hi, *S, j, false, key)) { gs[(size_t)j] = -1; continue; }
+        if (!group_key(preds, lo, hi, *S, j, false, key, false)) { gs[(size_t)j] = -1; continue; }
         auto it = index.find(key);
         if (it == index.end()) continue;
         gs[(size_t)j] = it->second;
@@ -295,7 +372,7 @@ struct Owned {
         return I * (uint64_t)p.den >= (uint64_t)p.num * U;
     }
 
-    bool dnf(int64_t i, int64_t j) const {
+    bool dnf1(int64_t i, int64_t j) const {
         for (int m = 0; m < n_md; m++) {
             bool all = true;
             for (int32_t k = md_start[m]; k < md_start[m + 1] && all; k++) all = holds_p(preds[k], i, j);
@@ -303,6 +380,10 @@ struct Owned {
         }
         return false;
     }
+
+    /* as pair_holds: both valuations of a self-join pair when a predicate is asymmetric */
+    bool dnf(int64_t i, int64_t j) const { return dnf1(i, j) || (self && asym && dnf1(j, i)); }
+    bool asym = false;
 };
 
 }  // namespace
@@ -349,7 +430,8 @@ int64_t or_block_literal(int64_t nR, int32_t ncR, const or_col *R, int64_t nS, i
     std::vector<uint64_t> res;
     for (int64_t i = 0; i < r.n; i++)
         for (int64_t j = S ? 0 : i + 1; j < s.n; j++)
-            if (dnf_holds(n_md, md_start, preds, r, i, s, j)) res.push_back(((uint64_t)i << 32) | (uint64_t)j);
+            if (dnf_holds(n_md, md_start, preds, r, i, s, j) || (!S && dnf_holds(n_md, md_start, preds, r, j, s, i)))
+                res.push_back(((uint64_t)i << 32) | (uint64_t)j);
     return emit(res, out, cap);
 }
 
@@ -364,6 +446,7 @@ int64_t or_block_hash(int64_t nR, int32_t ncR, const or_col *R, int64_t nS, int3
     Rel r{nR, ncR, R};
     Rel s = S ? Rel{nS, ncS, S} : r;
     const bool self = (S == nullptr);
+    const bool asym = any_asymmetric(n_md, md_start, preds);
     struct Group { std::vector<int64_t> left, right; };
     std::vector<Group> groups;
     for (int m = 0; m < n_md; m++) {
@@ -371,14 +454,14 @@ int64_t or_block_hash(int64_t nR, int32_t ncR, const or_col *R, int64_t nS, int3
         std::string key;
         size_t first = groups.size();
         for (int64_t i = 0; i < r.n; i++) {
-            if (!group_key(preds, md_start[m], md_start[m + 1], r, i, true, key)) continue;
+            if (!group_key(preds, md_start[m], md_start[m + 1], r, i, true, key, self)) continue;
             auto it = index.find(key);
             if (it == index.end()) { it = index.emplace(key, groups.size()).first; groups.emplace_back(); }
             groups[it->second].left.push_back(i);
         }
         if (!self) {
             for (int64_t j = 0; j < s.n; j++) {
-                if (!group_key(preds, md_start[m], md_start[m + 1], s, j, false, key)) continue;
+                if (!group_key(preds, md_start[m], md_start[m + 1], s, j, false, key, false)) continue;
                 auto it = index.find(key);
                 if (it == index.end()) continue;
                 groups[it->second].right.push_back(j);
@@ -399,14 +482,14 @@ int64_t or_block_hash(int64_t nR, int32_t ncR, const or_col *R, int64_t nS, int3
                         int64_t i = G.left[a], j = G.left[b];
                         uint64_t key = ((uint64_t)i << 32) | (uint64_t)j;
                         if (count_candidates) cand[t].push_back(key);
-                        if (dnf_holds(n_md, md_start, preds, r, i, s, j)) res[t].push_back(key);
+                        if (pair_holds(n_md, md_start, preds, r, i, s, j, self, asym)) res[t].push_back(key);
                     }
             } else {
                 for (int64_t i : G.left)
                     for (int64_t j : G.right) {
                         uint64_t key = ((uint64_t)i << 32) | (uint64_t)j;
                         if (count_candidates) cand[t].push_back(key);
-                        if (dnf_holds(n_md, md_start, preds, r, i, s, j)) res[t].push_back(key);
+                        if (pair_holds(n_md, md_start, preds, r, i, s, j, self, asym)) res[t].push_back(key);
                     }
             }
         }
@@ -501,6 +584,7 @@ int64_t or_block_owned(int64_t nR, int32_t ncR, const or_col *R, int64_t nS, int
         }
     }
     Owned ev{n_md, md_start, preds, r, s, grams, self};
+    ev.asym = any_asymmetric(n_md, md_start, preds);
     std::atomic<size_t> next{0};
     std::vector<std::vector<uint64_t>> res((size_t)nt);
     std::vector<int64_t> cand((size_t)nt, 0);
@@ -696,7 +780,7 @@ void or_check_pairs(int64_t nR, int32_t ncR, const or_col *R, int64_t nS, int32_
     Rel s = S ? Rel{nS, ncS, S} : r;
     for (int64_t k = 0; k < n; k++) {
         int64_t i = (int64_t)(pairs[k] >> 32), j = (int64_t)(pairs[k] & 0xffffffffu);
-        verdict[k] = dnf_holds(n_md, md_start, preds, r, i, s, j) ? 1 : 0;
+        verdict[k] = pair_holds(n_md, md_start, preds, r, i, s, j, S == nullptr, true) ? 1 : 0;
     }
 }
 

@@ -15,8 +15,9 @@ Column representation (numpy, host memory):
   fp32   : data float32[n]
   valid  : uint8[n] (1 = present) or None (all present)
 
-Predicate representation: a tuple ``(kind, col_t, col_s, k, q, num, den, delta)``
-with kind one of "eq", "eq_prefix", "ed", "jaccard", "absdiff".
+Predicate representation: a tuple ``(kind, col_t, col_s, k, q, num, den, delta[, side[, value]])``
+with kind one of "eq", "eq_prefix", "ed", "jaccard", "absdiff", "const_eq", "contain",
+"tjaccard" (side and value as in ``const_eq`` / ``contain``).
 """
 from __future__ import annotations
 
@@ -251,6 +252,21 @@ def jac(c, num, den, q=3, cs=None):
 
 def absdiff(c, delta, cs=None):
     return ("absdiff", c, c if cs is None else cs, 0, 0, 0, 0, float(delta))
+
+
+def const_eq(c, value, side=0):
+    """t.A = c (side 0: the pair's first tuple) or s.A = c (side 1: its second)."""
+    return ("const_eq", c, c, 0, 0, 0, 0, 0.0, side, value)
+
+
+def contain(c, num, den, q=3, side=0, cs=None):
+    """q-gram containment: |G(t.A) n G(s.B)| >= num/den of |G(t.A)| (side 0) or of |G(s.B)| (side 1)."""
+    return ("contain", c, c if cs is None else cs, 0, q, num, den, 0.0, side)
+
+
+def tjac(c, num, den, cs=None):
+    """Jaccard similarity of the word-token sets (maximal runs of non-space bytes) >= num/den."""
+    return ("tjaccard", c, c if cs is None else cs, 0, 0, num, den, 0.0)
 
 
 BASE_SEED = 20241004
