@@ -9,21 +9,30 @@
  *   self-join : Ca = { (i, j) : 0 <= i < j < n,  some phi satisfied by (t_i, t_j) }
  *   R x S     : Ca = { (i, j) : i in R, j in S,  some phi satisfied by (r_i, s_j) }
  *
- * Predicates (Section 2, "Predicates": t.A = s.B and t.A ~ s.B with a
- * similarity measure and a threshold):
- *   HB_P_EQ          t.A = s.B          strings by bytes, int32 by value
+ * Predicates (Section 2, "Predicates": t.A = c, t.A = s.B and t.A ~ s.B with
+ * a symmetric or asymmetric similarity measure and a threshold):
+ *   HB_P_EQ          t.A = s.B          strings by bytes, int32 by value; A and B may be
+ *                                       two columns of one relation in a self-join
  *   HB_P_EQ_PREFIX   first k bytes equal (strings; a shorter string is its own prefix)
  *   HB_P_ED_LE       Levenshtein distance over bytes <= k          (edit distance, Example 2)
  *   HB_P_JACCARD_GE  q-gram set Jaccard >= num/den, compared as    (Jaccard measure, Example 2)
  *                    |A n B| * den >= num * |A u B| (q = 1..4, contiguous q-byte
  *                    substrings, no padding; a string shorter than q has no grams)
  *   HB_P_ABSDIFF_LE  fabsf(a - b) <= delta in binary32 (fp32 columns)
+ *   HB_P_CONST_EQ    t.A = c or s.A = c (string or int32 column; the constant is copied)
+ *   HB_P_CONTAIN_GE  |G(t.A) n G(s.B)| * den >= num * |G(side's value)|, q-grams as for
+ *                    Jaccard: how much of one side's gram set the other contains (asymmetric)
+ *   HB_P_TOKEN_JACCARD_GE  Jaccard of the sets of word tokens (maximal runs of bytes other
+ *                    than the space 0x20) >= num/den, compared in integers as above
  * A missing operand (valid[i] == 0) makes every predicate false (Example 3:
  * (t2, t3) is not a witness because t2.price is missing).
  *
- * All similarity predicates provided are symmetric, so a self-join emits each
- * unordered pair once as (i, j) with i < j (Section 5.1, last paragraph of
- * "Reusing computation").  The result is exact: no sampling, no approximation.
+ * A self-join emits each unordered pair once as (i, j) with i < j: the pair is
+ * in the result when some MD is a witness at (t_i, t_j) or at (t_j, t_i).
+ * With symmetric predicates only the two valuations agree (Section 5.1, last
+ * paragraph of "Reusing computation"); an MD with a constant, a containment or
+ * two different columns is evaluated at both.  The result is exact: no
+ * sampling, no approximation.
  *
  * Errors: every call returns an hb_status; nothing throws across this
  * boundary.  On a non-OK status hb_last_error() describes it.  Calls on one
@@ -76,7 +85,10 @@ typedef enum {
     HB_P_EQ_PREFIX = 1,
     HB_P_ED_LE = 2,
     HB_P_JACCARD_GE = 3,
-    HB_P_ABSDIFF_LE = 4
+    HB_P_ABSDIFF_LE = 4,
+    HB_P_CONST_EQ = 5,          /* t.A = c (side 0) or s.A = c (side 1) */
+    HB_P_CONTAIN_GE = 6,        /* q-gram containment, asymmetric */
+    HB_P_TOKEN_JACCARD_GE = 7   /* Jaccard of word-token sets */
 } hb_pkind;
 
 /* One predicate of an MD precondition (Section 2, "Predicates"). */
@@ -88,8 +100,14 @@ typedef struct {
                                  EQ_PREFIX: prefix length (>= 1) */
     int32_t q;                /* JACCARD_GE: gram length, 1..4; a compared string may hold at most
                                  8192 grams (a longer one makes hb_plan / hb_block return HB_ERR_ARG) */
-    uint32_t num, den;        /* JACCARD_GE: threshold num/den, 0 <= num <= den, den >= 1 */
+    uint32_t num, den;        /* JACCARD_GE, CONTAIN_GE, TOKEN_JACCARD_GE: threshold num/den,
+                                 0 <= num <= den, den >= 1 */
     float delta;              /* ABSDIFF_LE: threshold (>= 0) */
+    int32_t side;             /* CONST_EQ: 0 = the pair's first tuple (t.A = c, column col_t),
+                                 1 = its second (s.A = c, column col_s);
+                                 CONTAIN_GE: whose gram set divides, 0 = t's (col_t), 1 = s's (col_s) */
+    uint32_t value_len;       /* CONST_EQ: bytes of value (string column) or 4 (int32 column) */
+    const void *value;        /* CONST_EQ: the constant (host memory, copied by hb_add_md) */
 } hb_predicate;
 
 typedef struct { uint32_t tid1, tid2; } hb_pair;

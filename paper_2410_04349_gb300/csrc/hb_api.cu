@@ -91,6 +91,12 @@ static void free_dicts(hb_ctx *c) {
         if (d) cudaFreeAsync(d, c->stream);
     c->dict.clear();
     c->dict_cap.clear();
+    for (auto &t : c->tok) {
+        if (t.table) cudaFreeAsync(t.table, c->stream);
+        if (t.start) cudaFreeAsync(t.start, c->stream);
+        if (t.len) cudaFreeAsync(t.len, c->stream);
+    }
+    c->tok.clear();
 }
 
 static void invalidate_encoding(hb_ctx *c) {
@@ -360,8 +366,11 @@ extern "C" hb_status hb_load_table(hb_ctx *c, int32_t side, int64_t n_rows, int3
 
 // ===================================================================== rules
 static bool same_pred(const hb_predicate &a, const hb_predicate &b) {
-    return a.kind == b.kind && a.col_t == b.col_t && a.col_s == b.col_s && a.k == b.k && a.q == b.q &&
-           a.num == b.num && a.den == b.den && a.delta == b.delta;
+    if (!(a.kind == b.kind && a.col_t == b.col_t && a.col_s == b.col_s && a.k == b.k && a.q == b.q &&
+          a.num == b.num && a.den == b.den && a.delta == b.delta && a.side == b.side))
+        return false;
+    if (a.kind != HB_P_CONST_EQ) return true;
+    return a.value_len == b.value_len && memcmp(a.value, b.value, a.value_len) == 0;
 }
 
 static hb_predicate normalize(hb_predicate p) {
@@ -381,6 +390,23 @@ static hb_predicate normalize(hb_predicate p) {
         break;
     }
     case HB_P_ABSDIFF_LE: r.delta = p.delta; break;
+    case HB_P_CONTAIN_GE:
+    case HB_P_TOKEN_JACCARD_GE: {
+        r.q = p.kind == HB_P_CONTAIN_GE ? p.q : 0;
+        r.side = p.kind == HB_P_CONTAIN_GE ? p.side : 0;
+        uint32_t g = std::gcd(p.num, p.den);
+        if (g == 0) g = 1;
+        r.num = p.num / g;
+        r.den = p.den / g;
+        break;
+    }
+    case HB_P_CONST_EQ:
+        r.side = p.side;
+        r.value = p.value;
+        r.value_len = p.value_len;
+        if (p.side == 0) r.col_s = p.col_t;   // the constant's column, on the side it names
+        else r.col_t = p.col_s;
+        break;
     default: break;
     }
     return r;
@@ -393,7 +419,7 @@ extern "C" hb_status hb_add_md(hb_ctx *c, int32_t n_pred, const hb_predicate *pr
     std::vector<hb_predicate> v;
     for (int i = 0; i < n_pred; i++) {
         const hb_predicate &p = preds[i];
-        if (p.kind < 0 || p.kind > 4) return fail(HB_ERR_ARG, "hb_add_md: unknown predicate kind");
+        if (p.kind < 0 || p.kind > 7) return fail(HB_ERR_ARG, "hb_add_md: unknown predicate kind");
         if (p.col_t < 0 || p.col_s < 0) return fail(HB_ERR_ARG, "hb_add_md: negative column index");
         if (p.kind == HB_P_EQ_PREFIX && p.k < 1) return fail(HB_ERR_ARG, "hb_add_md: prefix length must be >= 1");
         if (p.kind == HB_P_ED_LE && (p.k < 0 || p.k > 31))
@@ -402,7 +428,18 @@ extern "C" hb_status hb_add_md(hb_ctx *c, int32_t n_pred, const hb_predicate *pr
             return fail(HB_ERR_ARG, "hb_add_md: Jaccard needs q in 1..4 and 0 <= num <= den, den >= 1");
         if (p.kind == HB_P_ABSDIFF_LE && !(p.delta >= 0.f))
             return fail(HB_ERR_ARG, "hb_add_md: |a-b| threshold must be >= 0");
-        v.push_back(normalize(p));
+        if (p.kind == HB_P_CONTAIN_GE && (p.q < 1 || p.q > 4 || p.den < 1 || p.num > p.den || p.side < 0 || p.side > 1))
+            return fail(HB_ERR_ARG, "hb_add_md: containment needs q in 1..4, 0 <= num <= den, den >= 1, side 0 or 1");
+        if (p.kind == HB_P_TOKEN_JACCARD_GE && (p.den < 1 || p.num > p.den))
+            return fail(HB_ERR_ARG, "hb_add_md: token Jaccard needs 0 <= num <= den, den >= 1");
+        if (p.kind == HB_P_CONST_EQ && (p.side < 0 || p.side > 1 || (p.value_len > 0 && !p.value)))
+            return fail(HB_ERR_ARG, "hb_add_md: a constant needs side 0 or 1 and its bytes");
+        hb_predicate n = normalize(p);
+        if (p.kind == HB_P_CONST_EQ) {
+            c->consts.emplace_back(static_cast<const char *>(p.value ? p.value : ""), (size_t)p.value_len);
+            n.value = c->consts.back().data();
+        }
+        v.push_back(n);
     }
     c->md_raw.push_back(v);
     c->planned = false;
@@ -414,6 +451,7 @@ extern "C" hb_status hb_add_md(hb_ctx *c, int32_t n_pred, const hb_predicate *pr
 extern "C" hb_status hb_clear_mds(hb_ctx *c) {
     if (!c) return fail(HB_ERR_ARG, "hb_clear_mds: ctx is NULL");
     c->md_raw.clear();
+    c->consts.clear();
     c->planned = false;
     invalidate_encoding(c);
     return HB_OK;
@@ -434,6 +472,26 @@ static hb_status check_column(hb_ctx *c, int side, int col, int want_type, const
     return HB_OK;
 }
 
+// A predicate whose verdict can change when the pair's two tuples exchange
+// roles: a constant on one of them, containment, or two different columns.
+static bool asymmetric(const hb_predicate &p) {
+    return p.kind == HB_P_CONST_EQ || p.kind == HB_P_CONTAIN_GE || p.col_t != p.col_s;
+}
+
+// The MD with its two tuple variables exchanged: a self-join pair {i, j}
+// (i < j) is a candidate when some MD is a witness at (t_i, t_j) or at
+// (t_j, t_i), and an MD's witness at (t_j, t_i) is its transpose's at
+// (t_i, t_j), so evaluating every MD and the transpose of every asymmetric
+// one at (t_i, t_j) gives the self-join result.
+static std::vector<hb_predicate> transpose(const std::vector<hb_predicate> &md) {
+    std::vector<hb_predicate> out = md;
+    for (hb_predicate &p : out) {
+        std::swap(p.col_t, p.col_s);
+        if (p.kind == HB_P_CONST_EQ || p.kind == HB_P_CONTAIN_GE) p.side ^= 1;
+    }
+    return out;
+}
+
 // distinct predicates, equality keys, feature groups and the record layout
 static hb_status build_layout(hb_ctx *c, bool job_key) {
     const bool self = is_self(c);
@@ -442,13 +500,39 @@ static hb_status build_layout(hb_ctx *c, bool job_key) {
     c->md_preds.clear();
     c->eqkeys.clear();
     c->groups.clear();
-    for (auto &md : c->md_raw) {
+    std::vector<std::vector<hb_predicate>> mds = c->md_raw;
+    if (self) {
+        const size_t n0 = mds.size();
+        for (size_t m = 0; m < n0; m++) {
+            bool asym = false;
+            for (const hb_predicate &p : mds[m]) asym = asym || asymmetric(p);
+            if (asym) mds.push_back(transpose(mds[m]));
+        }
+        if ((int)mds.size() > HB_MAX_MDS)
+            return fail(HB_ERR_ARG, "at most 64 MDs, counting the transposed copy of each asymmetric MD");
+    }
+    c->n_user_mds = (int)c->md_raw.size();
+    for (auto &md : mds) {
         std::vector<int> ids;
         for (auto &p : md) {
-            if (self && p.col_t != p.col_s)
-                return fail(HB_ERR_ARG, "self-join predicates must compare the same column (col_t == col_s)");
+            if (self && p.col_t != p.col_s && p.kind != HB_P_EQ && p.kind != HB_P_CONST_EQ)
+                return fail(HB_ERR_ARG, "in a self-join only equality compares two different columns (col_t != col_s)");
             const char *what = "predicate";
             switch (p.kind) {
+            case HB_P_CONST_EQ: {
+                const int sd = p.side == 0 ? 0 : rs, col = p.side == 0 ? p.col_t : p.col_s;
+                HB_TRY(check_column(c, sd, col, -1, what));
+                const int ty = c->side[sd].cols[col].type;
+                if (ty == HB_COL_FP32 || (ty == HB_COL_INT32 && p.value_len != 4))
+                    return fail(HB_ERR_ARG, "a constant compares a string column (value bytes) or an int32 column "
+                                            "(4 value bytes)");
+                break;
+            }
+            case HB_P_CONTAIN_GE:
+            case HB_P_TOKEN_JACCARD_GE:
+                HB_TRY(check_column(c, 0, p.col_t, HB_COL_STRING, what));
+                HB_TRY(check_column(c, rs, p.col_s, HB_COL_STRING, what));
+                break;
             case HB_P_EQ: {
                 HB_TRY(check_column(c, 0, p.col_t, -1, what));
                 HB_TRY(check_column(c, rs, p.col_s, -1, what));
@@ -482,9 +566,10 @@ static hb_status build_layout(hb_ctx *c, bool job_key) {
         }
         c->md_preds.push_back(ids);
     }
-    // equality keys
+    // equality keys (in a self-join an equality across two columns is checked per pair instead)
     for (auto &pi : c->preds) {
         if (pi.p.kind != HB_P_EQ && pi.p.kind != HB_P_EQ_PREFIX) continue;
+        if (self && pi.p.col_t != pi.p.col_s) continue;
         EqKey k{pi.p.col_t, pi.p.col_s, pi.p.kind == HB_P_EQ_PREFIX ? pi.p.k : -1};
         int e = -1;
         for (size_t j = 0; j < c->eqkeys.size(); j++)
@@ -499,18 +584,44 @@ static hb_status build_layout(hb_ctx *c, bool job_key) {
     c->n_eq_total = (int)c->eqkeys.size() + (job_key ? 1 : 0);
     if (c->n_eq_total > MAX_EQ) return fail(HB_ERR_ARG, "at most 16 distinct equality keys");
     int word = c->n_eq_total;
-    for (auto &pi : c->preds) {
+    for (int pid = 0; pid < (int)c->preds.size(); pid++) {
+        PredInfo &pi = c->preds[pid];
         if (pi.eq_index >= 0) continue;
-        int kind = pi.p.kind == HB_P_ED_LE ? OP_ED : pi.p.kind == HB_P_JACCARD_GE ? OP_JAC : OP_ABS;
-        int q = kind == OP_JAC ? pi.p.q : 0;
+        const hb_predicate &p = pi.p;
+        int kind = OP_ABS, q = 0, tokens = 0, ct = p.col_t, cs = p.col_s;
+        switch (p.kind) {
+        case HB_P_ED_LE: kind = OP_ED; break;
+        case HB_P_JACCARD_GE:
+        case HB_P_CONTAIN_GE: kind = OP_JAC; q = p.q; break;   // containment reads the q-gram group
+        case HB_P_TOKEN_JACCARD_GE: kind = OP_JAC; tokens = 1; break;
+        case HB_P_EQ:   // two columns of one relation: codes of both in one dictionary
+            kind = OP_EQX;
+            ct = std::min(p.col_t, p.col_s);
+            cs = std::max(p.col_t, p.col_s);
+            break;
+        case HB_P_CONST_EQ:   // a flag word per (side's column, constant)
+            kind = OP_CONST;
+            if (self) ct = cs = p.col_t;
+            else if (p.side == 0) cs = -1;
+            else ct = -1;
+            break;
+        default: break;
+        }
         int g = -1;
-        for (size_t j = 0; j < c->groups.size(); j++) {
+        for (size_t j = 0; j < c->groups.size() && g < 0; j++) {
             const FeatGroup &G = c->groups[j];
-            if (G.kind == kind && G.col_t == pi.p.col_t && G.col_s == pi.p.col_s && G.q == q) g = (int)j;
+            if (G.kind != kind || G.col_t != ct || G.col_s != cs || G.q != q || G.tokens != tokens) continue;
+            if (kind == OP_CONST) {
+                const hb_predicate &o = c->preds[G.pred].p;
+                if (o.value_len != p.value_len || memcmp(o.value, p.value, p.value_len) != 0) continue;
+            }
+            g = (int)j;
         }
         if (g < 0) {
-            FeatGroup G{kind, pi.p.col_t, pi.p.col_s, q, word};
-            word += kind == OP_ED ? FEAT_ED_WORDS : kind == OP_JAC ? FEAT_JAC_WORDS : FEAT_ABS_WORDS;
+            FeatGroup G{kind, ct, cs, q, word};
+            G.tokens = tokens;
+            G.pred = pid;
+            word += kind == OP_ED ? FEAT_ED_WORDS : kind == OP_JAC ? FEAT_JAC_WORDS : kind == OP_EQX ? 2 : 1;
             g = (int)c->groups.size();
             c->groups.push_back(G);
         }
@@ -525,7 +636,7 @@ static hb_status build_layout(hb_ctx *c, bool job_key) {
     c->eqset.assign(n_md, 0);
     c->eqonly = 0;
     for (int m = 0; m < n_md; m++) {
-        uint16_t s = job_key ? (uint16_t)(1u << c->eqkeys.size()) : 0;
+        uint16_t s = job_key ? (uint16_t)(1u << c->eqkeys.size()) : 0;   // (cross-column equalities are ops)
         bool has_other = false;
         for (int id : c->md_preds[m]) {
             if (c->preds[id].eq_index >= 0) s |= (uint16_t)(1u << c->preds[id].eq_index);
@@ -566,16 +677,21 @@ static hb_status plan_stats(hb_ctx *c, std::vector<double> &sp, std::vector<doub
     std::vector<SampleSpec> specs(P);
     for (int p = 0; p < P; p++) {
         const hb_predicate &q = c->preds[p].p;
-        const DevCol &col = R.cols[q.col_t];
+        // a constant on S's tuple (R x S) has no R column: its value distribution is not sampled
+        const int ci = (q.kind == HB_P_CONST_EQ && q.side == 1 && !is_self(c)) ? 0 : q.col_t;
+        const DevCol &col = R.cols[ci];
         SampleSpec s{};
-        s.kind = q.kind;
+        // sampled like the basic kind they resemble: constants and cross-column equality by value,
+        // containment and word-token Jaccard by a MinHash over q-grams
+        s.kind = q.kind == HB_P_CONST_EQ ? HB_P_EQ
+                 : (q.kind == HB_P_CONTAIN_GE || q.kind == HB_P_TOKEN_JACCARD_GE) ? HB_P_JACCARD_GE : q.kind;
         s.type = col.type;
         s.bytes = col.bytes;
         s.off = col.off;
         s.vals = col.vals;
         s.valid = col.valid;
         s.prefix = q.kind == HB_P_EQ_PREFIX ? q.k : -1;
-        s.q = q.kind == HB_P_JACCARD_GE ? q.q : 3;
+        s.q = (q.kind == HB_P_JACCARD_GE || q.kind == HB_P_CONTAIN_GE) ? q.q : 3;
         s.delta = q.delta;
         specs[p] = s;
     }
@@ -625,7 +741,10 @@ static hb_status plan_stats(hb_ctx *c, std::vector<double> &sp, std::vector<doub
         case HB_P_EQ_PREFIX: cost[p] = 1.0; break;
         case HB_P_ABSDIFF_LE: cost[p] = 2.0; break;
         case HB_P_ED_LE: cost[p] = 4.0 + 0.5 * mlen * (2.0 * q.k + 1.0); break;
-        case HB_P_JACCARD_GE: cost[p] = 6.0 + 2.0 * mg; break;
+        case HB_P_JACCARD_GE:
+        case HB_P_CONTAIN_GE: cost[p] = 6.0 + 2.0 * mg; break;
+        case HB_P_TOKEN_JACCARD_GE: cost[p] = 6.0 + 2.0 * (mlen / 6.0); break;
+        case HB_P_CONST_EQ: cost[p] = 1.0; break;
         }
     }
     // the sampled lengths / gram counts stay for the learned cost model's
@@ -731,13 +850,22 @@ static hb_status finish_plan(hb_ctx *c, int mode, const std::vector<double> &sp,
         const PredInfo &pi = c->preds[program[k]];
         const FeatGroup &G = c->groups[pi.group];
         Op op{};
-        op.kind = (uint8_t)G.kind;
+        op.kind = (uint8_t)(pi.p.kind == HB_P_CONTAIN_GE ? OP_CONT : G.kind);
         op.feat = (uint8_t)G.word;
         op.hot = (uint8_t)(c->n_eq_total + pi.group);
         op.k = (uint8_t)(pi.p.kind == HB_P_ED_LE ? pi.p.k : 0);
         op.num = pi.p.num;
         op.den = pi.p.den;
         op.delta = pi.p.delta;
+        if (op.kind == OP_EQX) {   // t-side code word, s-side code word (the group holds min(col), max(col))
+            const bool lo_first = pi.p.col_t <= pi.p.col_s;
+            op.feat = (uint8_t)(G.word + (lo_first ? 0 : 1));
+            op.k = (uint8_t)(G.word + (lo_first ? 1 : 0));
+        } else if (op.kind == OP_CONST) {
+            op.num = (uint32_t)pi.p.side;
+        } else if (op.kind == OP_CONT) {
+            op.k = (uint8_t)pi.p.side;
+        }
         for (int m = 0; m < n_md; m++) {
             for (int p : c->md_preds[m])
                 if (p == program[k]) op.need |= 1ull << m;
@@ -761,8 +889,10 @@ static hb_status finish_plan(hb_ctx *c, int mode, const std::vector<double> &sp,
             if (c->ops[k].need & (1ull << m)) mdops[m][n++] = (int)k;
     }
     auto group_of = [&](int k) { return c->preds[program[k]].group; };
+    // only edit distance, Jaccard and |a-b| have filter operands and screens
+    auto screenable = [&](int k) { const int kd = c->ops[k].kind; return kd == OP_ED || kd == OP_JAC || kd == OP_ABS; };
     for (int m = 0; m < n_md; m++) {
-        if (mdops[m][0] < 0) continue;
+        if (mdops[m][0] < 0 || !screenable(mdops[m][0])) continue;
         const int g = group_of(mdops[m][0]);
         if (hot_word[g] < 0) {
             hot_word[g] = (int)c->hot_map.size();
@@ -774,7 +904,7 @@ static hb_status finish_plan(hb_ctx *c, int mode, const std::vector<double> &sp,
     auto add_bins = [&](int k) {
         const int g = group_of(k);
         const FeatGroup &G = c->groups[g];
-        const int nb = G.kind == OP_ED ? 1 : G.kind == OP_JAC ? 2 : 0;
+        const int nb = !screenable(k) ? 0 : G.kind == OP_ED ? 1 : G.kind == OP_JAC ? 2 : 0;
         const int w0 = G.kind == OP_ED ? FEAT_ED_SIG : FEAT_JAC_MASK;
         if (nb == 0 || hot_word[g] < 0 || hot_bins[g] >= 0 || (int)c->hot_map.size() + nb > HOT_BUDGET) return;
         hot_bins[g] = (int)c->hot_map.size();
@@ -790,7 +920,7 @@ static hb_status finish_plan(hb_ctx *c, int mode, const std::vector<double> &sp,
     for (int m : by_pass)
         if (mdops[m][0] >= 0) add_bins(mdops[m][0]);
     for (int m : by_pass) {
-        if (mdops[m][1] < 0) continue;
+        if (mdops[m][1] < 0 || !screenable(mdops[m][1])) continue;
         const int g = group_of(mdops[m][1]);
         if (hot_word[g] < 0 && (int)c->hot_map.size() + 1 <= HOT_BUDGET) {
             hot_word[g] = (int)c->hot_map.size();
@@ -803,8 +933,8 @@ static hb_status finish_plan(hb_ctx *c, int mode, const std::vector<double> &sp,
     c->HW = (int)c->hot_map.size();
     for (size_t k = 0; k < c->ops.size(); k++) {
         const int g = group_of((int)k);
-        c->ops[k].hot = hot_word[g] < 0 ? 255 : (uint8_t)hot_word[g];
-        c->ops[k].hot2 = hot_bins[g] < 0 ? 255 : (uint8_t)hot_bins[g];
+        c->ops[k].hot = (hot_word[g] < 0 || !screenable((int)k)) ? 255 : (uint8_t)hot_word[g];
+        c->ops[k].hot2 = (hot_bins[g] < 0 || !screenable((int)k)) ? 255 : (uint8_t)hot_bins[g];
     }
     hb_plan_info &I = c->info;
     memset(&I, 0, sizeof(I));
@@ -947,7 +1077,74 @@ hb_status encode_side(hb_ctx *c, int side) {
     HB_CUDA(cudaMemsetAsync(flag.p, 0, 16, c->stream));
     for (size_t g = 0; g < c->groups.size(); g++) {
         const FeatGroup &G = c->groups[g];
+        if (G.kind == OP_CONST) {
+            // the flag word of the side the constant names (the other side's word stays 0)
+            const int ci = side == 0 ? G.col_t : G.col_s;
+            if (ci < 0) continue;
+            const hb_predicate &q = c->preds[G.pred].p;
+            Buf cv;
+            HB_TRY(grow(c, cv, q.value_len + 8));
+            HB_CUDA(cudaMemcpyAsync(cv.p, q.value, q.value_len, cudaMemcpyHostToDevice, c->stream));
+            const_feature(S.cols[ci], as<uint8_t>(cv), q.value_len, S.rec, W, G.word, c->stream);
+            HB_CUDA(cudaStreamSynchronize(c->stream));   // the constant's host bytes were read
+            free_buf(c, cv);
+            continue;
+        }
         const DevCol &col = S.cols[side == 0 ? G.col_t : G.col_s];
+        if (G.kind == OP_EQX) {
+            // two columns of one relation (self-join): both coded in the first column's dictionary
+            const DevCol &A = S.cols[G.col_t], &B = S.cols[G.col_s];
+            const uint64_t cap = pow2_at_least(std::max<uint64_t>(2 * (uint64_t)n, 1024));
+            Buf table, cb;
+            HB_TRY(grow(c, table, sizeof(uint64_t) * cap));
+            HB_TRY(grow(c, cb, sizeof(uint32_t) * (size_t)(n + 1)));
+            dict_build(A, -1, as<uint64_t>(table), cap, as<uint32_t>(cb), c->stream);
+            code_feature(as<uint32_t>(cb), n, S.rec, W, G.word, c->stream);
+            dict_probe(B, -1, A, -1, as<uint64_t>(table), cap, as<uint32_t>(cb), c->stream);
+            code_feature(as<uint32_t>(cb), n, S.rec, W, G.word + 1, c->stream);
+            free_buf(c, table);
+            free_buf(c, cb);
+            continue;
+        }
+        if (G.kind == OP_JAC && G.tokens) {
+            // word tokens: exact codes from R's token dictionary (S's tokens probe it), then per
+            // string the sorted unique code list and its Jaccard feature words
+            HB_TRY(grow(c, c->w_jac, tok_scratch_bytes(n)));
+            Buf toff;
+            HB_TRY(grow(c, toff, sizeof(uint32_t) * (size_t)(n + 2)));
+            const int64_t T = tok_count(col, as<uint32_t>(toff), c->w_jac.p, c->w_jac.bytes, c->stream);
+            if (T >= (1ll << 29)) return fail(HB_ERR_ARG, "more than 2^29 word tokens in a column");
+            void *ts = nullptr, *tl = nullptr;
+            HB_TRY(dmalloc(c, &ts, sizeof(uint32_t) * (size_t)(T + 1)));
+            HB_TRY(dmalloc(c, &tl, sizeof(uint32_t) * (size_t)(T + 1)));
+            HB_TRY(dmalloc(c, &p, sizeof(uint32_t) * (size_t)(T + 4)));
+            S.grams[g] = static_cast<uint32_t *>(p);
+            tok_fill(col, as<uint32_t>(toff), static_cast<uint32_t *>(ts), static_cast<uint32_t *>(tl), c->stream);
+            if (c->tok.size() < c->groups.size()) c->tok.resize(c->groups.size());
+            hb_ctx::TokDict &D = c->tok[g];
+            if (side == 0) {
+                D.cap = pow2_at_least(std::max<uint64_t>(2 * (uint64_t)T, 1024));
+                void *tb = nullptr;
+                HB_TRY(dmalloc(c, &tb, sizeof(uint64_t) * D.cap));
+                D.table = static_cast<uint64_t *>(tb);
+                D.start = static_cast<uint32_t *>(ts);
+                D.len = static_cast<uint32_t *>(tl);
+                D.bytes = col.bytes;
+                tok_insert(col.bytes, D.start, D.len, T, D.table, D.cap, S.grams[g], c->stream);
+            } else {
+                if (!D.table) return fail(HB_ERR_STATE, "R's word tokens are not encoded");
+                tok_probe(col.bytes, static_cast<uint32_t *>(ts), static_cast<uint32_t *>(tl), T, D.bytes, D.start,
+                          D.len, D.table, D.cap, S.grams[g], c->stream);
+            }
+            tok_lists(col, as<uint32_t>(toff), static_cast<uint32_t *>(ts), static_cast<uint32_t *>(tl), S.grams[g],
+                      S.rec, W, G.word, as<unsigned int>(flag), c->stream);
+            if (side != 0) {
+                cudaFreeAsync(ts, c->stream);
+                cudaFreeAsync(tl, c->stream);
+            }
+            free_buf(c, toff);
+            continue;
+        }
         if (G.kind == OP_ED) {
             ed_features(col, S.rec, W, G.word, c->stream);
         } else if (G.kind == OP_ABS) {
@@ -965,7 +1162,7 @@ hb_status encode_side(hb_ctx *c, int side) {
     HB_CUDA(cudaStreamSynchronize(c->stream));
     free_buf(c, flag);
     HB_CUDA(cudaGetLastError());
-    if (too_long) return fail(HB_ERR_ARG, "a string compared by q-gram Jaccard has more than 8192 grams");
+    if (too_long) return fail(HB_ERR_ARG, "a string compared by Jaccard or containment has more than 8192 grams or tokens");
     if (c->batch_layout && side == 0) {
         // the job id is one more equality key held by every MD: blocks never span jobs
         const int n_jobs = (int)c->job_rows.size() - 1;
@@ -1121,6 +1318,10 @@ EvalParams make_params(hb_ctx *c, const uint32_t *rec_r, const uint32_t *rec_s, 
         for (int j = 0; j < (int)c->md_preds.size() && filterable; j++) {
             if (!(base & (1ull << j))) continue;
             const int f = P.first_op[j];
+            if (f < 0 || c->ops[f].hot == 255) {   // no staged filter operand: no phase-1 filter
+                filterable = false;
+                break;
+            }
             bool seen = false;
             for (int i = 0; i < nb; i++) seen |= P.base_op[m][i] == f;
             if (seen) continue;
@@ -1165,7 +1366,7 @@ EvalParams make_params(hb_ctx *c, const uint32_t *rec_r, const uint32_t *rec_s, 
         if (G.kind == OP_ED) {
             P.ptr_r[k] = c->side[0].cols[G.col_t].bytes;
             P.ptr_s[k] = self ? c->side[0].cols[G.col_t].bytes : c->side[side_s].cols[G.col_s].bytes;
-        } else if (G.kind == OP_JAC) {
+        } else if (G.kind == OP_JAC) {   // q-gram or word-token code lists (Jaccard, containment)
             P.ptr_r[k] = c->side[0].grams[pi.group];
             P.ptr_s[k] = self ? c->side[0].grams[pi.group] : c->side[side_s].grams[pi.group];
         }

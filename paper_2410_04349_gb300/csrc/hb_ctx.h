@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <deque>
 #include <vector>
 
 #include "hb_internal.h"
@@ -42,9 +43,11 @@ struct EqKey {
     int col_t, col_s, prefix;   // prefix < 0: whole value
 };
 struct FeatGroup {
-    int kind;   // OP_ED, OP_JAC, OP_ABS
+    int kind;   // OP_ED, OP_JAC, OP_ABS, OP_EQX, OP_CONST, OP_CONT (uses the OP_JAC groups)
     int col_t, col_s, q;
     int word;
+    int tokens = 0;   // OP_JAC: 1 = word-token codes instead of q-grams
+    int pred = -1;    // OP_CONST: the predicate whose constant the flag word tests
 };
 struct PredInfo {
     hb_predicate p;
@@ -89,6 +92,8 @@ struct hb_ctx {
     SideData side[2];
     // rules
     std::vector<std::vector<hb_predicate>> md_raw;
+    std::deque<std::string> consts;   // constants of CONST_EQ predicates (md_raw points here)
+    int n_user_mds = 0;               // MDs added; md_preds also holds transposed copies (self-join)
     // plan
     bool planned = false;
     bool batch_layout = false;   // extra job key
@@ -111,6 +116,14 @@ struct hb_ctx {
     // R-side dictionaries (kept for probing S)
     std::vector<uint64_t *> dict;
     std::vector<uint64_t> dict_cap;
+    // word-token dictionaries of R's token groups (kept to probe S's tokens)
+    struct TokDict {
+        uint64_t *table = nullptr;
+        uint64_t cap = 0;
+        uint32_t *start = nullptr, *len = nullptr;
+        const uint8_t *bytes = nullptr;
+    };
+    std::vector<TokDict> tok;
     // work buffers
     Buf w_slot_r, w_slot_s, w_count_s, w_start_s, w_cursor, w_members_r,
         w_members_s, w_blocks, w_tiles, w_prefix, w_scan, w_out, w_alt, w_sort, w_pairs, w_counters, w_lut, w_log,

@@ -51,7 +51,14 @@ struct DevCol {
 };
 
 // ---- evaluation program (Section 5.1: sequential execution path) ----
-enum OpKind : uint8_t { OP_ED = 0, OP_JAC = 1, OP_ABS = 2 };
+enum OpKind : uint8_t {
+    OP_ED = 0,     // edit distance <= k
+    OP_JAC = 1,    // Jaccard of q-gram or word-token code sets >= num/den
+    OP_ABS = 2,    // |a - b| <= delta
+    OP_EQX = 3,    // equality of two columns' codes (one dictionary): a[feat] == b[k]
+    OP_CONST = 4,  // t.A = c (num 0: a[feat]) or s.A = c (num 1: b[feat]): the tuple's flag word
+    OP_CONT = 5    // containment: |A n B| * den >= num * |side k's set| over a q-gram group
+};
 
 struct Op {
     uint8_t kind;
@@ -157,6 +164,21 @@ void code_feature(const uint32_t *codes, int64_t n, uint32_t *rec, int W, int fe
 void hot_pack(const uint32_t *rec, int W, int64_t n, uint32_t *hot, int HW, const int32_t *map, cudaStream_t s);
 void ed_features(const DevCol &c, uint32_t *rec, int W, int feat, cudaStream_t s);
 void abs_feature(const DevCol &c, uint32_t *rec, int W, int feat, cudaStream_t s);
+// one word per row: 1 when the row's value equals the constant (device bytes; int32 little-endian)
+void const_feature(const DevCol &c, const uint8_t *cval_dev, uint32_t clen, uint32_t *rec, int W, int feat,
+                   cudaStream_t s);
+// word tokens (maximal runs of bytes other than 0x20): toff[n+1] exclusive starts; returns the total
+size_t tok_scratch_bytes(int64_t n);
+int64_t tok_count(const DevCol &c, uint32_t *toff, void *scratch, size_t scratch_bytes, cudaStream_t s);
+void tok_fill(const DevCol &c, const uint32_t *toff, uint32_t *tstart, uint32_t *tlen, cudaStream_t s);
+void tok_insert(const uint8_t *bytes, const uint32_t *tstart, const uint32_t *tlen, int64_t T, uint64_t *table,
+                uint64_t cap, uint32_t *codes, cudaStream_t s);
+void tok_probe(const uint8_t *bytes, const uint32_t *tstart, const uint32_t *tlen, int64_t T, const uint8_t *obytes,
+               const uint32_t *ostart, const uint32_t *olen, const uint64_t *table, uint64_t cap, uint32_t *codes,
+               cudaStream_t s);
+// per string: local codes for tokens absent from the owner, sort, unique, Jaccard feature words
+void tok_lists(const DevCol &c, const uint32_t *toff, const uint32_t *tstart, const uint32_t *tlen, uint32_t *codes,
+               uint32_t *rec, int W, int feat, unsigned int *too_long, cudaStream_t s);
 size_t jac_scratch_bytes(int64_t n);
 // grams: capacity >= the column's byte count; too_long: device flag set for strings of > 8192 grams
 void jac_features_impl(const DevCol &c, int q, uint32_t *rec, int W, int feat, uint32_t *grams, void *scratch,

@@ -151,10 +151,14 @@ hb_status predicate_features(hb_ctx *c, std::vector<float> &F) {
     for (int p = 0; p < P; p++) {
         float *f = &F[(size_t)p * HB_FEATURES];
         const hb_predicate &q = c->preds[p].p;
-        f[q.kind] = 1.f;
+        // kind one-hot over the five basic kinds: a constant reads like an equality, containment and
+        // word-token Jaccard like q-gram Jaccard
+        const int kslot = q.kind == HB_P_CONST_EQ ? HB_P_EQ
+                          : (q.kind == HB_P_CONTAIN_GE || q.kind == HB_P_TOKEN_JACCARD_GE) ? HB_P_JACCARD_GE : q.kind;
+        f[kslot] = 1.f;
         if (q.kind == HB_P_ED_LE) f[5] = q.k / 8.f;
         if (q.kind == HB_P_EQ_PREFIX) f[5] = q.k / 8.f;
-        if (q.kind == HB_P_JACCARD_GE) {
+        if (q.kind == HB_P_JACCARD_GE || q.kind == HB_P_CONTAIN_GE || q.kind == HB_P_TOKEN_JACCARD_GE) {
             f[6] = (float)q.num / (float)q.den;
             f[7] = q.q / 4.f;
         }

@@ -172,6 +172,10 @@ extern "C" hb_status hb_block_stream(hb_ctx *c, int64_t n_rows_s, int32_t n_cols
     }
     c->side[1].n = 0;
     if (!c->planned || c->batch_layout) HB_TRY(do_plan(c, HB_PLAN_RULE_DATA, false));
+    for (const FeatGroup &G : c->groups)
+        if (G.kind == OP_CONST || G.tokens)
+            return fail(HB_ERR_ARG, "hb_block_stream: constants and word-token Jaccard are not supported when S is "
+                                    "streamed (load S with hb_load_table and call hb_block)");
     HB_TRY(encode_side(c, 0));
     HB_TRY(grow(c, c->w_counters, 64 * sizeof(unsigned long long)));
     if (!c->lut.empty()) {

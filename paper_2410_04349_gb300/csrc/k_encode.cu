@@ -520,6 +520,174 @@ __global__ void k_hot_pack(const uint32_t *rec, int W, int64_t n, uint32_t *hot,
     for (int h = 0; h < HW; h++) hot[i * HW + h] = map.w[h] >= 0 ? rec[i * W + map.w[h]] : 0u;
 }
 
+// ---- constants: one flag word per (column, constant) ----
+__global__ void k_const_flag(View v, int64_t n, const uint8_t *cval, uint32_t clen, uint32_t *rec, int W, int feat) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint32_t f = 0;
+    if (!v.valid || v.valid[i]) {
+        if (v.type == HB_COL_STRING) {
+            const uint8_t *p;
+            uint32_t len;
+            view_str(v, i, p, len);
+            f = len == clen ? 1u : 0u;
+            for (uint32_t k = 0; k < len && f; k++) f = p[k] == cval[k] ? 1u : 0u;
+        } else {
+            int32_t want = (int32_t)((uint32_t)cval[0] | ((uint32_t)cval[1] << 8) | ((uint32_t)cval[2] << 16) |
+                                     ((uint32_t)cval[3] << 24));
+            f = v.i32[i] == want ? 1u : 0u;
+        }
+    }
+    rec[i * W + feat] = f;
+}
+
+// ---- word tokens: the maximal runs of bytes other than the space 0x20 ----
+__global__ void k_tok_count(const uint8_t *bytes, const uint32_t *off, const uint8_t *valid, int64_t n,
+                            uint32_t *cnt) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint32_t t = 0;
+    if (!valid || valid[i]) {
+        bool in = false;
+        for (uint32_t k = off[i]; k < off[i + 1]; k++) {
+            const bool word = bytes[k] != 0x20;
+            t += (word && !in) ? 1u : 0u;
+            in = word;
+        }
+    }
+    cnt[i] = t;
+}
+
+__global__ void k_tok_fill(const uint8_t *bytes, const uint32_t *off, const uint8_t *valid, int64_t n,
+                           const uint32_t *toff, uint32_t *tstart, uint32_t *tlen) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || (valid && !valid[i])) return;
+    uint32_t t = toff[i], k = off[i];
+    const uint32_t e = off[i + 1];
+    while (k < e) {
+        while (k < e && bytes[k] == 0x20) k++;
+        const uint32_t a = k;
+        while (k < e && bytes[k] != 0x20) k++;
+        if (k > a) {
+            tstart[t] = a;
+            tlen[t] = k - a;
+            t++;
+        }
+    }
+}
+
+struct TokView {
+    const uint8_t *bytes;
+    const uint32_t *start, *len;
+};
+
+__device__ __forceinline__ bool tok_equal(const TokView &a, int64_t i, const TokView &b, int64_t j) {
+    const uint32_t la = a.len[i];
+    if (la != b.len[j]) return false;
+    const uint8_t *p = a.bytes + a.start[i], *q = b.bytes + b.start[j];
+    for (uint32_t k = 0; k < la; k++)
+        if (p[k] != q[k]) return false;
+    return true;
+}
+
+// exact token dictionary: slots hold (32-bit hash << 32 | representative token);
+// a token's code is its slot (byte-exact comparison on equal hashes)
+__global__ void k_tok_insert(TokView v, int64_t T, uint64_t *table, uint64_t mask, uint32_t *codes) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= T) return;
+    const uint64_t h = hash_bytes(v.bytes + v.start[t], v.len[t]);
+    const uint32_t h32 = (uint32_t)(h >> 32);
+    const uint64_t mine = ((uint64_t)h32 << 32) | (uint64_t)(uint32_t)t;
+    uint64_t slot = h & mask;
+    for (uint64_t probe = 0; probe <= mask; probe++) {
+        uint64_t cur = table[slot];
+        if (cur == EMPTY_SLOT) {
+            const uint64_t prev = atomicCAS(reinterpret_cast<unsigned long long *>(table + slot),
+                                            (unsigned long long)EMPTY_SLOT, (unsigned long long)mine);
+            if (prev == EMPTY_SLOT) {
+                codes[t] = (uint32_t)slot;
+                return;
+            }
+            cur = prev;
+        }
+        if ((uint32_t)(cur >> 32) == h32 && tok_equal(v, t, v, (int64_t)(uint32_t)cur)) {
+            codes[t] = (uint32_t)slot;
+            return;
+        }
+        slot = (slot + 1) & mask;
+    }
+    codes[t] = NOMATCH_CODE;   // unreachable: the table has at least twice as many slots as tokens
+}
+
+// the other relation's tokens: the slot of an equal token of the owner, or NOMATCH
+__global__ void k_tok_probe(TokView v, int64_t T, TokView owner, const uint64_t *table, uint64_t mask,
+                            uint32_t *codes) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= T) return;
+    const uint64_t h = hash_bytes(v.bytes + v.start[t], v.len[t]);
+    const uint32_t h32 = (uint32_t)(h >> 32);
+    uint64_t slot = h & mask;
+    for (uint64_t probe = 0; probe <= mask; probe++) {
+        const uint64_t cur = table[slot];
+        if (cur == EMPTY_SLOT) break;
+        if ((uint32_t)(cur >> 32) == h32 && tok_equal(v, t, owner, (int64_t)(uint32_t)cur)) {
+            codes[t] = (uint32_t)slot;
+            return;
+        }
+        slot = (slot + 1) & mask;
+    }
+    codes[t] = NOMATCH_CODE;
+}
+
+// Per string: tokens that no owner token equals get codes local to the string
+// (0x80000000 | position of the string's first equal token: such tokens meet
+// no token of the other relation, so only their identity within the string
+// matters), then the codes are sorted, made unique and summarised like q-grams.
+__global__ void k_tok_lists(const uint8_t *bytes, const uint8_t *valid, int64_t n, const uint32_t *toff,
+                            const uint32_t *tstart, const uint32_t *tlen, uint32_t *codes, uint32_t *rec, int W,
+                            int feat, unsigned int *too_long) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint32_t *r = rec + i * W + feat;
+    if (valid && !valid[i]) {
+        r[0] = NULL_LEN;
+        r[1] = 0;
+        for (int k = 2; k < FEAT_JAC_WORDS; k++) r[k] = 0;
+        return;
+    }
+    const uint32_t a = toff[i], b = toff[i + 1];
+    if (b - a > 8192u) {
+        atomicExch(too_long, 1u);
+        r[0] = NULL_LEN;
+        r[1] = 0;
+        return;
+    }
+    TokView v{bytes, tstart, tlen};
+    for (uint32_t t = a; t < b; t++) {
+        if (codes[t] != NOMATCH_CODE) continue;
+        uint32_t code = 0x80000000u | (t - a);
+        for (uint32_t u = a; u < t; u++)
+            if (codes[u] >= 0x80000000u && codes[u] != NOMATCH_CODE && tok_equal(v, t, v, u)) {
+                code = codes[u];
+                break;
+            }
+        codes[t] = code;
+    }
+    for (uint32_t t = a + 1; t < b; t++) {   // insertion sort (a string holds few tokens)
+        const uint32_t x = codes[t];
+        uint32_t u = t;
+        while (u > a && codes[u - 1] > x) {
+            codes[u] = codes[u - 1];
+            u--;
+        }
+        codes[u] = x;
+    }
+    uint32_t m = a;
+    for (uint32_t t = a; t < b; t++)
+        if (t == a || codes[t] != codes[m - 1]) codes[m++] = codes[t];
+    write_gram_feature(r, m - a, a, codes + a);
+}
+
 inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t > 0 ? (n + t - 1) / t : 1); }
 
 }  // namespace
@@ -558,6 +726,62 @@ void ed_features(const DevCol &c, uint32_t *rec, int W, int feat, cudaStream_t s
     if (c.n == 0) return;
     HB_LAUNCHED(1);
     k_ed_features<<<blocks_for(c.n, ENC_THREADS), ENC_THREADS, 0, s>>>(c.bytes, c.off, c.valid, c.n, rec, W, feat);
+}
+
+void const_feature(const DevCol &c, const uint8_t *cval_dev, uint32_t clen, uint32_t *rec, int W, int feat,
+                   cudaStream_t s) {
+    if (c.n == 0) return;
+    HB_LAUNCHED(1);
+    k_const_flag<<<blocks_for(c.n, ENC_THREADS), ENC_THREADS, 0, s>>>(make_view(c, -1), c.n, cval_dev, clen, rec, W,
+                                                                     feat);
+}
+
+size_t tok_scratch_bytes(int64_t n) { return (size_t)(n + 1) * 4 + scan_tmp_bytes(n + 1) + 4096; }
+
+int64_t tok_count(const DevCol &c, uint32_t *toff, void *scratch, size_t scratch_bytes, cudaStream_t s) {
+    if (c.n == 0) return 0;
+    uint32_t *cnt = static_cast<uint32_t *>(scratch);
+    void *tmp = static_cast<char *>(scratch) + (((size_t)(c.n + 1) * 4 + 255) & ~(size_t)255);
+    HB_LAUNCHED(1);
+    k_tok_count<<<blocks_for(c.n, ENC_THREADS), ENC_THREADS, 0, s>>>(c.bytes, c.off, c.valid, c.n, cnt);
+    cudaMemsetAsync(cnt + c.n, 0, 4, s);
+    scan_exclusive_u32(cnt, toff, c.n + 1, nullptr, tmp, scratch_bytes - (((size_t)(c.n + 1) * 4 + 255) & ~(size_t)255), s);
+    uint32_t total = 0;
+    cudaMemcpyAsync(&total, toff + c.n, 4, cudaMemcpyDeviceToHost, s);
+    cudaStreamSynchronize(s);
+    return (int64_t)total;
+}
+
+void tok_fill(const DevCol &c, const uint32_t *toff, uint32_t *tstart, uint32_t *tlen, cudaStream_t s) {
+    if (c.n == 0) return;
+    HB_LAUNCHED(1);
+    k_tok_fill<<<blocks_for(c.n, ENC_THREADS), ENC_THREADS, 0, s>>>(c.bytes, c.off, c.valid, c.n, toff, tstart, tlen);
+}
+
+void tok_insert(const uint8_t *bytes, const uint32_t *tstart, const uint32_t *tlen, int64_t T, uint64_t *table,
+                uint64_t cap, uint32_t *codes, cudaStream_t s) {
+    cudaMemsetAsync(table, 0xFF, cap * sizeof(uint64_t), s);
+    if (T == 0) return;
+    HB_LAUNCHED(1);
+    k_tok_insert<<<blocks_for(T, ENC_THREADS), ENC_THREADS, 0, s>>>(TokView{bytes, tstart, tlen}, T, table, cap - 1,
+                                                                   codes);
+}
+
+void tok_probe(const uint8_t *bytes, const uint32_t *tstart, const uint32_t *tlen, int64_t T, const uint8_t *obytes,
+               const uint32_t *ostart, const uint32_t *olen, const uint64_t *table, uint64_t cap, uint32_t *codes,
+               cudaStream_t s) {
+    if (T == 0) return;
+    HB_LAUNCHED(1);
+    k_tok_probe<<<blocks_for(T, ENC_THREADS), ENC_THREADS, 0, s>>>(TokView{bytes, tstart, tlen}, T,
+                                                                  TokView{obytes, ostart, olen}, table, cap - 1, codes);
+}
+
+void tok_lists(const DevCol &c, const uint32_t *toff, const uint32_t *tstart, const uint32_t *tlen, uint32_t *codes,
+               uint32_t *rec, int W, int feat, unsigned int *too_long, cudaStream_t s) {
+    if (c.n == 0) return;
+    HB_LAUNCHED(1);
+    k_tok_lists<<<blocks_for(c.n, 128), 128, 0, s>>>(c.bytes, c.valid, c.n, toff, tstart, tlen, codes, rec, W, feat,
+                                                    too_long);
 }
 
 void abs_feature(const DevCol &c, uint32_t *rec, int W, int feat, cudaStream_t s) {

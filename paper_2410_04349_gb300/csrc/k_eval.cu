@@ -227,9 +227,53 @@ __device__ __forceinline__ bool eval_op(const EvalParams &P, int k, const uint32
         if (LOG) log_add(lg, k * LOG_FIELDS + 5, rows * (2u * op.k + 1u));
         return r;
     }
-    // OP_JAC
+    if (op.kind == OP_EQX) {   // two columns' codes in one dictionary; a missing or unmatched code equals nothing
+        const uint32_t x = __ldg(a + f), y = __ldg(b + op.k);
+        return x < NOMATCH_CODE && x == y;
+    }
+    if (op.kind == OP_CONST) return __ldg((op.num ? b : a) + f) != 0u;   // the named tuple's flag word
     const uint32_t na = __ldg(a + f), nb = __ldg(b + f);
     if (na == NULL_LEN || nb == NULL_LEN) return false;
+    if (op.kind == OP_CONT) {
+        // containment: |A n B| * den >= num * |D|, D the set of side k (0: a's, 1: b's); the
+        // size, presence-mask and gram-bin bounds of |A n B| first, then an early-exit merge
+        const uint64_t den = op.den;
+        const uint64_t need = (uint64_t)op.num * (op.k ? nb : na);
+        if ((uint64_t)min(na, nb) * den < need) return false;
+        if (LOG) log_add(lg, k * LOG_FIELDS + 3, 1u);
+        {
+            const uint64_t ma = (uint64_t)__ldg(a + f + FEAT_JAC_MASK) | ((uint64_t)__ldg(a + f + FEAT_JAC_MASK + 1) << 32);
+            const uint64_t mb = (uint64_t)__ldg(b + f + FEAT_JAC_MASK) | ((uint64_t)__ldg(b + f + FEAT_JAC_MASK + 1) << 32);
+            if ((uint64_t)mask_common_ub(na, ma, nb, mb) * den < need) return false;
+        }
+        if (na <= 255u && nb <= 255u) {
+            unsigned ub = 0;
+#pragma unroll
+            for (int w = 0; w < 8; w++) ub = __dp4a(__vminu4(__ldg(a + f + 2 + w), __ldg(b + f + 2 + w)), 0x01010101u, ub);
+            if ((uint64_t)ub * den < need) return false;
+        }
+        if (LOG) log_add(lg, k * LOG_FIELDS + 4, 1u);
+        const uint64_t imin = (need + den - 1) / den;
+        if (imin == 0) return true;
+        const uint32_t *A = static_cast<const uint32_t *>(P.ptr_r[k]) + __ldg(a + f + 1);
+        const uint32_t *B = static_cast<const uint32_t *>(P.ptr_s[k]) + __ldg(b + f + 1);
+        uint32_t i = 0, j = 0, I = 0;
+        bool res = false;
+        while (i < na && j < nb) {
+            const uint32_t x = __ldg(A + i), y = __ldg(B + j);
+            I += (x == y) ? 1u : 0u;
+            i += (x <= y) ? 1u : 0u;
+            j += (y <= x) ? 1u : 0u;
+            if (I >= imin) {
+                res = true;
+                break;
+            }
+            if ((uint64_t)I + min(na - i, nb - j) < imin) break;
+        }
+        if (LOG) log_add(lg, k * LOG_FIELDS + 5, i + j);
+        return res;
+    }
+    // OP_JAC (q-gram or word-token code sets)
     const uint64_t num = op.num, den = op.den;
     const uint32_t mn = min(na, nb), mx = max(na, nb);
     if ((uint64_t)mn * den < num * mx) return false;   // J <= min/max

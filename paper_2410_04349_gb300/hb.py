@@ -10,8 +10,10 @@ Columns are passed as objects with attributes ``type`` ("string", "int32",
 uint32) and ``valid`` (uint8 per row or None).  Tensors on a CUDA device are
 passed as device pointers (``on_device=True``).
 
-Predicates are tuples ``(kind, col_t, col_s, k, q, num, den, delta)`` with
-kind in {"eq", "eq_prefix", "ed", "jaccard", "absdiff"}.
+Predicates are tuples ``(kind, col_t, col_s, k, q, num, den, delta[, side[, value]])``
+with kind in {"eq", "eq_prefix", "ed", "jaccard", "absdiff", "const_eq", "contain",
+"tjaccard"}; side and value carry a constant's side and bytes (or int) and a
+containment's dividing side.
 """
 from __future__ import annotations
 
@@ -24,7 +26,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libhb.so")
 
 HB_OK, HB_ERR_ARG, HB_ERR_OOM, HB_ERR_CUDA, HB_ERR_STATE, HB_ERR_OVERFLOW, HB_ERR_DEVICE_TIMEOUT = 0, -1, -2, -3, -4, -5, -6
-KINDS = {"eq": 0, "eq_prefix": 1, "ed": 2, "jaccard": 3, "absdiff": 4}
+KINDS = {"eq": 0, "eq_prefix": 1, "ed": 2, "jaccard": 3, "absdiff": 4, "const_eq": 5, "contain": 6, "tjaccard": 7}
 TYPES = {"string": 0, "int32": 1, "fp32": 2}
 FLAG_PER_JOB_LAUNCHES, FLAG_NO_GRAPH = 1, 2
 PLAN_MODES = {"rule_data": 0, "learned": 1, "given": 2, "random": 3, "cost_first": 4, "sel_first": 5}
@@ -46,7 +48,8 @@ class hb_column(ctypes.Structure):
 class hb_predicate(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("col_t", ctypes.c_int32), ("col_s", ctypes.c_int32),
                 ("k", ctypes.c_int32), ("q", ctypes.c_int32), ("num", ctypes.c_uint32), ("den", ctypes.c_uint32),
-                ("delta", ctypes.c_float)]
+                ("delta", ctypes.c_float), ("side", ctypes.c_int32), ("value_len", ctypes.c_uint32),
+                ("value", ctypes.c_void_p)]
 
 
 class hb_pair(ctypes.Structure):
@@ -215,10 +218,24 @@ def pin_columns(columns):
 
 
 def _preds(md):
+    """The C predicates of one MD; a constant's bytes (a string's, or an int32's
+    little-endian 4) stay referenced by the returned array while hb_add_md
+    copies them."""
     arr = (hb_predicate * len(md))()
+    keep = []
     for i, p in enumerate(md):
-        kind, ct, cs, k, q, num, den, delta = p
-        arr[i] = hb_predicate(KINDS[kind], ct, cs, k, q, num, den, delta)
+        kind, ct, cs, k, q, num, den, delta = p[:8]
+        side = p[8] if len(p) > 8 else 0
+        arr[i] = hb_predicate(KINDS[kind], ct, cs, k, q, num, den, delta, side, 0, None)
+        if kind == "const_eq":
+            v = p[9]
+            b = (v.encode() if isinstance(v, str) else bytes(v)) if isinstance(v, (str, bytes, bytearray)) \
+                else np.array([v], np.int32).tobytes()
+            buf = ctypes.create_string_buffer(b, max(len(b), 1))
+            keep.append(buf)
+            arr[i].value = ctypes.cast(buf, ctypes.c_void_p)
+            arr[i].value_len = len(b)
+    arr._keep = keep
     return arr
 
 

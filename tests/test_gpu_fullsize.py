@@ -124,12 +124,13 @@ def _subset_pairs(pairs, rows):
     return out[np.lexsort((out[:, 1], out[:, 0]))]
 
 
-def test_config5_full_size_exact_on_the_subset_and_every_plan_equal():
+def test_config5_full_size_exact_on_the_subset_and_learned_given_rule_data_plans_equal():
     g = _golden("c5")
     t, mds = synth.config5()
     assert table_sha256(t) == g["input_sha256"], "input generation differs on this machine"
     rows = c5_subset(t.n_rows)
     assert len(rows) == g["subset_rows"]
+    from gpu_helpers import committed_model
     with hb.Context(device=0) as ctx:
         ctx.load_table(0, t.n_rows, t.columns)
         for md in mds:
@@ -139,7 +140,12 @@ def test_config5_full_size_exact_on_the_subset_and_every_plan_equal():
         st = ctx.stats()
         ctx.plan("given")
         again = ctx.block()
+        ctx.set_cost_model(committed_model())
+        info = ctx.plan("learned")
+        assert info.mode == 1   # the learned plan is applied, not the rule-data fallback
+        learned = ctx.block()
     assert st["candidate_pairs"] == g["candidates"]
     assert np.array_equal(pairs, again)
+    assert np.array_equal(pairs, learned)
     sub = _subset_pairs(pairs, rows)
     assert len(sub) == g["n_pairs"] and pairs_sha256(sub) == g["pairs_sha256"]

@@ -9,7 +9,7 @@ import oracle
 import synth
 from synth import absdiff, ed, eq, eq_prefix, jac
 
-from gpu_helpers import as_set, run_gpu
+from gpu_helpers import committed_model, as_set, run_gpu
 
 pytestmark = pytest.mark.gpu
 
@@ -55,9 +55,12 @@ def test_paper_table1_fixture():
 @pytest.mark.parametrize("mode", ["rule_data", "given", "random", "cost_first", "sel_first", "learned"])
 def test_every_plan_mode_gives_the_same_set(mode):
     t, mds = synth.config2(n=30000, cards=(30, 300, 3000))
-    got, _, info = run_gpu(t, mds, mode=mode)
+    model = committed_model() if mode == "learned" else None
+    got, _, info = run_gpu(t, mds, mode=mode, model=model)
     want, _ = oracle.block_hash(t, mds)
     assert np.array_equal(got, want)
+    if mode == "learned":
+        assert info.mode == 1   # the committed model was applied, not the rule-data fallback
 
 
 def test_r_x_s_small():
