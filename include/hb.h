@@ -355,6 +355,66 @@ HB_API hb_status hb_adam_step(float *params, const float *grad, float *m, float 
                        float lr, float beta1, float beta2, float eps, void *stream);
 
 /*
+ * Tile shape chosen by a learned model (batched form).  hb_block_batch's
+ * autotuner times every candidate shape (tuples per tile side 32 or 64 x 1, 2,
+ * 4 or 8 tiles per claim) the first time it meets a job-size signature and
+ * logs each measurement (HB_FEATURES features of the signature and the shape,
+ * log of the milliseconds).  hb_tile_log copies the logged rows out (up to cap;
+ * *n_out receives the total); hb_train_tile_model trains a 32-64-64-1 network
+ * on such rows (as hb_train_cost_model) and makes it the context's tile model;
+ * hb_set_tile_model installs one (NULL removes it), hb_get_tile_model copies it
+ * out (HB_MLP_PARAMS floats).  With a tile model, a new signature takes the
+ * shape of smallest predicted time without trial runs; without one, or when a
+ * prediction is not finite, the autotuner measures.  hb_batch_tile reports the
+ * shape of the last batch and whether the model chose it (learned = 1).
+ */
+HB_API hb_status hb_tile_log(hb_ctx *ctx, int32_t cap, float *X_out, float *y_out, int32_t *n_out);
+HB_API hb_status hb_train_tile_model(hb_ctx *ctx, int32_t n, const float *X, const float *y, int32_t epochs, float lr,
+                                     uint64_t seed, float *loss_out);
+HB_API hb_status hb_set_tile_model(hb_ctx *ctx, const float *params);
+HB_API hb_status hb_get_tile_model(hb_ctx *ctx, float *params_out);
+HB_API hb_status hb_batch_tile(const hb_ctx *ctx, int32_t *tile, int32_t *claim, int32_t *learned);
+
+/* ---------------- the paper's per-pair cost model N ----------------
+ * Section 4.2 ("Shallow NNs") trains a small network N(p, t1, t2) on logged
+ * times of checking p on tuple pairs; cost(p, D) is then estimated as
+ * norm(sum of N over sampled pairs).  Section 6's defaults give hidden layers
+ * of 2, 6 and 1 neurons; here N maps HB_PAIR_FEATURES features to one output
+ * through layers of 2 and 6 ReLU units (the last neuron is the output).
+ * Features of (p, t1, t2): kind one-hot (edit distance, Jaccard, |a-b|),
+ * threshold (k/8, num/den or log1p(delta)), s(o1), s(o2), s(|o1 - o2|) and
+ * min/max of |o1|, |o2|, where o is the tuple's operand (string length,
+ * distinct q-gram count, or value), s(v) = v/64 for lengths and counts and
+ * log1p(|v|)/8 for values; a missing operand sets the last four to -1.
+ */
+#define HB_PAIR_FEATURES 8
+#define HB_PAIR_MODEL_PARAMS (8 * 2 + 2 + 2 * 6 + 6 + 6 + 1)   /* W1 b1 W2 b2 W3 b3, row-major */
+
+/*
+ * Check distinct predicate `pred` (an edit-distance, Jaccard or |a-b|
+ * predicate of the current plan's program) on n given pairs (host arrays i[],
+ * j[]: rows of R and of S, or of R twice in a self-join), one thread per pair,
+ * and write per pair the clock64 cycles of the check (cycles_out), its
+ * verdict (verdict_out, 0/1) and N's features (features_out, n x
+ * HB_PAIR_FEATURES floats).  All outputs are host arrays.  HB_ERR_ARG for an
+ * unknown or unsupported predicate or a row out of range.
+ */
+HB_API hb_status hb_time_pairs(hb_ctx *ctx, int32_t pred, int32_t n, const uint32_t *i, const uint32_t *j,
+                               uint32_t *cycles_out, uint8_t *verdict_out, float *features_out);
+/* N's forward pass and the gradient of mean((y - t)^2) (device pointers; grad overwritten). */
+HB_API hb_status hb_pair_model_forward(const float *X, int32_t n, const float *params, float *y, void *stream);
+HB_API hb_status hb_pair_model_backward(const float *X, const float *t, int32_t n, const float *params, float *grad,
+                                        void *stream);
+/*
+ * Train N on the GPU (full-batch Adam, lr, `epochs` steps, He-uniform start
+ * from `seed`) on n rows (host arrays X [n x HB_PAIR_FEATURES], y [n]); writes
+ * the trained parameters (params_out, HB_PAIR_MODEL_PARAMS floats, host) and
+ * the final mean squared error (loss_out, optional).
+ */
+HB_API hb_status hb_train_pair_model(int32_t n, const float *X, const float *y, int32_t epochs, float lr,
+                                     uint64_t seed, float *params_out, float *loss_out);
+
+/*
  * Measurement aid (no counterpart in the paper): the integer issue rate of the
  * current device.  Launches 8 resident 256-thread blocks per SM whose threads
  * run 8 independent chains of three integer instructions (three-input add,

@@ -11,9 +11,11 @@ layers of 64 and one linear output:
     loss = mean((y - t)^2)
 
 Backward is the chain rule written out layer by layer; Adam follows Kingma &
-Ba (2015), Algorithm 1, with bias correction.  ``forward_bf16`` rounds the
-inputs, weights and the hidden activations to bfloat16 (round to nearest
-even) exactly where the GPU inference kernel does, and sums in fp64.
+Ba (2015), Algorithm 1, with bias correction.  ``forward_bf16`` is bf16
+inference as this build specifies it: the inputs, the weights and each hidden
+activation are rounded to bfloat16 (round to nearest even), the biases are
+binary32, and products and sums are exact (fp64 here, at least fp32 on the
+GPU); the output is not rounded.
 
 Pinned in tests/test_oracle_mlp.py by closed forms (a network that sums its
 inputs, a dead-ReLU network), central finite differences of the forward

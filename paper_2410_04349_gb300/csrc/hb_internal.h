@@ -207,6 +207,13 @@ void clamp_blocks(uint32_t *n_blocks, uint32_t block_cap, cudaStream_t s);
 // k_eval.cu
 size_t eval_smem_bytes(int W, int n_eq, int use_lut, int tile);
 int eval_blocks_per_sm(int tile, int logging, size_t smem);
+// the paper's per-pair model N, 8 -> 2 -> 6 -> 1 (k_mlp.cu)
+cudaError_t pair_model_forward(const float *X, int n, const float *params, float *y, cudaStream_t s);
+cudaError_t pair_model_backward(const float *X, const float *t, int n, const float *params, float *grad,
+                                cudaStream_t s);
+// per-pair cycles, verdict and the paper's per-pair model features of program op k (k_eval.cu)
+cudaError_t launch_pair_times(const EvalParams &p, int k, const uint32_t *pi, const uint32_t *pj, int n,
+                              uint32_t *cycles, uint8_t *verdict, float *X, cudaStream_t s);
 cudaError_t launch_eval(const EvalParams &p, int grid, size_t smem, int logging, cudaStream_t s);
 void pack_pairs(const uint64_t *keys, int64_t n, int key_bits_s, hb_pair *out, cudaStream_t s);
 

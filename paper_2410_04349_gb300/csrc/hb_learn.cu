@@ -429,3 +429,144 @@ extern "C" hb_status hb_train_cost_model(hb_ctx *c, int32_t n, const float *X, c
     return HB_OK;
 }
 
+
+// ---------------------------------------------------------------------------
+// The paper's per-pair cost model N: per-pair timing logs, kernels and trainer
+// ---------------------------------------------------------------------------
+extern "C" hb_status hb_time_pairs(hb_ctx *c, int32_t pred, int32_t n, const uint32_t *pi, const uint32_t *pj,
+                                   uint32_t *cycles_out, uint8_t *verdict_out, float *features_out) {
+    if (!c || n < 0 || (n > 0 && (!pi || !pj || !cycles_out || !verdict_out || !features_out)))
+        return fail(HB_ERR_ARG, "hb_time_pairs: bad arguments");
+    cudaSetDevice(c->device);
+    HB_TRY(ensure_ready(c, false));
+    int k = -1;
+    for (size_t q = 0; q < c->program.size(); q++)
+        if (c->program[q] == pred) k = (int)q;
+    if (k < 0) return fail(HB_ERR_ARG, "hb_time_pairs: pred is not a non-equality predicate of the plan's program");
+    const int kind = c->ops[k].kind;
+    if (kind != OP_ED && kind != OP_JAC && kind != OP_ABS)
+        return fail(HB_ERR_ARG, "hb_time_pairs: the per-pair model covers edit distance, Jaccard and |a-b|");
+    const bool self = is_self(c);
+    const int64_t nr = c->side[0].n, ns = self ? nr : c->side[1].n;
+    for (int32_t t = 0; t < n; t++)
+        if ((int64_t)pi[t] >= nr || (int64_t)pj[t] >= ns) return fail(HB_ERR_ARG, "hb_time_pairs: row out of range");
+    if (n == 0) return HB_OK;
+    Buf dev;
+    const size_t n8 = (size_t)n;
+    HB_TRY(grow(c, dev, n8 * (4 + 4 + 4 + 1 + 4 * HB_PAIR_FEATURES) + 256));
+    uint32_t *di = as<uint32_t>(dev), *dj = di + n8, *dc = dj + n8;
+    float *dX = reinterpret_cast<float *>(dc + n8);
+    uint8_t *dv = reinterpret_cast<uint8_t *>(dX + n8 * HB_PAIR_FEATURES);
+    HB_CUDA(cudaMemcpyAsync(di, pi, 4 * n8, cudaMemcpyHostToDevice, c->stream));
+    HB_CUDA(cudaMemcpyAsync(dj, pj, 4 * n8, cudaMemcpyHostToDevice, c->stream));
+    EvalParams P = make_params(c, c->side[0].rec, self ? c->side[0].rec : c->side[1].rec, 1, self,
+                               as<unsigned long long>(c->w_counters), 32);
+    HB_CUDA(launch_pair_times(P, k, di, dj, n, dc, dv, dX, c->stream));
+    HB_CUDA(cudaMemcpyAsync(cycles_out, dc, 4 * n8, cudaMemcpyDeviceToHost, c->stream));
+    HB_CUDA(cudaMemcpyAsync(verdict_out, dv, n8, cudaMemcpyDeviceToHost, c->stream));
+    HB_CUDA(cudaMemcpyAsync(features_out, dX, 4 * n8 * HB_PAIR_FEATURES, cudaMemcpyDeviceToHost, c->stream));
+    HB_CUDA(cudaStreamSynchronize(c->stream));
+    free_buf(c, dev);
+    return HB_OK;
+}
+
+extern "C" hb_status hb_pair_model_forward(const float *X, int32_t n, const float *params, float *y, void *stream) {
+    if (n < 0 || (n > 0 && (!X || !params || !y))) return fail(HB_ERR_ARG, "hb_pair_model_forward: bad arguments");
+    HB_CUDA(pair_model_forward(X, n, params, y, static_cast<cudaStream_t>(stream)));
+    return HB_OK;
+}
+
+extern "C" hb_status hb_pair_model_backward(const float *X, const float *t, int32_t n, const float *params,
+                                            float *grad, void *stream) {
+    if (n < 0 || !params || !grad || (n > 0 && (!X || !t)))
+        return fail(HB_ERR_ARG, "hb_pair_model_backward: bad arguments");
+    HB_CUDA(pair_model_backward(X, t, n, params, grad, static_cast<cudaStream_t>(stream)));
+    return HB_OK;
+}
+
+extern "C" hb_status hb_train_pair_model(int32_t n, const float *X, const float *y, int32_t epochs, float lr,
+                                         uint64_t seed, float *params_out, float *loss_out) {
+    if (n < 1 || !X || !y || !params_out || epochs < 0 || !(lr > 0.f))
+        return fail(HB_ERR_ARG, "hb_train_pair_model: bad arguments");
+    const int PN = HB_PAIR_MODEL_PARAMS;
+    // He-uniform start: fan-in 8 for W1, 2 for W2, 6 for W3; zero biases
+    std::vector<float> p0(PN, 0.f);
+    std::mt19937_64 rng(seed);
+    std::uniform_real_distribution<double> U(-1.0, 1.0);
+    const int fan[3] = {8, 2, 6}, off[3] = {0, 8 * 2 + 2, 8 * 2 + 2 + 2 * 6 + 6}, cnt[3] = {16, 12, 6};
+    for (int l = 0; l < 3; l++) {
+        const double lim = std::sqrt(6.0 / fan[l]);
+        for (int i = 0; i < cnt[l]; i++) p0[off[l] + i] = (float)(lim * U(rng));
+    }
+    cudaStream_t s = nullptr;
+    float *d = nullptr;
+    const size_t nf = (size_t)n * HB_PAIR_FEATURES;
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&d), sizeof(float) * (nf + 2 * (size_t)n + 4 * PN + 64), s);
+    if (e != cudaSuccess) return fail(HB_ERR_OOM, "hb_train_pair_model: device allocation failed");
+    float *dX = d, *dy = dX + nf, *dp = dy + n, *dg = dp + PN, *dm = dg + PN, *dv = dm + PN, *dout = dv + PN;
+    auto done = [&](hb_status st) {
+        cudaFreeAsync(d, s);
+        cudaStreamSynchronize(s);
+        return st;
+    };
+    e = cudaMemcpyAsync(dX, X, sizeof(float) * nf, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dy, y, sizeof(float) * n, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dp, p0.data(), sizeof(float) * PN, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(dm, 0, sizeof(float) * 2 * PN, s);
+    for (int ep = 0; ep < epochs && e == cudaSuccess; ep++) {
+        e = pair_model_backward(dX, dy, n, dp, dg, s);
+        if (e == cudaSuccess) e = adam_step(dp, dg, dm, dv, PN, ep + 1, lr, 0.9f, 0.999f, 1e-8f, s);
+    }
+    if (e == cudaSuccess) e = pair_model_forward(dX, n, dp, dout, s);
+    std::vector<float> out(n);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(params_out, dp, sizeof(float) * PN, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out.data(), dout, sizeof(float) * n, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return done(fail(HB_ERR_CUDA, std::string("hb_train_pair_model: ") + cudaGetErrorString(e)));
+    double mse = 0;
+    for (int r = 0; r < n; r++) mse += (double)(out[r] - y[r]) * (out[r] - y[r]);
+    if (loss_out) *loss_out = (float)(mse / n);
+    for (int i = 0; i < PN; i++)
+        if (!std::isfinite(params_out[i])) return done(fail(HB_ERR_INTERNAL, "hb_train_pair_model: training diverged"));
+    return done(HB_OK);
+}
+
+// The tile-shape model: the same network, trained on the batch autotuner's
+// measurements (features of a job-size signature and a tile shape, log ms).
+extern "C" hb_status hb_train_tile_model(hb_ctx *c, int32_t n, const float *X, const float *y, int32_t epochs,
+                                         float lr, uint64_t seed, float *loss_out) {
+    if (!c || n < 2 || !X || !y || epochs < 1 || !(lr > 0.f))
+        return fail(HB_ERR_ARG, "hb_train_tile_model: needs >= 2 rows, epochs >= 1, lr > 0");
+    for (size_t i = 0; i < (size_t)n * HB_FEATURES; i++)
+        if (!std::isfinite(X[i])) return fail(HB_ERR_ARG, "hb_train_tile_model: non-finite feature");
+    for (int i = 0; i < n; i++)
+        if (!std::isfinite(y[i])) return fail(HB_ERR_ARG, "hb_train_tile_model: non-finite target");
+    cudaSetDevice(c->device);
+    std::vector<double> mu(HB_FEATURES, 0.0), sd(HB_FEATURES, 0.0);
+    for (int i = 0; i < n; i++)
+        for (int f = 0; f < HB_FEATURES; f++) mu[f] += X[(size_t)i * HB_FEATURES + f];
+    for (int f = 0; f < HB_FEATURES; f++) mu[f] /= n;
+    for (int i = 0; i < n; i++)
+        for (int f = 0; f < HB_FEATURES; f++) {
+            const double d = X[(size_t)i * HB_FEATURES + f] - mu[f];
+            sd[f] += d * d;
+        }
+    for (int f = 0; f < HB_FEATURES; f++) {
+        sd[f] = std::sqrt(sd[f] / n);
+        if (sd[f] < 1e-6) sd[f] = 1.0;
+    }
+    std::vector<float> Xn((size_t)n * HB_FEATURES);
+    for (int i = 0; i < n; i++)
+        for (int f = 0; f < HB_FEATURES; f++)
+            Xn[(size_t)i * HB_FEATURES + f] = (float)((X[(size_t)i * HB_FEATURES + f] - mu[f]) / sd[f]);
+    std::vector<float> model(HB_MLP_PARAMS);
+    float loss = 0;
+    HB_TRY(train_one(c, n, Xn, std::vector<float>(y, y + n), epochs, lr, seed, mu, sd, model.data(), loss));
+    for (float v : model)
+        if (!std::isfinite(v)) return fail(HB_ERR_INTERNAL, "hb_train_tile_model: training diverged");
+    c->tile_model = model;
+    c->tile_model_ok = true;
+    c->tune_cache.clear();
+    if (loss_out) *loss_out = loss;
+    return HB_OK;
+}

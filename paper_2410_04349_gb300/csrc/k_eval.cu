@@ -1049,6 +1049,59 @@ __global__ void __launch_bounds__(EV_THREADS, 4) k_eval(const __grid_constant__ 
     }
 }
 
+// Per-pair timing of one program op (the paper's T_p(t1, t2) that its shallow
+// model N learns): each given pair has a warp of its own, whose lane 0
+// evaluates op k and records the clock64 cycles (no other lane's divergence
+// enters them), the verdict and N's 8 input features (kind one-hot,
+// threshold, the two operands, their difference and min/max ratio).
+__global__ void k_pair_times(const __grid_constant__ EvalParams P, int k, const uint32_t *pi, const uint32_t *pj,
+                             int n, uint32_t *cycles, uint8_t *verdict, float *X) {
+    const int t = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    if ((threadIdx.x & 31) != 0 || t >= n) return;
+    const uint32_t *a = P.rec_r + (size_t)pi[t] * P.W;
+    const uint32_t *b = (P.self_join ? P.rec_r : P.rec_s) + (size_t)pj[t] * P.W;
+    const Op &op = P.ops[k];
+    LogAcc lg{nullptr};
+    const long long c0 = clock64();
+    const bool r = eval_op<false>(P, k, a, b, lg);
+    const long long c1 = clock64();
+    cycles[t] = (uint32_t)min(c1 - c0, 0x7fffffffll);
+    verdict[t] = r ? 1 : 0;
+    float *f = X + (size_t)t * 8;
+    f[0] = op.kind == OP_ED ? 1.f : 0.f;
+    f[1] = op.kind == OP_JAC ? 1.f : 0.f;
+    f[2] = op.kind == OP_ABS ? 1.f : 0.f;
+    f[3] = op.kind == OP_ED ? op.k / 8.f : op.kind == OP_JAC ? (float)op.num / (float)op.den : log1pf(op.delta);
+    const uint32_t x1 = a[op.feat], x2 = b[op.feat];
+    bool miss;
+    float o1, o2;
+    if (op.kind == OP_ABS) {
+        o1 = __uint_as_float(x1);
+        o2 = __uint_as_float(x2);
+        miss = isnan(o1) || isnan(o2);
+    } else {
+        miss = x1 == NULL_LEN || x2 == NULL_LEN;
+        o1 = (float)x1;
+        o2 = (float)x2;
+    }
+    if (miss) {
+        f[4] = f[5] = f[6] = f[7] = -1.f;
+        return;
+    }
+    const float a1 = fabsf(o1), a2 = fabsf(o2), d = fabsf(o1 - o2);
+    if (op.kind == OP_ABS) {
+        f[4] = log1pf(a1) / 8.f;
+        f[5] = log1pf(a2) / 8.f;
+        f[6] = log1pf(d) / 8.f;
+    } else {
+        f[4] = o1 / 64.f;
+        f[5] = o2 / 64.f;
+        f[6] = d / 64.f;
+    }
+    const float mx = fmaxf(a1, a2);
+    f[7] = mx > 0.f ? fminf(a1, a2) / mx : 0.f;
+}
+
 __global__ void k_pack_pairs(const uint64_t *keys, int64_t n, int key_bits_s, hb_pair *out) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -1112,6 +1165,14 @@ cudaError_t launch_eval(const EvalParams &p, int grid, size_t smem, int logging,
         if (logging) launch<1, true>(p, multi, ring, grid, smem, s);
         else launch<1, false>(p, multi, ring, grid, smem, s);
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pair_times(const EvalParams &p, int k, const uint32_t *pi, const uint32_t *pj, int n,
+                              uint32_t *cycles, uint8_t *verdict, float *X, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    HB_LAUNCHED(1);
+    k_pair_times<<<(unsigned)((n + 3) / 4), 128, 0, s>>>(p, k, pi, pj, n, cycles, verdict, X);   // 4 pairs a block
     return cudaGetLastError();
 }
 

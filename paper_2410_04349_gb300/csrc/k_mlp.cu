@@ -203,6 +203,114 @@ cudaError_t adam_step(float *params, const float *grad, float *m, float *v, int 
 }  // namespace hb
 
 // ---------------------------------------------------------------------------
+// The paper's per-pair cost model N (Section 4.2 "Shallow NNs"; layer sizes
+// 8 -> 2 -> 6 -> 1 with ReLU after the first two, Section 6's defaults):
+// parameters W1 [8 x 2], b1 [2], W2 [2 x 6], b2 [6], W3 [6], b3, row-major.
+// One thread per row; the backward pass sums each row's gradient into the
+// block in shared memory and then into grad with one atomic per parameter.
+// ---------------------------------------------------------------------------
+namespace hb {
+namespace {
+constexpr int PF = 8, PH1 = 2, PH2 = 6;
+constexpr int PO_W1 = 0, PO_B1 = PO_W1 + PF * PH1, PO_W2 = PO_B1 + PH1, PO_B2 = PO_W2 + PH1 * PH2,
+              PO_W3 = PO_B2 + PH2, PO_B3 = PO_W3 + PH2, PN = PO_B3 + 1;
+static_assert(PN == HB_PAIR_MODEL_PARAMS, "pair model parameter layout");
+
+__device__ __forceinline__ float pn_forward(const float *x, const float *P, float *z1, float *h1, float *z2,
+                                            float *h2) {
+#pragma unroll
+    for (int j = 0; j < PH1; j++) {
+        float acc = P[PO_B1 + j];
+#pragma unroll
+        for (int i = 0; i < PF; i++) acc = fmaf(x[i], P[PO_W1 + i * PH1 + j], acc);
+        z1[j] = acc;
+        h1[j] = fmaxf(acc, 0.f);
+    }
+#pragma unroll
+    for (int j = 0; j < PH2; j++) {
+        float acc = P[PO_B2 + j];
+#pragma unroll
+        for (int i = 0; i < PH1; i++) acc = fmaf(h1[i], P[PO_W2 + i * PH2 + j], acc);
+        z2[j] = acc;
+        h2[j] = fmaxf(acc, 0.f);
+    }
+    float y = P[PO_B3];
+#pragma unroll
+    for (int i = 0; i < PH2; i++) y = fmaf(h2[i], P[PO_W3 + i], y);
+    return y;
+}
+
+__global__ void k_pn_fwd(const float *X, int n, const float *P, float *y) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    float x[PF], z1[PH1], h1[PH1], z2[PH2], h2[PH2];
+#pragma unroll
+    for (int i = 0; i < PF; i++) x[i] = X[(size_t)r * PF + i];
+    y[r] = pn_forward(x, P, z1, h1, z2, h2);
+}
+
+// gradient of mean((y - t)^2); grad must be zero on entry
+__global__ void k_pn_bwd(const float *X, const float *t, int n, const float *P, float *grad) {
+    __shared__ float g[PN];
+    for (int i = threadIdx.x; i < PN; i += blockDim.x) g[i] = 0.f;
+    __syncthreads();
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < n) {
+        float x[PF], z1[PH1], h1[PH1], z2[PH2], h2[PH2];
+#pragma unroll
+        for (int i = 0; i < PF; i++) x[i] = X[(size_t)r * PF + i];
+        const float y = pn_forward(x, P, z1, h1, z2, h2);
+        const float dy = 2.f * (y - t[r]) / (float)n;
+        atomicAdd(&g[PO_B3], dy);
+        float dz2[PH2];
+#pragma unroll
+        for (int i = 0; i < PH2; i++) {
+            atomicAdd(&g[PO_W3 + i], dy * h2[i]);
+            dz2[i] = z2[i] > 0.f ? dy * P[PO_W3 + i] : 0.f;
+            atomicAdd(&g[PO_B2 + i], dz2[i]);
+        }
+        float dz1[PH1];
+#pragma unroll
+        for (int i = 0; i < PH1; i++) {
+            float dh = 0.f;
+#pragma unroll
+            for (int j = 0; j < PH2; j++) {
+                atomicAdd(&g[PO_W2 + i * PH2 + j], h1[i] * dz2[j]);
+                dh = fmaf(dz2[j], P[PO_W2 + i * PH2 + j], dh);
+            }
+            dz1[i] = z1[i] > 0.f ? dh : 0.f;
+            atomicAdd(&g[PO_B1 + i], dz1[i]);
+        }
+#pragma unroll
+        for (int i = 0; i < PF; i++)
+#pragma unroll
+            for (int j = 0; j < PH1; j++) atomicAdd(&g[PO_W1 + i * PH1 + j], x[i] * dz1[j]);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < PN; i += blockDim.x)
+        if (g[i] != 0.f) atomicAdd(&grad[i], g[i]);
+}
+}  // namespace
+
+cudaError_t pair_model_forward(const float *X, int n, const float *params, float *y, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    HB_LAUNCHED(1);
+    k_pn_fwd<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(X, n, params, y);
+    return cudaGetLastError();
+}
+
+cudaError_t pair_model_backward(const float *X, const float *t, int n, const float *params, float *grad,
+                                cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(grad, 0, sizeof(float) * PN, s);
+    if (e != cudaSuccess || n <= 0) return e;
+    HB_LAUNCHED(1);
+    k_pn_bwd<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(X, t, n, params, grad);
+    return cudaGetLastError();
+}
+
+}  // namespace hb
+
+// ---------------------------------------------------------------------------
 // Allocation-free variant of the backward pass (hb_mlp_backward_noalloc).
 //
 // Some callers cannot allocate device memory at the moment they need a

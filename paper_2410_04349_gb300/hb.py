@@ -31,6 +31,8 @@ TYPES = {"string": 0, "int32": 1, "fp32": 2}
 FLAG_PER_JOB_LAUNCHES, FLAG_NO_GRAPH = 1, 2
 PLAN_MODES = {"rule_data": 0, "learned": 1, "given": 2, "random": 3, "cost_first": 4, "sel_first": 5}
 MAX_MDS, MAX_PREDS, FEATURES = 64, 128, 32
+PAIR_FEATURES = 8
+PAIR_MODEL_PARAMS = 8 * 2 + 2 + 2 * 6 + 6 + 6 + 1
 MLP_PARAMS = 32 * 64 + 64 + 64 * 64 + 64 + 64 + 1
 
 
@@ -100,7 +102,9 @@ EXPORTS = ["hb_create", "hb_destroy", "hb_last_error", "hb_version", "hb_load_ta
            "hb_plan", "hb_block", "hb_block_device", "hb_block_stream", "hb_block_batch", "hb_free_pairs",
            "hb_get_stats", "hb_plan_order", "hb_log_predicates", "hb_predicate_features", "hb_train_cost_model",
            "hb_get_cost_model", "hb_set_cost_model", "hb_mlp_forward", "hb_mlp_forward_bf16", "hb_mlp_backward",
-           "hb_mlp_backward_noalloc", "hb_adam_step", "hb_probe_int_issue"]
+           "hb_mlp_backward_noalloc", "hb_adam_step", "hb_probe_int_issue", "hb_time_pairs",
+           "hb_pair_model_forward", "hb_pair_model_backward", "hb_train_pair_model", "hb_tile_log",
+           "hb_train_tile_model", "hb_set_tile_model", "hb_get_tile_model", "hb_batch_tile"]
 
 _lib = None
 
@@ -130,6 +134,14 @@ def lib():
         "hb_adam_step": (st, [P, P, P, P, i32, i32, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                               P]),
         "hb_probe_int_issue": (st, [i32, P, P, P]),
+        "hb_time_pairs": (st, [P, i32, i32, P, P, P, P, P]),
+        "hb_pair_model_forward": (st, [P, i32, P, P, P]),
+        "hb_pair_model_backward": (st, [P, P, i32, P, P, P]),
+        "hb_train_pair_model": (st, [i32, P, P, i32, ctypes.c_float, ctypes.c_uint64, P, P]),
+        "hb_tile_log": (st, [P, i32, P, P, P]),
+        "hb_train_tile_model": (st, [P, i32, P, P, i32, ctypes.c_float, ctypes.c_uint64, P]),
+        "hb_set_tile_model": (st, [P, P]), "hb_get_tile_model": (st, [P, P]),
+        "hb_batch_tile": (st, [P, P, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -364,6 +376,54 @@ class Context:
                                          epochs, lr, seed, loss.ctypes.data), "hb_train_cost_model")
         return loss
 
+    def time_pairs(self, pred, i, j):
+        """(cycles [n], verdicts [n], features [n, 8]) of checking distinct
+        predicate pred on the pairs (i[k], j[k])."""
+        i = np.ascontiguousarray(i, np.uint32)
+        j = np.ascontiguousarray(j, np.uint32)
+        n = len(i)
+        cyc = np.zeros(max(n, 1), np.uint32)
+        ver = np.zeros(max(n, 1), np.uint8)
+        X = np.zeros((max(n, 1), PAIR_FEATURES), np.float32)
+        _check(lib().hb_time_pairs(self._h, pred, n, i.ctypes.data, j.ctypes.data, cyc.ctypes.data, ver.ctypes.data,
+                                   X.ctypes.data), "hb_time_pairs")
+        return cyc[:n], ver[:n], X[:n]
+
+    def tile_log(self):
+        """(features [n, 32], log ms [n]) of every tile shape the batch autotuner timed."""
+        n = ctypes.c_int32()
+        _check(lib().hb_tile_log(self._h, 0, None, None, ctypes.byref(n)), "hb_tile_log")
+        X = np.zeros((max(n.value, 1), FEATURES), np.float32)
+        y = np.zeros(max(n.value, 1), np.float32)
+        _check(lib().hb_tile_log(self._h, n.value, X.ctypes.data, y.ctypes.data, ctypes.byref(n)), "hb_tile_log")
+        return X[:n.value], y[:n.value]
+
+    def train_tile_model(self, X, y, epochs=1500, lr=2e-3, seed=0):
+        X = np.ascontiguousarray(X, np.float32)
+        y = np.ascontiguousarray(y, np.float32)
+        loss = ctypes.c_float()
+        _check(lib().hb_train_tile_model(self._h, len(y), X.ctypes.data, y.ctypes.data, epochs, lr, seed,
+                                         ctypes.byref(loss)), "hb_train_tile_model")
+        return loss.value
+
+    def set_tile_model(self, params):
+        if params is None:
+            _check(lib().hb_set_tile_model(self._h, None), "hb_set_tile_model")
+            return
+        p = np.ascontiguousarray(params, np.float32)
+        _check(lib().hb_set_tile_model(self._h, p.ctypes.data), "hb_set_tile_model")
+
+    def get_tile_model(self):
+        out = np.zeros(MLP_PARAMS, np.float32)
+        _check(lib().hb_get_tile_model(self._h, out.ctypes.data), "hb_get_tile_model")
+        return out
+
+    def batch_tile(self):
+        """(tile side, tiles per claim, 1 when the tile model chose them) of the last batch."""
+        t, c, l = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        _check(lib().hb_batch_tile(self._h, ctypes.byref(t), ctypes.byref(c), ctypes.byref(l)), "hb_batch_tile")
+        return t.value, c.value, l.value
+
     def get_cost_model(self):
         out = np.zeros(2 * MLP_PARAMS, np.float32)
         _check(lib().hb_get_cost_model(self._h, out.ctypes.data), "hb_get_cost_model")
@@ -424,3 +484,24 @@ def probe_int_issue(iters=4096, stream=None):
     ms = ctypes.c_double()
     _check(lib().hb_probe_int_issue(iters, ctypes.byref(ops), ctypes.byref(ms), stream), "hb_probe_int_issue")
     return ops.value, ms.value
+
+
+def pair_model_forward(X, params, y, stream=None):
+    """The paper's per-pair model N on device tensors X [n, 8], params [43], y [n]."""
+    _check(lib().hb_pair_model_forward(_ptr(X), X.shape[0], _ptr(params), _ptr(y), stream), "hb_pair_model_forward")
+
+
+def pair_model_backward(X, t, params, grad, stream=None):
+    _check(lib().hb_pair_model_backward(_ptr(X), _ptr(t), X.shape[0], _ptr(params), _ptr(grad), stream),
+           "hb_pair_model_backward")
+
+
+def train_pair_model(X, y, epochs=2000, lr=1e-2, seed=0):
+    """(parameters [43], final mean squared error) of N trained on the GPU."""
+    X = np.ascontiguousarray(X, np.float32)
+    y = np.ascontiguousarray(y, np.float32)
+    params = np.zeros(PAIR_MODEL_PARAMS, np.float32)
+    loss = ctypes.c_float()
+    _check(lib().hb_train_pair_model(len(y), X.ctypes.data, y.ctypes.data, epochs, lr, seed, params.ctypes.data,
+                                     ctypes.byref(loss)), "hb_train_pair_model")
+    return params, loss.value
