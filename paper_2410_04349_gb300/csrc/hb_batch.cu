@@ -123,10 +123,39 @@ static hb_status time_batch(hb_ctx *c, int n_jobs, int key_bits, int kbs, int ti
     return st;
 }
 
+// Features of a batch and a tile shape for the tile-shape model (HB_FEATURES
+// floats): the fraction of rows in jobs of 2^(5+b) .. 2^(6+b) rows for
+// b = 0..15 (smaller jobs in b = 0, larger in b = 15), log2 of the rows and of
+// the jobs, the tile side (1 for 64), log2 of the tiles per claim / 3, the
+// program's ops, MDs and equality keys, and log10 of the sum of squared job
+// sizes / 14 (the pair volume).
+static void tile_features(const hb_ctx *c, int n_jobs, int tile, int claim, float *f) {
+    for (int i = 0; i < HB_FEATURES; i++) f[i] = 0.f;
+    const double total = (double)std::max<int64_t>(c->job_rows[n_jobs], 1);
+    double sq = 0;
+    for (int j = 0; j < n_jobs; j++) {
+        const int64_t s = c->job_rows[j + 1] - c->job_rows[j];
+        int b = 0;
+        while (b < 40 && (1ll << (b + 1)) <= s) b++;
+        f[std::min(std::max(b - 5, 0), 15)] += (float)((double)s / total);
+        sq += (double)s * (double)s;
+    }
+    f[16] = (float)(std::log2(total + 1.0) / 24.0);
+    f[17] = (float)(std::log2((double)n_jobs + 1.0) / 16.0);
+    f[18] = tile == 64 ? 1.f : 0.f;
+    f[19] = (float)(std::log2((double)claim) / 3.0);
+    f[20] = (float)c->ops.size() / 16.f;
+    f[21] = (float)c->md_preds.size() / 16.f;
+    f[22] = (float)c->n_eq_total / 8.f;
+    f[23] = (float)(std::log10(sq + 1.0) / 14.0);
+}
+
 // Autotuner: the first time a job-size signature is seen, every candidate tile
 // shape (tile side x tiles per claim) is timed on the real batch and the
 // fastest is cached for the signature (log2 histogram of job sizes, job count
-// and the program).
+// and the program); each measurement is logged for the tile-shape model.
+// With a tile-shape model set, the shape of smallest predicted time is taken
+// instead of timing all of them.
 static hb_status autotune_batch(hb_ctx *c, int n_jobs, int key_bits, int kbs) {
     if (c->opt.tile != 0) {
         c->tile = c->opt.tile;
@@ -151,10 +180,55 @@ static hb_status autotune_batch(hb_ctx *c, int n_jobs, int key_bits, int kbs) {
     const int claims[] = {1, 2, 4, 8};
     float best = 1e30f;
     int bt = 32, bc = 2;
+    if (c->tile_model_ok) {
+        // the tile-shape model's argmin over the same candidates (bf16 inference, no trial runs)
+        float F[8 * HB_FEATURES], y[8];
+        int k = 0;
+        for (int t : tiles)
+            for (int cl : claims) tile_features(c, n_jobs, t, cl, F + (size_t)HB_FEATURES * k++);
+        Buf d;
+        HB_TRY(grow(c, d, sizeof(float) * (8 * HB_FEATURES + 8 + HB_MLP_PARAMS)));
+        float *dX = as<float>(d), *dy = dX + 8 * HB_FEATURES, *dp = dy + 8;
+        HB_CUDA(cudaMemcpyAsync(dX, F, sizeof(F), cudaMemcpyHostToDevice, c->stream));
+        HB_CUDA(cudaMemcpyAsync(dp, c->tile_model.data(), sizeof(float) * HB_MLP_PARAMS, cudaMemcpyHostToDevice,
+                                c->stream));
+        HB_CUDA(mlp_forward(dX, 8, dp, dy, 1, c->stream));
+        HB_CUDA(cudaMemcpyAsync(y, dy, sizeof(y), cudaMemcpyDeviceToHost, c->stream));
+        HB_CUDA(cudaStreamSynchronize(c->stream));
+        free_buf(c, d);
+        k = 0;
+        bool ok = true;
+        for (int t : tiles)
+            for (int cl : claims) {
+                ok = ok && std::isfinite(y[k]);
+                const size_t smem = eval_smem_bytes(c->HW, c->n_eq_total, c->lut.empty() ? 0 : 1, t);
+                if (eval_blocks_per_sm(t, 0, smem) >= 1 && y[k] < best) {
+                    best = y[k];
+                    bt = t;
+                    bc = cl;
+                }
+                k++;
+            }
+        if (ok && best < 1e30f) {
+            c->tile = bt;
+            c->claim = bc;
+            c->tune_learned = 1;
+            c->tune_cache.push_back({sig, {bt, bc}});
+            return HB_OK;
+        }
+        best = 1e30f;   // unusable predictions: measure
+    }
+    c->tune_learned = 0;
     for (int t : tiles)
         for (int cl : claims) {
             float ms = 0;
             HB_TRY(time_batch(c, n_jobs, key_bits, kbs, t, cl, ms));
+            if (ms < 1e29f) {
+                float F[HB_FEATURES];
+                tile_features(c, n_jobs, t, cl, F);
+                c->tune_log.insert(c->tune_log.end(), F, F + HB_FEATURES);
+                c->tune_log.push_back((float)std::log(std::max(ms, 1e-3f)));
+            }
             if (ms < best) {
                 best = ms;
                 bt = t;
@@ -330,4 +404,45 @@ extern "C" hb_status hb_block_batch(hb_ctx *c, int32_t n_jobs, const int64_t *jo
         return HB_OK;
     }
     return fail(HB_ERR_OVERFLOW, "hb_block_batch: result capacity could not be settled");
+}
+
+extern "C" hb_status hb_tile_log(hb_ctx *c, int32_t cap, float *X_out, float *y_out, int32_t *n_out) {
+    if (!c || !n_out || (cap > 0 && (!X_out || !y_out))) return fail(HB_ERR_ARG, "hb_tile_log: bad arguments");
+    const int rows = (int)(c->tune_log.size() / (HB_FEATURES + 1));
+    *n_out = rows;
+    for (int r = 0; r < rows && r < cap; r++) {
+        memcpy(X_out + (size_t)r * HB_FEATURES, &c->tune_log[(size_t)r * (HB_FEATURES + 1)], sizeof(float) * HB_FEATURES);
+        y_out[r] = c->tune_log[(size_t)r * (HB_FEATURES + 1) + HB_FEATURES];
+    }
+    return HB_OK;
+}
+
+extern "C" hb_status hb_set_tile_model(hb_ctx *c, const float *params) {
+    if (!c) return fail(HB_ERR_ARG, "hb_set_tile_model: ctx is NULL");
+    c->tune_cache.clear();
+    if (!params) {
+        c->tile_model.clear();
+        c->tile_model_ok = false;
+        return HB_OK;
+    }
+    for (int i = 0; i < HB_MLP_PARAMS; i++)
+        if (!std::isfinite(params[i])) return fail(HB_ERR_ARG, "hb_set_tile_model: non-finite parameter");
+    c->tile_model.assign(params, params + HB_MLP_PARAMS);
+    c->tile_model_ok = true;
+    return HB_OK;
+}
+
+extern "C" hb_status hb_get_tile_model(hb_ctx *c, float *params_out) {
+    if (!c || !params_out) return fail(HB_ERR_ARG, "hb_get_tile_model: NULL argument");
+    if (!c->tile_model_ok) return fail(HB_ERR_STATE, "hb_get_tile_model: no tile model trained or set");
+    memcpy(params_out, c->tile_model.data(), sizeof(float) * HB_MLP_PARAMS);
+    return HB_OK;
+}
+
+extern "C" hb_status hb_batch_tile(const hb_ctx *c, int32_t *tile, int32_t *claim, int32_t *learned) {
+    if (!c || !tile || !claim || !learned) return fail(HB_ERR_ARG, "hb_batch_tile: NULL argument");
+    *tile = c->tile;
+    *claim = c->claim;
+    *learned = c->tune_learned;
+    return HB_OK;
 }

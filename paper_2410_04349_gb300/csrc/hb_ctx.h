@@ -134,6 +134,12 @@ struct hb_ctx {
     // learned model: [cost net | selectivity net]
     std::vector<float> model;
     bool model_ok = false;
+    // tile-shape model (same 32-64-64-1 network): predicts the log of a batch launch
+    // sequence's milliseconds for a job-size signature and a tile shape
+    std::vector<float> tile_model;
+    bool tile_model_ok = false;
+    std::vector<float> tune_log;      // autotuner measurements: HB_FEATURES features + log(ms) per shape
+    int tune_learned = 0;             // 1 when the last batch's shape came from the tile model
     // pinned staging
     void *pin[2] = {nullptr, nullptr};
     cudaEvent_t pin_ev[2] = {nullptr, nullptr};

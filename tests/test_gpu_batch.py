@@ -61,3 +61,46 @@ def test_batch_rejects_bad_job_rows():
         bad[-1] += 1
         with pytest.raises(hb.HBError):
             ctx.block_batch(bad)
+
+
+@pytest.mark.slow
+def test_learned_tile_shape_skips_trial_runs_on_a_held_out_batch():
+    """The committed tile-shape model (trained on the autotuner's logs of other
+    batches) picks the batched form's tile shape without timing the eight
+    candidates: on a held-out batch the first call is faster than with the
+    autotuner, the chosen shape runs within 15 % of the autotuner's choice and
+    the pairs are identical."""
+    import os
+    import statistics
+    import time
+    import torch
+    model = np.load(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                                 "paper_2410_04349_gb300", "tile_model.npy"))
+    rng = np.random.default_rng(77)
+    sizes = [int(x) for x in np.clip(np.round(np.exp(np.log(700) + 0.9 * rng.standard_normal(1200))), 20, 8000)]
+    t, mds = synth.config4(n_jobs=len(sizes), sizes=sizes, seed=424242)
+    res = {}
+    for name, m in (("autotuned", None), ("learned", model)):
+        with hb.Context(device=0) as ctx:
+            ctx.load_table(0, t.n_rows, t.columns)
+            for md in mds:
+                ctx.add_md(md)
+            if m is not None:
+                ctx.set_tile_model(m)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            pairs, offs = ctx.block_batch(t.job_offsets)
+            first = time.perf_counter() - t0
+            shape = ctx.batch_tile()
+            steady = []
+            for _ in range(7):
+                t0 = time.perf_counter()
+                ctx.block_batch(t.job_offsets)
+                steady.append(time.perf_counter() - t0)
+            res[name] = (first, statistics.median(steady), shape, pairs, offs)
+    fa, sa, sha, pa, oa = res["autotuned"]
+    fl, sl, shl, pl, ol = res["learned"]
+    assert sha[2] == 0 and shl[2] == 1
+    assert np.array_equal(pa, pl) and np.array_equal(oa, ol)
+    assert fl < fa
+    assert sl <= 1.15 * sa, (res["autotuned"][:3], res["learned"][:3])
