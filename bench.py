@@ -329,12 +329,23 @@ def compare_c4(args):
     from paper_2410_04349_gb300 import hb
     t, mds = synth.config4()
     res = {}
-    for name, flags, steps in (("batched", 0, args.steps), ("per_job", hb.FLAG_PER_JOB_LAUNCHES, 1)):
+    first, shapes = {}, {}
+    tile_model = np.load(os.path.join(ROOT, "paper_2410_04349_gb300", "tile_model.npy"))
+    for name, flags, steps, tm in (("batched", 0, args.steps, None), ("learned_tile", 0, args.steps, tile_model),
+                                   ("per_job", hb.FLAG_PER_JOB_LAUNCHES, 1, None)):
         with hb.Context(device=0, flags=flags) as ctx:
             ctx.load_table(0, t.n_rows, t.columns)
             for md in mds:
                 ctx.add_md(md)
-            for _ in range(1 if flags else max(args.warmup, 3)):
+            if tm is not None:
+                ctx.set_tile_model(tm)
+            torch.cuda.synchronize()
+            f0 = time.perf_counter()
+            pairs, offs = ctx.block_batch(t.job_offsets)   # first call: tile shape chosen, graph captured
+            first[name] = time.perf_counter() - f0
+            if not flags:
+                shapes[name] = ctx.batch_tile()
+            for _ in range(0 if flags else max(args.warmup, 3) - 1):
                 pairs, offs = ctx.block_batch(t.job_offsets)
             times = []
             l0 = ctx.stats()["kernel_launches"]
@@ -347,13 +358,20 @@ def compare_c4(args):
             res[name] = (statistics.median(times), st, pairs, offs, (st["kernel_launches"] - l0) // steps)
     tb, stb, pb, ob, lb = res["batched"]
     tp, stp, pp, op_, lp = res["per_job"]
-    identical = bool(np.array_equal(pb, pp) and np.array_equal(ob, op_))
+    tl, stl, pl, ol, ll = res["learned_tile"]
+    identical = bool(np.array_equal(pb, pp) and np.array_equal(ob, op_) and np.array_equal(pb, pl)
+                     and np.array_equal(ob, ol))
     return {"workload": f"10,000 independent jobs, {t.n_rows} tuples in all (lognormal sizes in [50, 20000]), "
                         "C2 schema and rules, host-resident tables",
             "candidate_pairs": stb["candidate_pairs"], "emitted_pairs": int(len(pb)),
             "batched": {"ms_per_step": tb * 1e3, "value": stb["candidate_pairs"] / tb, "gpu_launches": lb,
                         "tile": stb["tile"], "steps": args.steps},
             "per_job": {"ms_per_step": tp * 1e3, "value": stp["candidate_pairs"] / tp, "gpu_launches": lp, "steps": 1},
+            "learned_tile": {"ms_per_step": tl * 1e3, "first_call_ms": first["learned_tile"] * 1e3,
+                             "autotuned_first_call_ms": first["batched"] * 1e3,
+                             "shape": {"tile": shapes["learned_tile"][0], "claim": shapes["learned_tile"][1],
+                                       "from_model": shapes["learned_tile"][2]},
+                             "autotuned_shape": {"tile": shapes["batched"][0], "claim": shapes["batched"][1]}},
             "speedup": tp / tb, "identical_pair_sets": identical, "unit": UNIT,
             "timing": "wall clock around each hb_block_batch call (host tables in, pairs out), median"}
 

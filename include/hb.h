@@ -155,6 +155,8 @@ typedef struct {
     int32_t n_mds;
     int32_t record_words;             /* 32-bit words of a tuple's packed record (codes and features) */
     int32_t hot_words;                /* 32-bit words of a tuple's hot record (what every pair's first test reads) */
+    int32_t n_branches;               /* partitioned blocking (hb_set_partitions): root branches, else 0 */
+    int32_t branch_pred[HB_MAX_MDS];  /* per branch: its root-edge predicate id (-1: one partition of all tuples) */
 } hb_plan_info;
 
 typedef struct {
@@ -172,7 +174,14 @@ typedef struct {
 } hb_stats;
 
 /* ---- context ---- */
-HB_API hb_status hb_create(hb_ctx **out, const hb_options *opt);   /* opt may be NULL (defaults) */
+/*
+ * opt may be NULL (defaults).  Fault injection for tests of the error paths:
+ * when the environment holds HB_FAIL_ALLOC_AFTER=N (a decimal N >= 0) at
+ * hb_create, the context's (N+1)-th device or page-locked allocation fails
+ * once with HB_ERR_OOM; the call that met it returns HB_ERR_OOM and leaves the
+ * context usable (a repeated call allocates again).
+ */
+HB_API hb_status hb_create(hb_ctx **out, const hb_options *opt);
 HB_API void hb_destroy(hb_ctx *ctx);
 HB_API const char *hb_last_error(void);                            /* thread-local; "" when none */
 HB_API const char *hb_version(void);
@@ -210,6 +219,29 @@ HB_API hb_status hb_clear_mds(hb_ctx *ctx);
  * Must follow the last hb_add_md / hb_load_table.  info_out is optional.
  */
 HB_API hb_status hb_plan(hb_ctx *ctx, int32_t mode, hb_plan_info *info_out);
+
+/*
+ * Section 5.3 "Data partitioning": block by root-edge hash partitions instead
+ * of exact equality groups.  Each child of the execution tree's root gives one
+ * hash function, built from the predicate on that edge; here an MD's root edge
+ * is its first equality predicate in written order (equality predicates are
+ * the block keys and head every path), and MDs without one share a branch
+ * whose single partition holds all tuples (the section's remark: a partition
+ * may pull all others).  A tuple's partition under a function is the 32-bit
+ * FNV-1a hash (offset basis 2166136261, prime 16777619) of the value's bytes
+ * (a string or its prefix, an int32's four little-endian bytes) modulo m; a
+ * missing value is in no partition.  A pair is a candidate when some branch
+ * puts both tuples in one partition; it is evaluated once, in the first such
+ * branch, against every MD, so the result equals the unpartitioned one while
+ * the candidate count (hb_get_stats) grows as m shrinks.
+ *
+ * m = 0 restores exact equality groups (the default); m >= 1 applies from the
+ * next hb_plan (a later hb_block plans again if needed).  Partitioned blocking
+ * runs on hb_block and hb_block_device with at most 8 distinct equality keys;
+ * hb_block_stream and hb_block_batch then return HB_ERR_STATE.  m > 2^31 is
+ * HB_ERR_ARG.
+ */
+HB_API hb_status hb_set_partitions(hb_ctx *ctx, uint32_t m);
 
 /*
  * Compute Ca for the loaded tables (self-join when only R is loaded).

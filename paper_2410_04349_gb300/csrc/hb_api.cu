@@ -43,13 +43,30 @@ using namespace hb;
 
 namespace hb {
 
+// Host-side fault injection: HB_FAIL_ALLOC_AFTER=N in the environment at
+// hb_create makes the (N+1)-th device or page-locked allocation of the context
+// fail once with HB_ERR_OOM, as a real shortage would.
+static bool injected_failure(hb_ctx *c) {
+    if (c->fail_alloc_after < 0) return false;
+    if (c->fail_alloc_after == 0) {
+        c->fail_alloc_after = -1;
+        return true;
+    }
+    c->fail_alloc_after--;
+    return false;
+}
+
 hb_status grow(hb_ctx *c, Buf &b, size_t bytes) {
     if (bytes == 0) bytes = 16;
     if (b.bytes >= bytes) return HB_OK;
-    if (b.p) cudaFreeAsync(b.p, c->stream);
+    if (b.p) {
+        cudaFreeAsync(b.p, c->stream);
+        c->batch_graph_key.clear();   // a captured batch sequence may hold the old buffer
+    }
     b.p = nullptr;
     b.bytes = 0;
     size_t want = bytes + bytes / 8;
+    if (injected_failure(c)) return fail(HB_ERR_OOM, "device allocation of " + std::to_string(want) + " bytes failed (injected)");
     cudaError_t e = cudaMallocAsync(&b.p, want, c->stream);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -100,6 +117,7 @@ static void free_dicts(hb_ctx *c) {
 }
 
 static void invalidate_encoding(hb_ctx *c) {
+    c->batch_graph_key.clear();
     free_side_encoding(c, c->side[0]);
     free_side_encoding(c, c->side[1]);
     free_dicts(c);
@@ -107,6 +125,10 @@ static void invalidate_encoding(hb_ctx *c) {
 
 hb_status dmalloc(hb_ctx *c, void **p, size_t bytes) {
     if (bytes == 0) bytes = 16;
+    if (injected_failure(c)) {
+        *p = nullptr;
+        return fail(HB_ERR_OOM, "device allocation of " + std::to_string(bytes) + " bytes failed (injected)");
+    }
     cudaError_t e = cudaMallocAsync(p, bytes, c->stream);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -132,7 +154,9 @@ hb_status ensure_pinned(hb_ctx *c, size_t want) {
         }
         c->pin[b] = nullptr;
     }
+    c->pin_bytes = 0;
     for (int b = 0; b < 2; b++) {
+        if (injected_failure(c)) return fail(HB_ERR_OOM, "page-locked allocation failed (injected)");
         HB_CUDA(cudaMallocHost(&c->pin[b], want));
         if (!c->pin_ev[b]) HB_CUDA(cudaEventCreateWithFlags(&c->pin_ev[b], cudaEventDisableTiming));
     }
@@ -207,6 +231,11 @@ extern "C" hb_status hb_create(hb_ctx **out, const hb_options *opt) {
         return fail(HB_ERR_ARG, "hb_create: tile must be 0, 32 or 64");
     }
     c->device = c->opt.device;
+    if (const char *inj = getenv("HB_FAIL_ALLOC_AFTER")) {
+        char *end = nullptr;
+        const long long v = strtoll(inj, &end, 10);
+        if (end != inj && *end == 0 && v >= 0) c->fail_alloc_after = v;
+    }
     cudaError_t e = cudaSetDevice(c->device);
     if (e != cudaSuccess) {
         delete c;
@@ -582,6 +611,14 @@ static hb_status build_layout(hb_ctx *c, bool job_key) {
         pi.eq_index = e;
     }
     c->n_eq_total = (int)c->eqkeys.size() + (job_key ? 1 : 0);
+    c->layout_part_m = c->part_m;
+    if (c->part_m) {
+        // Section 5.3 partitions: key e's partition under its hash function in
+        // word n_eq + e, next to the exact codes (which the rules still test)
+        if (job_key) return fail(HB_ERR_STATE, "partitioned blocking runs on hb_block / hb_block_device only");
+        c->n_eq_total = 2 * (int)c->eqkeys.size();
+        if (c->n_eq_total > MAX_EQ) return fail(HB_ERR_ARG, "at most 8 distinct equality keys when partitioned");
+    }
     if (c->n_eq_total > MAX_EQ) return fail(HB_ERR_ARG, "at most 16 distinct equality keys");
     int word = c->n_eq_total;
     for (int pid = 0; pid < (int)c->preds.size(); pid++) {
@@ -807,6 +844,57 @@ void ensure_pred_stats(hb_ctx *c) {
     }
 }
 
+// Section 5.3 "Data partitioning": one hash function per child of the root
+// of the execution tree, built from the predicate on that root edge.  The
+// equality predicates of an MD are its block keys and head its path, so an
+// MD's root edge is its first equality key in written order; an MD without
+// one hangs from a similarity root, whose partitions may pull all others (the
+// section's remark): that branch is one partition of all tuples.  Each branch
+// becomes a grouping MD (after the rules' MDs) whose only key is the branch's
+// partition word: the grouping MDs alone own pairs (the lowest branch that
+// puts both tuples in one partition), and the program still tests every
+// rule, so the result is the plain blocking result.
+static hb_status add_partition_groups(hb_ctx *c) {
+    const int n_md = (int)c->md_preds.size();
+    const int n_eq = (int)c->eqkeys.size();
+    c->branch_key.clear();
+    c->branch_pred.clear();
+    for (int m = 0; m < n_md; m++) {
+        int key = -1, pred = -1;
+        for (int id : c->md_preds[m])
+            if (c->preds[id].eq_index >= 0) {
+                key = c->preds[id].eq_index;
+                pred = id;
+                break;
+            }
+        bool seen = false;
+        for (int k : c->branch_key) seen |= k == key;
+        if (!seen) {
+            c->branch_key.push_back(key);
+            c->branch_pred.push_back(pred);
+        }
+    }
+    const int nb = (int)c->branch_key.size();
+    if (n_md + nb > MAX_MD) return fail(HB_ERR_ARG, "rules plus partition branches exceed 64");
+    c->eqset.resize(n_md);
+    c->group_mds = 0;
+    c->active.clear();
+    for (int b = 0; b < nb; b++) {
+        const int k = c->branch_key[b];
+        c->eqset.push_back(k >= 0 ? (uint16_t)(1u << (n_eq + k)) : (uint16_t)0);
+        c->group_mds |= 1ull << (n_md + b);
+        c->active.push_back(n_md + b);
+    }
+    c->lut.clear();
+    if (c->n_eq_total <= LUT_MAX_EQ) {
+        c->lut.assign((size_t)1 << c->n_eq_total, 0);
+        for (uint32_t E = 0; E < c->lut.size(); E++)
+            for (int m = 0; m < (int)c->eqset.size(); m++)
+                if ((E & c->eqset[m]) == c->eqset[m]) c->lut[E] |= 1ull << m;
+    }
+    return HB_OK;
+}
+
 static hb_status finish_plan(hb_ctx *c, int mode, const std::vector<double> &sp, const std::vector<double> &cost) {
     const int P = (int)c->preds.size();
     const int n_md = (int)c->md_preds.size();
@@ -958,6 +1046,12 @@ static hb_status finish_plan(hb_ctx *c, int mode, const std::vector<double> &sp,
     I.tile = tile;
     I.record_words = c->W;
     I.hot_words = c->HW;
+    c->group_mds = 0;
+    if (c->part_m) {
+        HB_TRY(add_partition_groups(c));
+        I.n_branches = (int32_t)c->branch_key.size();
+        for (size_t b = 0; b < c->branch_pred.size() && b < HB_MAX_MDS; b++) I.branch_pred[b] = c->branch_pred[b];
+    }
     c->planned = true;
     return HB_OK;
 }
@@ -969,7 +1063,7 @@ hb_status do_plan(hb_ctx *c, int mode, bool job_key) {
     if (mode < 0 || mode > 5) return fail(HB_ERR_ARG, "hb_plan: unknown mode");
     cudaSetDevice(c->device);
     auto t0 = std::chrono::steady_clock::now();
-    bool relayout = !c->planned || c->batch_layout != job_key || c->preds.empty();
+    bool relayout = !c->planned || c->batch_layout != job_key || c->preds.empty() || c->layout_part_m != c->part_m;
     if (relayout) {
         invalidate_encoding(c);
         HB_TRY(build_layout(c, job_key));
@@ -1005,6 +1099,16 @@ hb_status do_plan(hb_ctx *c, int mode, bool job_key) {
 
 }  // namespace hb
 
+extern "C" hb_status hb_set_partitions(hb_ctx *c, uint32_t m) {
+    if (!c) return fail(HB_ERR_ARG, "hb_set_partitions: ctx is NULL");
+    if (m > (1u << 31)) return fail(HB_ERR_ARG, "hb_set_partitions: m above 2^31");
+    if (m != c->part_m) {
+        c->part_m = m;
+        c->planned = false;   // the record layout changes: plan (and encode) again
+    }
+    return HB_OK;
+}
+
 extern "C" hb_status hb_plan(hb_ctx *c, int32_t mode, hb_plan_info *info_out) {
     if (!c) return fail(HB_ERR_ARG, "hb_plan: ctx is NULL");
     HB_TRY(do_plan(c, mode, false));
@@ -1030,26 +1134,29 @@ __global__ void k_job_codes(const int64_t *job_rows, int n_jobs, int64_t n, uint
 hb_status encode_side(hb_ctx *c, int side) {
     SideData &S = c->side[side];
     if (S.encoded && S.hot_map == c->hot_map) return HB_OK;
+    c->batch_graph_key.clear();   // a captured batch sequence holds the old records
     if (S.encoded) {
         // a new plan staged other filter operands: repack the hot records only
         if (S.hot) cudaFreeAsync(S.hot, c->stream);
+        S.hot = nullptr;
+        S.encoded = false;   // until the repack is done
         void *q = nullptr;
         HB_TRY(dmalloc(c, &q, sizeof(uint32_t) * (size_t)c->HW * (size_t)(S.n > 0 ? S.n : 1) + 64));
         S.hot = static_cast<uint32_t *>(q);
         hot_pack(S.rec, c->W, S.n, S.hot, c->HW, c->hot_map.data(), c->stream);
         S.hot_map = c->hot_map;
+        S.encoded = true;
         HB_CUDA(cudaGetLastError());
         return HB_OK;
     }
+    free_side_encoding(c, S);   // whatever an earlier, failed encoding left
     const int64_t n = S.n;
     const int W = c->W;
     void *p = nullptr;
     HB_TRY(dmalloc(c, &p, sizeof(uint32_t) * (size_t)W * (size_t)(n > 0 ? n : 1) + 64));
     S.rec = static_cast<uint32_t *>(p);
     HB_CUDA(cudaMemsetAsync(S.rec, 0, sizeof(uint32_t) * (size_t)W * (size_t)(n > 0 ? n : 1), c->stream));
-    // equality codes
-    Buf codes;
-    HB_TRY(grow(c, codes, sizeof(uint32_t) * (size_t)(n + 1)));
+    // equality codes, written into the records
     if (side == 0) {
         free_dicts(c);
         c->dict.assign(c->eqkeys.size(), nullptr);
@@ -1062,14 +1169,15 @@ hb_status encode_side(hb_ctx *c, int side) {
             HB_TRY(dmalloc(c, &p, sizeof(uint64_t) * cap));
             c->dict[e] = static_cast<uint64_t *>(p);
             c->dict_cap[e] = cap;
-            dict_build(S.cols[k.col_t], k.prefix, c->dict[e], cap, as<uint32_t>(codes), c->stream);
+            dict_build(S.cols[k.col_t], k.prefix, c->dict[e], cap, S.rec + e, W, c->stream);
         } else {
             dict_probe(S.cols[k.col_s], k.prefix, c->side[0].cols[k.col_t], k.prefix, c->dict[e], c->dict_cap[e],
-                       as<uint32_t>(codes), c->stream);
+                       S.rec + e, W, c->stream);
         }
-        code_feature(as<uint32_t>(codes), n, S.rec, W, (int)e, c->stream);
+        if (c->part_m)
+            part_feature(S.cols[side == 0 ? k.col_t : k.col_s], k.prefix, c->part_m, S.rec, W,
+                         (int)(c->eqkeys.size() + e), c->stream);
     }
-    free_buf(c, codes);
     // feature groups
     S.grams.assign(c->groups.size(), nullptr);
     Buf flag;
@@ -1095,15 +1203,11 @@ hb_status encode_side(hb_ctx *c, int side) {
             // two columns of one relation (self-join): both coded in the first column's dictionary
             const DevCol &A = S.cols[G.col_t], &B = S.cols[G.col_s];
             const uint64_t cap = pow2_at_least(std::max<uint64_t>(2 * (uint64_t)n, 1024));
-            Buf table, cb;
+            Buf table;
             HB_TRY(grow(c, table, sizeof(uint64_t) * cap));
-            HB_TRY(grow(c, cb, sizeof(uint32_t) * (size_t)(n + 1)));
-            dict_build(A, -1, as<uint64_t>(table), cap, as<uint32_t>(cb), c->stream);
-            code_feature(as<uint32_t>(cb), n, S.rec, W, G.word, c->stream);
-            dict_probe(B, -1, A, -1, as<uint64_t>(table), cap, as<uint32_t>(cb), c->stream);
-            code_feature(as<uint32_t>(cb), n, S.rec, W, G.word + 1, c->stream);
+            dict_build(A, -1, as<uint64_t>(table), cap, S.rec + G.word, W, c->stream);
+            dict_probe(B, -1, A, -1, as<uint64_t>(table), cap, S.rec + G.word + 1, W, c->stream);
             free_buf(c, table);
-            free_buf(c, cb);
             continue;
         }
         if (G.kind == OP_JAC && G.tokens) {
@@ -1308,14 +1412,15 @@ EvalParams make_params(hb_ctx *c, const uint32_t *rec_r, const uint32_t *rec_s, 
     for (int m = 0; m < (int)c->md_preds.size(); m++)
         for (int k = (int)c->ops.size() - 1; k >= 0; k--)
             if (c->ops[k].need & (1ull << m)) P.first_op[m] = (int8_t)k;
-    for (int m = 0; m < (int)c->md_preds.size(); m++) {
+    const int n_all = (int)c->eqset.size();   // the rules' MDs, then any grouping MDs
+    for (int m = 0; m < n_all; m++) {
         uint64_t base = 0;
-        for (int j = 0; j < (int)c->md_preds.size(); j++)
+        for (int j = 0; j < n_all; j++)
             if ((c->eqset[j] & ~c->eqset[m]) == 0) base |= 1ull << j;
         P.base_alive[m] = base;
         int nb = 0;
         bool filterable = (base & c->eqonly) == 0;
-        for (int j = 0; j < (int)c->md_preds.size() && filterable; j++) {
+        for (int j = 0; j < n_all && filterable; j++) {
             if (!(base & (1ull << j))) continue;
             const int f = P.first_op[j];
             if (f < 0 || c->ops[f].hot == 255) {   // no staged filter operand: no phase-1 filter
@@ -1353,8 +1458,15 @@ EvalParams make_params(hb_ctx *c, const uint32_t *rec_r, const uint32_t *rec_s, 
         }
     }
     P.self_join = self ? 1 : 0;
-    P.n_md = (int)c->md_preds.size();
+    P.n_md = (int)c->eqset.size();
     P.use_lut = c->lut.empty() ? 0 : 1;
+    P.group_mds = c->group_mds;
+    P.owner_mds = c->group_mds ? c->group_mds : ~0ull;
+    P.keymask = c->n_eq_total >= 32 ? 0xffffffffu : ((1u << c->n_eq_total) - 1u);
+    if (c->group_mds) {   // only the keys some MD holds: the rules' codes and the branches' partitions
+        P.keymask = 0;
+        for (uint16_t e : c->eqset) P.keymask |= e;
+    }
     P.tile = c->tile;
     P.key_bits_s = key_bits_s;
     P.eqonly = c->eqonly;

@@ -94,6 +94,15 @@ struct hb_ctx {
     std::vector<std::vector<hb_predicate>> md_raw;
     std::deque<std::string> consts;   // constants of CONST_EQ predicates (md_raw points here)
     int n_user_mds = 0;               // MDs added; md_preds also holds transposed copies (self-join)
+    // Section 5.3 data partitioning (hb_set_partitions): m partitions per
+    // root-edge hash function, 0 = exact equality groups; when partitioned,
+    // one grouping MD per root branch follows the rules' MDs in eqset
+    int64_t fail_alloc_after = -1;   // HB_FAIL_ALLOC_AFTER fault injection (-1: off)
+    uint32_t part_m = 0;
+    uint32_t layout_part_m = 0;       // part_m the layout was built for
+    uint64_t group_mds = 0;           // bits of the grouping MDs
+    std::vector<int> branch_key;      // per branch: equality key index (-1: one partition of all tuples)
+    std::vector<int> branch_pred;     // per branch: its root predicate (-1: none)
     // plan
     bool planned = false;
     bool batch_layout = false;   // extra job key

@@ -101,6 +101,13 @@ struct EvalParams {
     int32_t tile;           // 32 or 64
     int32_t key_bits_s;     // packed output key = tid1 << key_bits_s | tid2
     uint64_t eqonly;        // MDs without any non-equality predicate
+    // Section 5.3 partitions: MDs that only group pairs (one per root-edge hash
+    // function, no predicates: never a witness), the MDs that may own a pair
+    // (all by default; the grouping MDs when partitioned) and the equality
+    // words phase 1 compares (all by default)
+    uint64_t group_mds;
+    uint64_t owner_mds;
+    uint32_t keymask;
     uint16_t eqset[MAX_MD]; // equality keys of each MD (bit e = key e)
     int8_t first_op[MAX_MD];// first program op of each MD (-1: none)
     // per MD m: the MDs alive for every pair of m's blocks (equality keys a
@@ -156,10 +163,12 @@ void radix_sort_u64(uint64_t *keys, uint64_t *alt, int64_t n_max, const unsigned
                     void *tmp, size_t tmp_bytes, cudaStream_t s, uint64_t **result);
 
 // k_encode.cu
-void dict_build(const DevCol &c, int prefix, uint64_t *table, uint64_t cap, uint32_t *codes, cudaStream_t s);
+// exact codes (the slot of an equal value) written to codes[i * stride]
+void dict_build(const DevCol &c, int prefix, uint64_t *table, uint64_t cap, uint32_t *codes, int64_t stride,
+                cudaStream_t s);
 void dict_probe(const DevCol &probe, int prefix, const DevCol &owner, int owner_prefix, const uint64_t *table,
-                uint64_t cap, uint32_t *codes, cudaStream_t s);
-void code_feature(const uint32_t *codes, int64_t n, uint32_t *rec, int W, int feat, cudaStream_t s);
+                uint64_t cap, uint32_t *codes, int64_t stride, cudaStream_t s);
+void part_feature(const DevCol &c, int prefix, uint32_t m, uint32_t *rec, int W, int word, cudaStream_t s);
 // hot[i][h] = rec[i][map[h]] (0 where map[h] < 0); HW <= 64
 void hot_pack(const uint32_t *rec, int W, int64_t n, uint32_t *hot, int HW, const int32_t *map, cudaStream_t s);
 void ed_features(const DevCol &c, uint32_t *rec, int W, int feat, cudaStream_t s);

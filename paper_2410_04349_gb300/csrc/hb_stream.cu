@@ -108,7 +108,7 @@ cudaError_t copy_chunk_direct(const hb_column *cols, const std::vector<int> &nee
 }  // namespace
 
 // encoding of one S chunk, asynchronous (the Jaccard length flag is checked later)
-static hb_status encode_chunk(hb_ctx *c, SideData &S, unsigned int *too_long, Buf &codes, Buf &grams_buf,
+static hb_status encode_chunk(hb_ctx *c, SideData &S, unsigned int *too_long, Buf &grams_buf,
                               std::vector<size_t> &gram_off) {
     const int64_t n = S.n;
     const int W = c->W;
@@ -116,8 +116,7 @@ static hb_status encode_chunk(hb_ctx *c, SideData &S, unsigned int *too_long, Bu
     for (size_t e = 0; e < c->eqkeys.size(); e++) {
         const EqKey &k = c->eqkeys[e];
         dict_probe(S.cols[k.col_s], k.prefix, c->side[0].cols[k.col_t], k.prefix, c->dict[e], c->dict_cap[e],
-                   as<uint32_t>(codes), c->stream);
-        code_feature(as<uint32_t>(codes), n, S.rec, W, (int)e, c->stream);
+                   S.rec + e, W, c->stream);
     }
     S.grams.assign(c->groups.size(), nullptr);
     for (size_t g = 0; g < c->groups.size(); g++) {
@@ -147,6 +146,7 @@ extern "C" hb_status hb_block_stream(hb_ctx *c, int64_t n_rows_s, int32_t n_cols
     *pairs_out = nullptr;
     *n_out = 0;
     if (c->side[0].cols.empty() && c->side[0].n == 0) return fail(HB_ERR_STATE, "hb_block_stream: R not loaded");
+    if (c->part_m) return fail(HB_ERR_STATE, "hb_block_stream: partitioned blocking runs on hb_block only");
     if (n_rows_s < 0 || n_rows_s >= (1ll << 30)) return fail(HB_ERR_ARG, "hb_block_stream: n_rows_s out of range");
     for (int k = 0; k < n_cols; k++) {
         const hb_column &col = cols_s[k];
@@ -293,7 +293,7 @@ extern "C" hb_status hb_block_stream(hb_ctx *c, int64_t n_rows_s, int32_t n_cols
     const int W = c->W;
     const int na = (int)c->active.size();
     const uint64_t H = pow2_at_least(std::max<uint64_t>(2 * (uint64_t)std::max<int64_t>(n_r, 1), 1024));
-    Buf tables, cnt_r, start_r, chunk_rec, chunk_hot, chunk_grams, codes, flag;
+    Buf tables, cnt_r, start_r, chunk_rec, chunk_hot, chunk_grams, flag;
     HB_STRY(grow(c, tables, sizeof(uint64_t) * H * std::max(na, 1)));
     HB_STRY(grow(c, cnt_r, sizeof(uint32_t) * (H + 1) * std::max(na, 1)));
     HB_STRY(grow(c, start_r, sizeof(uint32_t) * (H + 1) * std::max(na, 1)));
@@ -329,7 +329,6 @@ extern "C" hb_status hb_block_stream(hb_ctx *c, int64_t n_rows_s, int32_t n_cols
         if (c->groups[g].kind == OP_JAC) gram_words += max_str + 16;
     }
     HB_STRY(grow(c, chunk_grams, sizeof(uint32_t) * gram_words));
-    HB_STRY(grow(c, codes, sizeof(uint32_t) * (size_t)(max_rows + 1)));
     HB_STRY(grow(c, flag, 16));
     HB_STRY(grow(c, c->w_jac, jac_scratch_bytes(max_rows)));
     HB_STRY(grow(c, c->w_slot_s, sizeof(uint32_t) * (size_t)(max_rows + 1)));
@@ -409,7 +408,7 @@ extern "C" hb_status hb_block_stream(hb_ctx *c, int64_t n_rows_s, int32_t n_cols
         }
         S.rec = as<uint32_t>(chunk_rec);
         S.hot = as<uint32_t>(chunk_hot);
-        HB_STRY(encode_chunk(c, S, as<unsigned int>(flag), codes, chunk_grams, gram_off));
+        HB_STRY(encode_chunk(c, S, as<unsigned int>(flag), chunk_grams, gram_off));
         // groups of the chunk against R's groups, blocks, tiles
         HB_SCUDA(cudaMemsetAsync(ctr, 0, sizeof(unsigned long long), c->stream));          // tile claims
         HB_SCUDA(cudaMemsetAsync(ctr + 3, 0, 2 * sizeof(unsigned long long), c->stream));  // blocks, overflow
@@ -496,7 +495,7 @@ extern "C" hb_status hb_block_stream(hb_ctx *c, int64_t n_rows_s, int32_t n_cols
     hb_pair *out = nullptr;
     HB_STRY(deliver(c, sorted, n_pairs, kbs, true, &out));
     cleanup();
-    Buf *tmp[] = {&tables, &cnt_r, &start_r, &chunk_rec, &chunk_hot, &chunk_grams, &codes, &flag};
+    Buf *tmp[] = {&tables, &cnt_r, &start_r, &chunk_rec, &chunk_hot, &chunk_grams, &flag};
     for (Buf *t : tmp) free_buf(c, *t);
     *pairs_out = out;
     *n_out = n_pairs;

@@ -87,11 +87,11 @@ __device__ __forceinline__ bool view_equal(const View &a, int64_t i, const View 
 // Insert every present value into an open-addressing table whose slots hold
 // (32-bit hash << 32 | representative row); the code of a value is its slot.
 // Two values share a slot only after a byte-exact comparison.
-__global__ void k_dict_insert(View v, int64_t n, uint64_t *table, uint64_t mask, uint32_t *codes) {
+__global__ void k_dict_insert(View v, int64_t n, uint64_t *table, uint64_t mask, uint32_t *codes, int64_t stride) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     if (v.valid && !v.valid[i]) {
-        codes[i] = NULL_CODE;
+        codes[i * stride] = NULL_CODE;
         return;
     }
     uint64_t h = view_hash(v, i);
@@ -104,26 +104,27 @@ __global__ void k_dict_insert(View v, int64_t n, uint64_t *table, uint64_t mask,
             uint64_t prev = atomicCAS(reinterpret_cast<unsigned long long *>(table + slot),
                                       (unsigned long long)EMPTY_SLOT, (unsigned long long)mine);
             if (prev == EMPTY_SLOT) {
-                codes[i] = (uint32_t)slot;
+                codes[i * stride] = (uint32_t)slot;
                 return;
             }
             cur = prev;
         }
         if ((uint32_t)(cur >> 32) == h32 && view_equal(v, i, v, (int64_t)(uint32_t)cur)) {
-            codes[i] = (uint32_t)slot;
+            codes[i * stride] = (uint32_t)slot;
             return;
         }
         slot = (slot + 1) & mask;
     }
-    codes[i] = NULL_CODE;   // unreachable: the table has at least twice as many slots as rows
+    codes[i * stride] = NULL_CODE;   // unreachable: the table has at least twice as many slots as rows
 }
 
 // Codes for the other relation: the slot of an equal value of the owner, or NOMATCH.
-__global__ void k_dict_probe(View v, int64_t n, View owner, const uint64_t *table, uint64_t mask, uint32_t *codes) {
+__global__ void k_dict_probe(View v, int64_t n, View owner, const uint64_t *table, uint64_t mask, uint32_t *codes,
+                             int64_t stride) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     if (v.valid && !v.valid[i]) {
-        codes[i] = NULL_CODE;
+        codes[i * stride] = NULL_CODE;
         return;
     }
     uint64_t h = view_hash(v, i);
@@ -133,17 +134,36 @@ __global__ void k_dict_probe(View v, int64_t n, View owner, const uint64_t *tabl
         uint64_t cur = table[slot];
         if (cur == EMPTY_SLOT) break;
         if ((uint32_t)(cur >> 32) == h32 && view_equal(v, i, owner, (int64_t)(uint32_t)cur)) {
-            codes[i] = (uint32_t)slot;
+            codes[i * stride] = (uint32_t)slot;
             return;
         }
         slot = (slot + 1) & mask;
     }
-    codes[i] = NOMATCH_CODE;
+    codes[i * stride] = NOMATCH_CODE;
 }
 
-__global__ void k_code_feature(const uint32_t *codes, int64_t n, uint32_t *rec, int W, int feat) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) rec[i * W + feat] = codes[i];
+// Section 5.3 data partitioning: the partition of a row's value under one
+// root-edge hash function, 32-bit FNV-1a (offset basis 2166136261, prime
+// 16777619) of the value's bytes (a string's bytes or its prefix, an int32's
+// four little-endian bytes) modulo m; a missing value is in no partition.
+__global__ void k_part_key(View v, int64_t n, uint32_t m, uint32_t *rec, int W, int word) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint32_t out = NULL_CODE;
+    if (!v.valid || v.valid[i]) {
+        uint32_t h = 2166136261u;
+        if (v.type == HB_COL_STRING) {
+            const uint8_t *p;
+            uint32_t len;
+            view_str(v, i, p, len);
+            for (uint32_t k = 0; k < len; k++) h = (h ^ p[k]) * 16777619u;
+        } else {
+            const uint32_t x = (uint32_t)v.i32[i];
+            for (int k = 0; k < 4; k++) h = (h ^ ((x >> (8 * k)) & 255u)) * 16777619u;
+        }
+        out = h % m;
+    }
+    rec[i * W + word] = out;
 }
 
 // length, byte offset and 16 saturating 8-bit counts of (byte & 15)
@@ -195,9 +215,7 @@ __device__ __forceinline__ uint32_t gram_bin(uint32_t g) { return (g * 0x9E3779B
 // 6-bit hash bin of a gram for the 64-bit presence mask
 __device__ __forceinline__ uint32_t gram_bit(uint32_t g) { return (g * 0x9E3779B1u) >> 26; }
 
-constexpr int QG_SHORT = 64;       // grams per string handled by one thread
 constexpr int QG_MID = 256;        // grams per string handled by one warp
-constexpr int QG_THREADS = 128;
 constexpr int QG_LONG_MAX = 8192;  // grams per string handled by one block
 
 // Strings are handed to the sorting threads in order of their gram count
@@ -243,8 +261,10 @@ __global__ void k_bucket_scan(const uint32_t *bucket_count, uint32_t *bucket_cur
     }
 }
 
-// order[bucket start + rank] = string: a block reserves one range per bucket
-__global__ void k_bucket_scatter(const uint32_t *cnt, int64_t n, uint32_t *bucket_cursor, uint32_t *order) {
+// ent[bucket start + rank] = (string, byte offset, length, first gram slot):
+// a block reserves one range per bucket
+__global__ void k_bucket_scatter(const uint32_t *cnt, const uint32_t *off, const uint32_t *gstart, int64_t n,
+                                 uint32_t *bucket_cursor, uint4 *ent) {
     __shared__ uint32_t h[QG_BUCKETS], base[QG_BUCKETS];
     for (int t = threadIdx.x; t < QG_BUCKETS; t += blockDim.x) h[t] = 0;
     __syncthreads();
@@ -258,7 +278,10 @@ __global__ void k_bucket_scatter(const uint32_t *cnt, int64_t n, uint32_t *bucke
     for (int t = threadIdx.x; t < QG_BUCKETS; t += blockDim.x)
         base[t] = h[t] ? atomicAdd(&bucket_cursor[t], h[t]) : 0u;
     __syncthreads();
-    if (i < n) order[base[b] + rank] = (uint32_t)i;
+    if (i < n) {
+        const uint32_t a = off[i];
+        ent[base[b] + rank] = make_uint4((uint32_t)i, a, off[i + 1] - a, gstart[i]);
+    }
 }
 
 __device__ void write_gram_feature(uint32_t *r, uint32_t ucount, uint32_t start, const uint32_t *g) {
@@ -279,98 +302,212 @@ __device__ void write_gram_feature(uint32_t *r, uint32_t ucount, uint32_t start,
     r[FEAT_JAC_MASK + 1] = (uint32_t)(mask >> 32);
 }
 
-// bitonic sorting network over N registers (every index is a compile-time
-// constant once the loops are unrolled)
-template <int N>
-__device__ __forceinline__ void sort_net(uint32_t (&v)[N]) {
+// One string's grams sorted by a group of G lanes (G = 4, 8, 16 or 32, two
+// grams per lane, up to 2G grams): a bitonic network over the 2G elements, the
+// element e = 2 * (lane in group) + j; partners at a distance of two or more
+// elements sit in another lane of the group (a shuffle), at distance one in the
+// same lane.  The unique grams are compacted with ballots and written in
+// order; their 32 bin counts (at most 64 grams, so no 8-bit count saturates)
+// and 64-bit presence mask are summed in the warp's shared words.  e is the
+// string's entry (id, byte offset, length, first gram slot), by the lane's
+// bytes 2gl .. 2gl+4 of it (zero past the end), both loaded beforehand.
+template <int G>
+__device__ __forceinline__ void grams_group(int q, bool has, uint4 e, const uint32_t (&by)[5], uint32_t *grams,
+                                            uint32_t *rec, int W, int feat, uint32_t *acc) {
+    const int lane = threadIdx.x & 31;
+    const int gl = lane & (G - 1), gi = lane / G;
+    const uint32_t i = e.x, gs = e.w;
+    const uint32_t g = has ? e.z - (uint32_t)q + 1u : 0u;   // strings of this class have 1..2G grams
+    uint32_t v0 = 0, v1 = 0;
 #pragma unroll
-    for (int size = 2; size <= N; size <<= 1)
-#pragma unroll
-        for (int stride = size / 2; stride > 0; stride >>= 1)
-#pragma unroll
-            for (int i = 0; i < N; i++) {
-                const int j = i ^ stride;
-                if (j > i) {
-                    const bool up = (i & size) == 0;
-                    const uint32_t a = v[i], b = v[j];
-                    const uint32_t lo = min(a, b), hi = max(a, b);
-                    v[i] = up ? lo : hi;
-                    v[j] = up ? hi : lo;
-                }
-            }
-}
-
-// The g (<= N) grams of one string in registers (a rolling window: the gram at
-// k is bytes k .. k+q-1, packed big-endian), padded with 0xFFFFFFFF, sorted by
-// the network; the unique ones are written at dst and counted in 32 bins.
-template <int N>
-__device__ __forceinline__ void grams_sorted(const uint8_t *p, uint32_t g, int q, uint32_t *dst, uint32_t *r,
-                                             uint32_t start) {
-    const uint32_t gmask = q >= 4 ? 0xFFFFFFFFu : ((1u << (8 * q)) - 1u);
-    uint32_t win = 0;
-    if (g > 0)
-        for (int t0 = 0; t0 < q - 1; t0++) win = (win << 8) | p[t0];
-    uint32_t v[N];
-#pragma unroll
-    for (int k = 0; k < N; k++) {
-        if ((uint32_t)k < g) win = ((win << 8) | p[k + q - 1]) & gmask;
-        v[k] = (uint32_t)k < g ? win : 0xFFFFFFFFu;
-    }
-    sort_net<N>(v);
-    uint32_t u = 0;
-    uint32_t sig[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    uint64_t mask = 0;
-#pragma unroll
-    for (int k = 0; k < N; k++) {
-        if ((uint32_t)k < g && (k == 0 || v[k] != v[k > 0 ? k - 1 : 0])) {
-            dst[u++] = v[k];
-            const uint32_t bin = gram_bin(v[k]);
-            const uint32_t word = bin >> 2, sh = (bin & 3u) * 8u;
-            const uint32_t cur = (sig[word] >> sh) & 255u;
-            if (cur < 255u) sig[word] += 1u << sh;
-            mask |= 1ull << gram_bit(v[k]);
+    for (int t = 0; t < 4; t++) {
+        if (t < q) {
+            v0 = (v0 << 8) | by[t];
+            v1 = (v1 << 8) | by[t + 1];
         }
     }
-    r[0] = u;
-    r[1] = start;
+    const uint32_t k0 = 2u * gl, k1 = k0 + 1u;
+    v0 = k0 < g ? v0 : 0xFFFFFFFFu;
+    v1 = k1 < g ? v1 : 0xFFFFFFFFu;
 #pragma unroll
-    for (int k = 0; k < 8; k++) r[2 + k] = sig[k];
-    r[FEAT_JAC_MASK] = (uint32_t)mask;
-    r[FEAT_JAC_MASK + 1] = (uint32_t)(mask >> 32);
+    for (int size = 2; size <= 2 * G; size <<= 1) {
+        const bool up = (k0 & (uint32_t)size) == 0u;   // the same for both elements once size >= 2
+#pragma unroll
+        for (int stride = size / 2; stride > 0; stride >>= 1) {
+            if (stride == 1) {
+                const uint32_t lo = min(v0, v1), hi = max(v0, v1);
+                v0 = up ? lo : hi;
+                v1 = up ? hi : lo;
+            } else {
+                const int ls = stride >> 1;
+                const uint32_t p0 = __shfl_xor_sync(0xffffffffu, v0, ls);
+                const uint32_t p1 = __shfl_xor_sync(0xffffffffu, v1, ls);
+                const bool keep_min = ((gl & ls) == 0) == up;
+                v0 = keep_min ? min(v0, p0) : max(v0, p0);
+                v1 = keep_min ? min(v1, p1) : max(v1, p1);
+            }
+        }
+    }
+    // unique flags: an element differs from the one before it (lane gl-1's second)
+    const uint32_t prev = __shfl_up_sync(0xffffffffu, v1, 1);
+    const bool u0 = k0 < g && (gl == 0 || v0 != prev);
+    const bool u1 = k1 < g && v1 != v0;
+    const uint32_t b0 = __ballot_sync(0xffffffffu, u0), b1 = __ballot_sync(0xffffffffu, u1);
+    const uint32_t gbits = (G == 32 ? 0xffffffffu : ((1u << G) - 1u)) << (gi * G);
+    const uint32_t lower = gbits & ((1u << lane) - 1u);
+    const uint32_t pos0 = __popc(b0 & lower) + __popc(b1 & lower);
+    const uint32_t ucount = __popc(b0 & gbits) + __popc(b1 & gbits);
+    if (u0) grams[gs + pos0] = v0;
+    if (u1) grams[gs + pos0 + (u0 ? 1u : 0u)] = v1;
+    // feature words: 8 words of 32 8-bit bin counts, then the 64-bit mask
+    uint32_t *sh = acc + gi * 10;
+    for (int w = gl; w < 10; w += G) sh[w] = 0u;
+    __syncwarp();
+    if (u0) {
+        const uint32_t bin = gram_bin(v0), bit = gram_bit(v0);
+        atomicAdd(sh + (bin >> 2), 1u << ((bin & 3u) * 8u));
+        atomicOr(sh + 8 + (bit >> 5), 1u << (bit & 31u));
+    }
+    if (u1) {
+        const uint32_t bin = gram_bin(v1), bit = gram_bit(v1);
+        atomicAdd(sh + (bin >> 2), 1u << ((bin & 3u) * 8u));
+        atomicOr(sh + 8 + (bit >> 5), 1u << (bit & 31u));
+    }
+    __syncwarp();
+    if (has) {
+        uint32_t *r = rec + (size_t)i * W + feat;
+        for (int w = gl; w < FEAT_JAC_WORDS; w += G) r[w] = w == 0 ? ucount : w == 1 ? gs : sh[w - 2];
+    }
+    __syncwarp();
 }
 
-// Strings with up to 64 grams: one thread per string sorts its grams in
-// registers with the smallest network that holds them (strings arrive ordered
-// by gram count, so a warp's threads take the same network).
-__global__ void __launch_bounds__(QG_THREADS) k_grams_short(const uint8_t *bytes, const uint32_t *off,
-                                                           const uint8_t *valid, int64_t n, int q,
-                                                           const uint32_t *order, const uint32_t *gstart,
-                                                           uint32_t *grams, uint32_t *rec, int W, int feat,
-                                                           uint32_t *mid_list, unsigned int *n_mid,
-                                                           uint32_t *long_list, unsigned int *n_long) {
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= n) return;
-    const int64_t i = order[t];
-    uint32_t *r = rec + i * W + feat;
-    if (valid && !valid[i]) {
-        r[0] = NULL_LEN;
-        r[1] = 0;
-        for (int k = 2; k < FEAT_JAC_WORDS; k++) r[k] = 0;
-        return;
+// Strings in bucket order (by gram count), in six classes: no grams (null or
+// shorter than q; a thread each), 1-8, 9-16, 17-32 and 33-64 grams (a group of
+// 4, 8, 16 or 32 lanes each), and more than 64 grams (a thread each, handed to
+// the per-warp and per-block kernels).  bucket_end[b] is the end of bucket b in
+// the order.  Warps walk the classes' groups with a grid stride; the entries
+// of the group two steps ahead and the bytes of the next are loaded before a
+// group is sorted, so the two dependent loads of a string overlap the sorting.
+constexpr int QG_COOP_THREADS = 256;
+
+struct CoopStep {
+    int c;          // class (-1: past the end)
+    uint32_t pos;   // this lane's entry
+    bool has;       // pos lies in the class
+};
+
+__device__ __forceinline__ CoopStep coop_step(uint32_t w, const uint32_t (&lo)[7], const uint32_t (&wstart)[7],
+                                              int lane) {
+    CoopStep st{-1, 0u, false};
+    if (w >= wstart[6]) return st;
+    int c = 0;
+#pragma unroll
+    for (int k = 1; k < 6; k++) c += w >= wstart[k] ? 1 : 0;
+    uint32_t lo_c = 0, hi_c = 0, ws_c = 0;
+#pragma unroll
+    for (int k = 0; k < 6; k++)
+        if (k == c) {
+            lo_c = lo[k];
+            hi_c = lo[k + 1];
+            ws_c = wstart[k];
+        }
+    const uint32_t wc = w - ws_c;
+    uint32_t pos;
+    if (c == 0 || c == 5) pos = lo_c + wc * 32u + (uint32_t)lane;
+    else if (c == 1) pos = lo_c + wc * 8u + (uint32_t)(lane >> 2);
+    else if (c == 2) pos = lo_c + wc * 4u + (uint32_t)(lane >> 3);
+    else if (c == 3) pos = lo_c + wc * 2u + (uint32_t)(lane >> 4);
+    else pos = lo_c + wc;
+    st.c = c;
+    st.pos = pos;
+    st.has = pos < hi_c;
+    return st;
+}
+
+__device__ __forceinline__ uint4 coop_entry(const CoopStep &st, const uint4 *ent) {
+    return st.has ? ent[st.pos] : make_uint4(0u, 0u, 0u, 0u);
+}
+
+// bytes 2gl .. 2gl+4 of the lane's string (group classes only)
+__device__ __forceinline__ void coop_bytes(const CoopStep &st, uint4 e, const uint8_t *bytes, int q,
+                                           uint32_t (&by)[5]) {
+    const int lane = threadIdx.x & 31;
+    const int gl = st.c >= 1 && st.c <= 4 ? (lane & ((4 << (st.c - 1)) - 1)) : 0;
+    const bool grp = st.has && st.c >= 1 && st.c <= 4;
+#pragma unroll
+    for (int t = 0; t < 5; t++) {
+        const uint32_t k = 2u * gl + (uint32_t)t;
+        by[t] = (grp && t <= q && k < e.z) ? (uint32_t)bytes[e.y + k] : 0u;
     }
-    const uint32_t a = off[i], len = off[i + 1] - a;
-    const uint32_t g = len >= (uint32_t)q ? len - (uint32_t)q + 1u : 0u;
-    if (g > (uint32_t)QG_SHORT) {
-        if (g <= (uint32_t)QG_MID) mid_list[atomicAdd(n_mid, 1u)] = (uint32_t)i;
-        else long_list[atomicAdd(n_long, 1u)] = (uint32_t)i;
-        return;
+}
+
+__global__ void __launch_bounds__(QG_COOP_THREADS) k_grams_coop(const uint8_t *bytes, const uint8_t *valid, int64_t n,
+                                                                int q, const uint4 *ent, const uint32_t *bucket_end,
+                                                                uint32_t *grams, uint32_t *rec, int W, int feat,
+                                                                uint32_t *mid_list, unsigned int *n_mid,
+                                                                uint32_t *long_list, unsigned int *n_long) {
+    __shared__ uint32_t acc_all[QG_COOP_THREADS / 32][80];
+    uint32_t *acc = acc_all[threadIdx.x >> 5];
+    const int lane = threadIdx.x & 31;
+    // class c covers order positions [lo[c], lo[c+1]) and takes per[c] strings per warp
+    uint32_t lo[7];
+    lo[0] = 0;
+    lo[1] = bucket_end[0];
+    lo[2] = bucket_end[8];
+    lo[3] = bucket_end[16];
+    lo[4] = bucket_end[32];
+    lo[5] = bucket_end[64];
+    lo[6] = (uint32_t)n;
+    const uint32_t per[6] = {32, 8, 4, 2, 1, 32};
+    uint32_t wstart[7];
+    wstart[0] = 0;
+#pragma unroll
+    for (int c = 0; c < 6; c++) wstart[c + 1] = wstart[c] + (lo[c + 1] - lo[c] + per[c] - 1) / per[c];
+    const uint32_t nw = (uint32_t)((gridDim.x * blockDim.x) >> 5);
+    uint32_t w = (uint32_t)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    CoopStep A = coop_step(w, lo, wstart, lane);
+    uint4 eA = coop_entry(A, ent);
+    CoopStep B = coop_step(w + nw, lo, wstart, lane);
+    uint4 eB = coop_entry(B, ent);
+    uint32_t bA[5];
+    coop_bytes(A, eA, bytes, q, bA);
+    while (A.c >= 0) {
+        w += nw;
+        const CoopStep C = coop_step(w + nw, lo, wstart, lane);
+        const uint4 eC = coop_entry(C, ent);
+        uint32_t bB[5];
+        coop_bytes(B, eB, bytes, q, bB);
+        if (A.c == 0) {
+            if (A.has) {
+                const uint32_t i = eA.x;
+                uint32_t *r = rec + (size_t)i * W + feat;
+                const bool null = valid && !valid[i];
+                r[0] = null ? NULL_LEN : 0u;
+                r[1] = null ? 0u : eA.w;
+                for (int k = 2; k < FEAT_JAC_WORDS; k++) r[k] = 0u;
+            }
+        } else if (A.c == 5) {
+            if (A.has) {
+                const uint32_t g = eA.z - (uint32_t)q + 1u;
+                if (g <= (uint32_t)QG_MID) mid_list[atomicAdd(n_mid, 1u)] = eA.x;
+                else long_list[atomicAdd(n_long, 1u)] = eA.x;
+            }
+        } else if (A.c == 1) {
+            grams_group<4>(q, A.has, eA, bA, grams, rec, W, feat, acc);
+        } else if (A.c == 2) {
+            grams_group<8>(q, A.has, eA, bA, grams, rec, W, feat, acc);
+        } else if (A.c == 3) {
+            grams_group<16>(q, A.has, eA, bA, grams, rec, W, feat, acc);
+        } else {
+            grams_group<32>(q, A.has, eA, bA, grams, rec, W, feat, acc);
+        }
+        A = B;
+        eA = eB;
+#pragma unroll
+        for (int t = 0; t < 5; t++) bA[t] = bB[t];
+        B = C;
+        eB = eC;
     }
-    const uint8_t *p = bytes + a;
-    uint32_t *dst = grams + gstart[i];
-    if (g <= 8) grams_sorted<8>(p, g, q, dst, r, gstart[i]);
-    else if (g <= 16) grams_sorted<16>(p, g, q, dst, r, gstart[i]);
-    else if (g <= 32) grams_sorted<32>(p, g, q, dst, r, gstart[i]);
-    else grams_sorted<64>(p, g, q, dst, r, gstart[i]);
 }
 
 // Strings with 65..256 grams: one warp per string, bitonic sort in the warp's
@@ -514,10 +651,18 @@ struct HotMap {
     int32_t w[64];
 };
 
+// A thread per (row, hot word): a block holds whole rows, so the hot records
+// are written contiguously and each row's record is read by neighbouring lanes.
 __global__ void k_hot_pack(const uint32_t *rec, int W, int64_t n, uint32_t *hot, int HW, HotMap map) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    for (int h = 0; h < HW; h++) hot[i * HW + h] = map.w[h] >= 0 ? rec[i * W + map.w[h]] : 0u;
+    __shared__ int32_t m[64];
+    if (threadIdx.x < 64) m[threadIdx.x] = map.w[threadIdx.x];
+    __syncthreads();
+    const int rpb = (int)blockDim.x / HW;
+    const int lr = (int)threadIdx.x / HW, h = (int)threadIdx.x - lr * HW;
+    const int64_t i = (int64_t)blockIdx.x * rpb + lr;
+    if (lr >= rpb || i >= n) return;
+    const int w = m[h];
+    hot[i * HW + h] = w >= 0 ? rec[i * W + w] : 0u;
 }
 
 // ---- constants: one flag word per (column, constant) ----
@@ -692,20 +837,20 @@ inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t
 
 }  // namespace
 
-void dict_build(const DevCol &c, int prefix, uint64_t *table, uint64_t cap, uint32_t *codes, cudaStream_t s) {
+void dict_build(const DevCol &c, int prefix, uint64_t *table, uint64_t cap, uint32_t *codes, int64_t stride,
+                cudaStream_t s) {
     cudaMemsetAsync(table, 0xFF, cap * sizeof(uint64_t), s);
     if (c.n == 0) return;
     HB_LAUNCHED(1);
     k_dict_insert<<<blocks_for(c.n, ENC_THREADS), ENC_THREADS, 0, s>>>(make_view(c, prefix), c.n, table, cap - 1,
-                                                                      codes);
+                                                                      codes, stride);
 }
-
 void dict_probe(const DevCol &probe, int prefix, const DevCol &owner, int owner_prefix, const uint64_t *table,
-                uint64_t cap, uint32_t *codes, cudaStream_t s) {
+                uint64_t cap, uint32_t *codes, int64_t stride, cudaStream_t s) {
     if (probe.n == 0) return;
     HB_LAUNCHED(1);
     k_dict_probe<<<blocks_for(probe.n, ENC_THREADS), ENC_THREADS, 0, s>>>(
-        make_view(probe, prefix), probe.n, make_view(owner, owner_prefix), table, cap - 1, codes);
+        make_view(probe, prefix), probe.n, make_view(owner, owner_prefix), table, cap - 1, codes, stride);
 }
 
 void hot_pack(const uint32_t *rec, int W, int64_t n, uint32_t *hot, int HW, const int32_t *map, cudaStream_t s) {
@@ -713,13 +858,14 @@ void hot_pack(const uint32_t *rec, int W, int64_t n, uint32_t *hot, int HW, cons
     HotMap m;
     for (int h = 0; h < 64; h++) m.w[h] = h < HW ? map[h] : -1;
     HB_LAUNCHED(1);
-    k_hot_pack<<<blocks_for(n, ENC_THREADS), ENC_THREADS, 0, s>>>(rec, W, n, hot, HW, m);
+    const int rpb = HW >= ENC_THREADS ? 1 : ENC_THREADS / HW;   // rows per block
+    k_hot_pack<<<(unsigned)((n + rpb - 1) / rpb), (unsigned)(rpb * HW), 0, s>>>(rec, W, n, hot, HW, m);
 }
 
-void code_feature(const uint32_t *codes, int64_t n, uint32_t *rec, int W, int feat, cudaStream_t s) {
-    if (n == 0) return;
+void part_feature(const DevCol &c, int prefix, uint32_t m, uint32_t *rec, int W, int word, cudaStream_t s) {
+    if (c.n == 0) return;
     HB_LAUNCHED(1);
-    k_code_feature<<<blocks_for(n, ENC_THREADS), ENC_THREADS, 0, s>>>(codes, n, rec, W, feat);
+    k_part_key<<<blocks_for(c.n, ENC_THREADS), ENC_THREADS, 0, s>>>(make_view(c, prefix), c.n, m, rec, W, word);
 }
 
 void ed_features(const DevCol &c, uint32_t *rec, int W, int feat, cudaStream_t s) {
@@ -792,7 +938,7 @@ void abs_feature(const DevCol &c, uint32_t *rec, int W, int feat, cudaStream_t s
 }
 
 size_t jac_scratch_bytes(int64_t n) {
-    return (size_t)(n + 1) * 4 * 5 + 2 * QG_BUCKETS * 4 + scan_tmp_bytes(n) + 4096;
+    return (size_t)(n + 1) * 4 * 4 + (size_t)(n + 1) * 16 + 16 + 2 * QG_BUCKETS * 4 + scan_tmp_bytes(n) + 4096;
 }
 
 // scratch: jac_scratch_bytes(n); grams: capacity >= nbytes of the column (one gram per byte at most)
@@ -803,9 +949,9 @@ void jac_features_impl(const DevCol &c, int q, uint32_t *rec, int W, int feat, u
     uint32_t *cnt = static_cast<uint32_t *>(scratch);
     uint32_t *gstart = cnt + (n + 1);
     uint32_t *long_list = gstart + (n + 1);
-    uint32_t *order = long_list + (n + 1);
-    uint32_t *mid_list = order + (n + 1);
-    uint32_t *bucket_count = mid_list + (n + 1);
+    uint32_t *mid_list = long_list + (n + 1);
+    uint4 *ent = reinterpret_cast<uint4 *>((reinterpret_cast<uintptr_t>(mid_list + (n + 1)) + 15) & ~uintptr_t(15));
+    uint32_t *bucket_count = reinterpret_cast<uint32_t *>(ent + (n + 1));
     uint32_t *bucket_cursor = bucket_count + QG_BUCKETS;
     unsigned int *n_long = bucket_cursor + QG_BUCKETS;
     unsigned int *n_mid = n_long + 1;
@@ -814,12 +960,11 @@ void jac_features_impl(const DevCol &c, int q, uint32_t *rec, int W, int feat, u
     cudaMemsetAsync(bucket_count, 0, sizeof(uint32_t) * (2 * QG_BUCKETS + 2), s);
     HB_LAUNCHED(4);
     k_gram_counts<<<blocks_for(n, ENC_THREADS), ENC_THREADS, 0, s>>>(c.off, c.valid, n, q, cnt, bucket_count);
-    k_bucket_scan<<<1, 32, 0, s>>>(bucket_count, bucket_cursor);
-    k_bucket_scatter<<<blocks_for(n, ENC_THREADS), ENC_THREADS, 0, s>>>(cnt, n, bucket_cursor, order);
     scan_exclusive_u32(cnt, gstart, n, nullptr, stmp, 0, s);
-    k_grams_short<<<blocks_for(n, QG_THREADS), QG_THREADS, 0, s>>>(c.bytes, c.off, c.valid, n, q, order, gstart,
-                                                                  grams, rec, W, feat, mid_list, n_mid, long_list,
-                                                                  n_long);
+    k_bucket_scan<<<1, 32, 0, s>>>(bucket_count, bucket_cursor);
+    k_bucket_scatter<<<blocks_for(n, ENC_THREADS), ENC_THREADS, 0, s>>>(cnt, c.off, gstart, n, bucket_cursor, ent);
+    k_grams_coop<<<(unsigned)(n_sm * 8), QG_COOP_THREADS, 0, s>>>(c.bytes, c.valid, n, q, ent, bucket_cursor, grams,
+                                                                  rec, W, feat, mid_list, n_mid, long_list, n_long);
     HB_LAUNCHED(1);
     k_grams_mid<<<(unsigned)(n_sm * 8), 256, 0, s>>>(c.bytes, c.off, q, gstart, grams, rec, W, feat, mid_list, n_mid);
     HB_LAUNCHED(1);

@@ -319,6 +319,7 @@ __device__ __forceinline__ bool run_program(const EvalParams &P, uint64_t alive,
     // profile mode (logging only): evaluate every predicate the initially alive
     // MDs hold, without early exit; the verdict is unchanged
     const bool prof = LOG && P.profile;
+    alive &= ~P.group_mds;
     const uint64_t alive0 = alive;
     bool hit = (alive & P.eqonly) != 0;
     if (hit && !prof) return true;
@@ -700,7 +701,7 @@ __global__ void __launch_bounds__(EV_THREADS, 4) k_eval(const __grid_constant__ 
     const uint32_t nb = *P.n_blocks;
     const uint64_t total = P.tile_prefix[nb];
     const unsigned lt = (1u << lane) - 1u;
-    const uint32_t allkeys = (P.n_eq >= 32) ? 0xffffffffu : ((1u << P.n_eq) - 1u);
+    const uint32_t allkeys = P.keymask;
     const uint32_t *rec_c = P.self_join ? P.rec_r : P.rec_s;
     const uint32_t *hot_c = P.self_join ? P.hot_r : P.hot_s;
     unsigned long long cand = 0, exam = 0;
@@ -725,7 +726,7 @@ __global__ void __launch_bounds__(EV_THREADS, 4) k_eval(const __grid_constant__ 
             const bool diag = P.self_join && ti == tj;
             const uint32_t m = B.md;
             const uint64_t mbit = 1ull << m;
-            const uint64_t below = mbit - 1ull;
+            const uint64_t below = (mbit - 1ull) & P.owner_mds;
             const uint32_t okeys = allkeys & ~(uint32_t)P.eqset[m];
             const uint64_t base = P.base_alive[m];
             const int nbase = P.base_nops[m];
@@ -990,7 +991,7 @@ __global__ void __launch_bounds__(EV_THREADS, 4) k_eval(const __grid_constant__ 
                     {
                         const uint64_t alive = alive_of(P, lut, E);
                         keep = (alive & P.eqonly) != 0;
-                        for (uint64_t a = alive; a && !keep; a &= a - 1) {
+                        for (uint64_t a = alive & ~P.group_mds; a && !keep; a &= a - 1) {
                             const int j = __ffsll((long long)a) - 1;
                             const int o0 = P.screen_op[j][0], o1 = P.screen_op[j][1];
                             keep = (o0 == 255 || screen(P.ops[o0], hr, hc, T)) &&

@@ -70,7 +70,8 @@ class hb_plan_info(ctypes.Structure):
                 ("md_order", ctypes.c_int32 * MAX_MDS), ("sp", ctypes.c_double * MAX_PREDS),
                 ("cost", ctypes.c_double * MAX_PREDS), ("pred_md", ctypes.c_int32 * MAX_PREDS),
                 ("tile", ctypes.c_int32), ("n_mds", ctypes.c_int32), ("record_words", ctypes.c_int32),
-                ("hot_words", ctypes.c_int32)]
+                ("hot_words", ctypes.c_int32), ("n_branches", ctypes.c_int32),
+                ("branch_pred", ctypes.c_int32 * MAX_MDS)]
 
 
 class hb_stats(ctypes.Structure):
@@ -104,7 +105,7 @@ EXPORTS = ["hb_create", "hb_destroy", "hb_last_error", "hb_version", "hb_load_ta
            "hb_get_cost_model", "hb_set_cost_model", "hb_mlp_forward", "hb_mlp_forward_bf16", "hb_mlp_backward",
            "hb_mlp_backward_noalloc", "hb_adam_step", "hb_probe_int_issue", "hb_time_pairs",
            "hb_pair_model_forward", "hb_pair_model_backward", "hb_train_pair_model", "hb_tile_log",
-           "hb_train_tile_model", "hb_set_tile_model", "hb_get_tile_model", "hb_batch_tile"]
+           "hb_train_tile_model", "hb_set_tile_model", "hb_get_tile_model", "hb_batch_tile", "hb_set_partitions"]
 
 _lib = None
 
@@ -142,6 +143,7 @@ def lib():
         "hb_train_tile_model": (st, [P, i32, P, P, i32, ctypes.c_float, ctypes.c_uint64, P]),
         "hb_set_tile_model": (st, [P, P]), "hb_get_tile_model": (st, [P, P]),
         "hb_batch_tile": (st, [P, P, P, P]),
+        "hb_set_partitions": (st, [P, ctypes.c_uint32]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -305,6 +307,11 @@ class Context:
         _check(lib().hb_plan(self._h, PLAN_MODES[mode] if isinstance(mode, str) else mode, ctypes.byref(info)),
                "hb_plan")
         return info
+
+    def set_partitions(self, m):
+        """Root-edge hash partitioning (Section 5.3) with m partitions per hash
+        function; 0 restores exact equality groups.  Applies from the next plan."""
+        _check(lib().hb_set_partitions(self._h, int(m)), "hb_set_partitions")
 
     # ---- blocking
     def block(self):
