@@ -406,6 +406,40 @@ def measure_all_pairs(args):
             "timing": "CUDA events around the evaluation kernel, median"}
 
 
+def measure_partitions(args, table, mds):
+    """Root-edge hash partitioning (Section 5.3) on the step's own table and
+    rules: m partitions per root-edge hash function instead of exact equality
+    groups (m = 0).  The pair sets must be equal; the candidate count and the
+    evaluation time show what coarser units cost on one GPU."""
+    import statistics as st_
+    from paper_2410_04349_gb300 import hb
+    runs = []
+    exact = None
+    for m in (0, 1 << 20, 1 << 12):
+        with hb.Context(device=0) as ctx:
+            ctx.load_table(0, table.n_rows, table.columns)
+            for md in mds:
+                ctx.add_md(md)
+            ctx.set_partitions(m)
+            info = ctx.plan("rule_data")
+            for _ in range(2):
+                pairs = ctx.block()
+            ev = []
+            for _ in range(max(1, min(args.steps, 3))):
+                pairs = ctx.block()
+                ev.append(ctx.stats()["ms_eval"])
+            st = ctx.stats()
+        if exact is None:
+            exact = pairs
+        ms = st_.median(ev)
+        runs.append({"m": m, "branches": int(info.n_branches), "candidate_pairs": st["candidate_pairs"],
+                     "eval_ms": ms, "value": st["candidate_pairs"] / (ms / 1e3),
+                     "identical_pair_sets": bool(np.array_equal(pairs, exact))})
+    return {"workload": f"the step's table and rules ({table.n_rows} tuples, {len(mds)} MDs); m = 0: exact "
+                        "equality groups, else m partitions per root-edge hash function", "unit": UNIT,
+            "runs": runs, "timing": "CUDA events around the evaluation kernel, median"}
+
+
 def run_c4(args):
     d = compare_c4(args)
     line = _line(METRIC, d["batched"]["value"], UNIT, args, d["batched"]["ms_per_step"], d["workload"],
@@ -637,6 +671,7 @@ def main():
         line["learned_vs_plain"] = compare_c5(args)
         line["batched_vs_per_job"] = compare_c4(args)
         line["all_pairs"] = measure_all_pairs(args)
+        line["partitions"] = measure_partitions(args, table, mds)
     if rank == 0 and world == 1 and not args.no_cpu:
         rate, dt, cand, threads = cpu_oracle_rate(table, mds, args.cpu_sample_rows)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",

@@ -65,7 +65,8 @@ typedef enum {
     HB_ERR_STATE = -4,          /* call out of order (e.g. hb_block before hb_load_table) */
     HB_ERR_OVERFLOW = -5,       /* a fixed-capacity output could not hold the result */
     HB_ERR_DEVICE_TIMEOUT = -6, /* a bounded device-side wait gave up */
-    HB_ERR_INTERNAL = -7
+    HB_ERR_INTERNAL = -7,
+    HB_ERR_BOUNDS = -8          /* checked build (libhb_checked.so) only: an index left its buffer (message names the site) */
 } hb_status;
 
 typedef enum { HB_COL_STRING = 0, HB_COL_INT32 = 1, HB_COL_FP32 = 2 } hb_coltype;

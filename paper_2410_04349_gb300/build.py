@@ -13,6 +13,9 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libhb.so")
+# checked variant: device-side bounds checks that record a site instead of touching memory out of range
+BUILD_CHECKED = os.path.join(HERE, "_build_checked")
+LIB_CHECKED = os.path.join(HERE, "libhb_checked.so")
 
 SOURCES = ["hb_api.cu", "hb_learn.cu", "k_sort.cu", "k_encode.cu", "k_block.cu", "k_eval.cu", "k_stats.cu",
            "k_mlp.cu", "planner.cpp", "hb_batch.cu", "hb_stream.cu", "k_probe.cu"]
@@ -26,22 +29,24 @@ def nvcc() -> str:
     raise RuntimeError("nvcc not found")
 
 
-def _flags(verbose_ptx: bool):
+def _flags(verbose_ptx: bool, checked: bool):
     f = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "-I", INCLUDE, "-I", CSRC, "--expt-relaxed-constexpr"] + ARCH
+    if checked:
+        f += ["-DHB_CHECKED"]
     if verbose_ptx:
         f += ["-Xptxas", "-v"]
     return f
 
 
-def _compile(src: str, verbose_ptx: bool) -> str:
-    obj = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")
+def _compile(src: str, verbose_ptx: bool, checked: bool) -> str:
+    obj = os.path.join(BUILD_CHECKED if checked else BUILD, os.path.splitext(src)[0] + ".o")
     path = os.path.join(CSRC, src)
     deps = [path] + [os.path.join(CSRC, h) for h in os.listdir(CSRC) if h.endswith(".h")] + \
         [os.path.join(INCLUDE, "hb.h")]
     if os.path.exists(obj) and not verbose_ptx and all(os.path.getmtime(obj) >= os.path.getmtime(d) for d in deps):
         return obj
-    cmd = [nvcc()] + _flags(verbose_ptx) + ["-c", path, "-o", obj + ".tmp"]
+    cmd = [nvcc()] + _flags(verbose_ptx, checked) + ["-c", path, "-o", obj + ".tmp"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")
@@ -51,18 +56,30 @@ def _compile(src: str, verbose_ptx: bool) -> str:
     return obj
 
 
-def build(verbose_ptx: bool = False) -> str:
-    os.makedirs(BUILD, exist_ok=True)
-    with cf.ThreadPoolExecutor(max_workers=min(len(SOURCES), os.cpu_count() or 4)) as ex:
-        objs = list(ex.map(lambda s: _compile(s, verbose_ptx), SOURCES))
-    if os.path.exists(LIB) and all(os.path.getmtime(LIB) >= os.path.getmtime(o) for o in objs):
-        return LIB
-    tmp = LIB + f".tmp{os.getpid()}"
+def _link(objs, lib) -> str:
+    if os.path.exists(lib) and all(os.path.getmtime(lib) >= os.path.getmtime(o) for o in objs):
+        return lib
+    tmp = lib + f".tmp{os.getpid()}"
     cmd = [nvcc()] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
+    os.replace(tmp, lib)
+    return lib
+
+
+def build(verbose_ptx: bool = False, checked: bool = True) -> str:
+    """libhb.so, and with checked=True also libhb_checked.so (compiled in the same pool)."""
+    variants = [False, True] if checked else [False]
+    os.makedirs(BUILD, exist_ok=True)
+    if checked:
+        os.makedirs(BUILD_CHECKED, exist_ok=True)
+    jobs = [(src, v) for v in variants for src in SOURCES]
+    with cf.ThreadPoolExecutor(max_workers=min(len(jobs), os.cpu_count() or 4)) as ex:
+        objs = list(ex.map(lambda j: _compile(j[0], verbose_ptx and not j[1], j[1]), jobs))
+    _link(objs[:len(SOURCES)], LIB)
+    if checked:
+        _link(objs[len(SOURCES):], LIB_CHECKED)
     return LIB
 
 

@@ -92,6 +92,7 @@ static void free_side_encoding(hb_ctx *c, SideData &s) {
     for (auto g : s.grams)
         if (g) cudaFreeAsync(g, c->stream);
     s.grams.clear();
+    s.gram_len.clear();
     s.encoded = false;
 }
 
@@ -121,6 +122,23 @@ static void invalidate_encoding(hb_ctx *c) {
     free_side_encoding(c, c->side[0]);
     free_side_encoding(c, c->side[1]);
     free_dicts(c);
+}
+
+// checked builds: a site recorded by a device-side check fails the call
+// (ordinary builds record nothing and return at once)
+hb_status check_bounds(hb_ctx *c, const char *what) {
+#ifdef HB_CHECKED
+    HB_CUDA(cudaStreamSynchronize(c->stream));
+    const unsigned int e = checked_error_eval(), n = checked_error_encode(), b = checked_error_block();
+    const unsigned int site = e ? e : n ? n : b;
+    if (site)
+        return fail(HB_ERR_BOUNDS, std::string(what) + ": an index left its buffer at checked site " +
+                                       std::to_string(site));
+#else
+    (void)c;
+    (void)what;
+#endif
+    return HB_OK;
 }
 
 hb_status dmalloc(hb_ctx *c, void **p, size_t bytes) {
@@ -218,7 +236,11 @@ static hb_status copy_in(hb_ctx *c, void *dst, const void *src, size_t bytes, bo
 
 // ===================================================================== context
 extern "C" const char *hb_last_error(void) { return g_err.c_str(); }
+#ifdef HB_CHECKED
+extern "C" const char *hb_version(void) { return "libhb 0.1 (sm_103a, checked)"; }
+#else
 extern "C" const char *hb_version(void) { return "libhb 0.1 (sm_103a)"; }
+#endif
 
 extern "C" hb_status hb_create(hb_ctx **out, const hb_options *opt) {
     if (!out) return fail(HB_ERR_ARG, "hb_create: out is NULL");
@@ -1180,6 +1202,7 @@ hb_status encode_side(hb_ctx *c, int side) {
     }
     // feature groups
     S.grams.assign(c->groups.size(), nullptr);
+    S.gram_len.assign(c->groups.size(), 0);
     Buf flag;
     HB_TRY(grow(c, flag, 16));
     HB_CUDA(cudaMemsetAsync(flag.p, 0, 16, c->stream));
@@ -1223,6 +1246,7 @@ hb_status encode_side(hb_ctx *c, int side) {
             HB_TRY(dmalloc(c, &tl, sizeof(uint32_t) * (size_t)(T + 1)));
             HB_TRY(dmalloc(c, &p, sizeof(uint32_t) * (size_t)(T + 4)));
             S.grams[g] = static_cast<uint32_t *>(p);
+            S.gram_len[g] = (uint64_t)T + 4;
             tok_fill(col, as<uint32_t>(toff), static_cast<uint32_t *>(ts), static_cast<uint32_t *>(tl), c->stream);
             if (c->tok.size() < c->groups.size()) c->tok.resize(c->groups.size());
             hb_ctx::TokDict &D = c->tok[g];
@@ -1256,6 +1280,7 @@ hb_status encode_side(hb_ctx *c, int side) {
         } else {
             HB_TRY(dmalloc(c, &p, sizeof(uint32_t) * (col.nbytes + 4)));
             S.grams[g] = static_cast<uint32_t *>(p);
+            S.gram_len[g] = col.nbytes + 4;
             HB_TRY(grow(c, c->w_jac, jac_scratch_bytes(n)));
             jac_features_impl(col, G.q, S.rec, W, G.word, S.grams[g], c->w_jac.p, as<unsigned int>(flag), c->n_sm,
                               c->stream);
@@ -1437,9 +1462,14 @@ EvalParams make_params(hb_ctx *c, const uint32_t *rec_r, const uint32_t *rec_s, 
     }
     // the general phase 1: some active MD's blocks have 2..4 distinct base
     // filters or 4 varying equality keys
+    P.keymask = c->n_eq_total >= 32 ? 0xffffffffu : ((1u << c->n_eq_total) - 1u);
+    if (c->group_mds) {   // only the keys some MD holds: the rules' codes and the branches' partitions
+        P.keymask = 0;
+        for (uint16_t e : c->eqset) P.keymask |= e;
+    }
     P.multi = 0;
     for (int m : c->active) {
-        const int ko = c->n_eq_total - __builtin_popcount((unsigned)c->eqset[m]);
+        const int ko = __builtin_popcount(P.keymask & ~(unsigned)c->eqset[m]);
         P.multi |= ((P.base_nops[m] >= 2 && P.base_nops[m] <= 4) || ko == 4) ? 1 : 0;
     }
     memset(P.screen_op, 255, sizeof(P.screen_op));
@@ -1462,11 +1492,7 @@ EvalParams make_params(hb_ctx *c, const uint32_t *rec_r, const uint32_t *rec_s, 
     P.use_lut = c->lut.empty() ? 0 : 1;
     P.group_mds = c->group_mds;
     P.owner_mds = c->group_mds ? c->group_mds : ~0ull;
-    P.keymask = c->n_eq_total >= 32 ? 0xffffffffu : ((1u << c->n_eq_total) - 1u);
-    if (c->group_mds) {   // only the keys some MD holds: the rules' codes and the branches' partitions
-        P.keymask = 0;
-        for (uint16_t e : c->eqset) P.keymask |= e;
-    }
+
     P.tile = c->tile;
     P.key_bits_s = key_bits_s;
     P.eqonly = c->eqonly;
@@ -1478,9 +1504,13 @@ EvalParams make_params(hb_ctx *c, const uint32_t *rec_r, const uint32_t *rec_s, 
         if (G.kind == OP_ED) {
             P.ptr_r[k] = c->side[0].cols[G.col_t].bytes;
             P.ptr_s[k] = self ? c->side[0].cols[G.col_t].bytes : c->side[side_s].cols[G.col_s].bytes;
+            P.len_r[k] = c->side[0].cols[G.col_t].nbytes;
+            P.len_s[k] = self ? P.len_r[k] : c->side[side_s].cols[G.col_s].nbytes;
         } else if (G.kind == OP_JAC) {   // q-gram or word-token code lists (Jaccard, containment)
             P.ptr_r[k] = c->side[0].grams[pi.group];
             P.ptr_s[k] = self ? c->side[0].grams[pi.group] : c->side[side_s].grams[pi.group];
+            P.len_r[k] = c->side[0].gram_len[pi.group];
+            P.len_s[k] = self ? P.len_r[k] : c->side[side_s].gram_len[pi.group];
         }
     }
     P.rec_r = rec_r;
@@ -1489,6 +1519,11 @@ EvalParams make_params(hb_ctx *c, const uint32_t *rec_r, const uint32_t *rec_s, 
     P.members_r = as<uint32_t>(c->w_members_r);
     P.members_s = self ? as<uint32_t>(c->w_members_r) : as<uint32_t>(c->w_members_s);
     P.small = self ? as<uint32_t>(c->w_small) : nullptr;
+    P.n_r = (uint64_t)c->side[0].n;
+    P.n_s = self ? P.n_r : (uint64_t)c->side[side_s].n;
+    P.members_r_len = c->w_members_r.bytes / 4;
+    P.members_s_len = self ? P.members_r_len : c->w_members_s.bytes / 4;
+    P.small_len = self ? c->w_small.bytes / 4 : 0;
     P.blocks = as<BlockDesc>(c->w_blocks);
     P.n_blocks = reinterpret_cast<const uint32_t *>(ctr + 3);
     P.tile_prefix = as<uint64_t>(c->w_prefix);
@@ -1613,6 +1648,7 @@ static hb_status run_block(hb_ctx *c, hb_pair **out, int64_t *n_out, bool to_hos
     uint64_t *sorted = nullptr;
     HB_TRY(block_eval_sort(c, c->side[0].rec, nr, self ? c->side[0].rec : c->side[1].rec, ns, self, 1, kb, kbs, 0,
                            res, &sorted, &tm));
+    HB_TRY(check_bounds(c, "hb_block"));
     HB_TRY(deliver(c, sorted, res.n_out, kbs, to_host, out));
     tm.mark();
     HB_CUDA(cudaStreamSynchronize(c->stream));

@@ -263,6 +263,7 @@ static hb_status per_job(hb_ctx *c, int n_jobs, const int64_t *job_rows, hb_pair
         hb_status st = block_eval_sort(c, c->side[0].rec, nj, c->side[0].rec, nj, true, 1, kb, kbs, 0, res, &sorted,
                                        nullptr);
         hb_pair *h = nullptr;
+        if (st == HB_OK) st = check_bounds(c, "hb_block_batch");
         if (st == HB_OK) st = deliver(c, sorted, res.n_out, kbs, true, &h);
         c->side[0].rec = save_rec;
         c->side[0].hot = save_hot;
@@ -377,6 +378,7 @@ extern "C" hb_status hb_block_batch(hb_ctx *c, int32_t n_jobs, const int64_t *jo
             drop_graph(c);
             continue;
         }
+        HB_TRY(check_bounds(c, "hb_block_batch"));
         std::vector<uint32_t> off(n_jobs + 1);
         HB_CUDA(cudaMemcpyAsync(off.data(), c->w_joboff.p, sizeof(uint32_t) * (n_jobs + 1), cudaMemcpyDeviceToHost,
                                 c->stream));

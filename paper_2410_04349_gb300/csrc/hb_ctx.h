@@ -70,6 +70,7 @@ struct SideData {
     uint32_t *hot = nullptr;   // per tuple: equality codes + one filter word per feature group (+ bin counts)
     std::vector<int32_t> hot_map;   // layout the hot records were packed with
     std::vector<uint32_t *> grams;   // per feature group (JAC only)
+    std::vector<uint64_t> gram_len;  // entries of grams[g]
     bool encoded = false;
 };
 

@@ -16,6 +16,46 @@ namespace hb {
 extern std::atomic<long long> g_kernel_launches;
 #define HB_LAUNCHED(n) (::hb::g_kernel_launches.fetch_add((n), std::memory_order_relaxed))
 
+// ---- checked builds (HB_CHECKED: libhb_checked.so) ----
+// The evaluation kernel's block, member, tuple, survivor, ring, string and
+// gram-list indices and the encoder's and block builder's output positions
+// are checked against their buffers.  A failing check records its site number
+// in the translation unit's error word and the access goes to element 0 (or an
+// empty range) instead, so nothing outside a buffer is touched; the host turns
+// a recorded site into HB_ERR_BOUNDS.  Ordinary builds compile the checks away.
+#if defined(HB_CHECKED) && defined(__CUDACC__)
+static __device__ unsigned int hb_dev_err;
+__device__ __forceinline__ uint64_t hb_checked_index(uint64_t i, uint64_t n, unsigned site) {
+    if (i < n) return i;
+    atomicCAS(&hb_dev_err, 0u, site);
+    return 0;
+}
+__device__ __forceinline__ bool hb_checked_range(uint64_t lo, uint64_t len, uint64_t n, unsigned site) {
+    if (lo <= n && len <= n - lo) return true;
+    atomicCAS(&hb_dev_err, 0u, site);
+    return false;
+}
+#define HB_IDX(i, n, site) ::hb::hb_checked_index((uint64_t)(i), (uint64_t)(n), (site))
+#define HB_RANGE_OK(lo, len, n, site) ::hb::hb_checked_range((uint64_t)(lo), (uint64_t)(len), (uint64_t)(n), (site))
+// reads and clears the unit's error word (the caller has synchronised the device)
+#define HB_ERROR_READER(name)                                              \
+    unsigned int name() {                                                  \
+        unsigned int v = 0, z = 0;                                         \
+        cudaMemcpyFromSymbol(&v, hb_dev_err, sizeof(v));                   \
+        if (v) cudaMemcpyToSymbol(hb_dev_err, &z, sizeof(z));              \
+        return v;                                                          \
+    }
+#else
+#define HB_IDX(i, n, site) (i)
+#define HB_RANGE_OK(lo, len, n, site) true
+#define HB_ERROR_READER(name) \
+    unsigned int name() { return 0; }
+#endif
+unsigned int checked_error_eval();     // k_eval.cu
+unsigned int checked_error_encode();   // k_encode.cu
+unsigned int checked_error_block();    // k_block.cu
+hb_status check_bounds(hb_ctx *c, const char *what);   // hb_api.cu: HB_ERR_BOUNDS if a check failed
+
 constexpr uint32_t NULL_CODE = 0xFFFFFFFFu;     // missing value: equal to nothing
 constexpr uint32_t NOMATCH_CODE = 0xFFFFFFFEu;  // S value that no R tuple holds
 constexpr uint32_t NULL_LEN = 0xFFFFFFFFu;      // missing string
@@ -108,6 +148,11 @@ struct EvalParams {
     uint64_t group_mds;
     uint64_t owner_mds;
     uint32_t keymask;
+    // buffer extents for the checks of checked builds: rows of each side,
+    // member-list and packed-start entries, per op the string bytes (edit
+    // distance) or gram codes (Jaccard) of each side
+    uint64_t n_r, n_s, members_r_len, members_s_len, small_len;
+    uint64_t len_r[MAX_OPS], len_s[MAX_OPS];
     uint16_t eqset[MAX_MD]; // equality keys of each MD (bit e = key e)
     int8_t first_op[MAX_MD];// first program op of each MD (-1: none)
     // per MD m: the MDs alive for every pair of m's blocks (equality keys a

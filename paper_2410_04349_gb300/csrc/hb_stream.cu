@@ -119,6 +119,7 @@ static hb_status encode_chunk(hb_ctx *c, SideData &S, unsigned int *too_long, Bu
                    S.rec + e, W, c->stream);
     }
     S.grams.assign(c->groups.size(), nullptr);
+    S.gram_len.assign(c->groups.size(), 0);
     for (size_t g = 0; g < c->groups.size(); g++) {
         const FeatGroup &G = c->groups[g];
         const DevCol &col = S.cols[G.col_s];
@@ -128,6 +129,7 @@ static hb_status encode_chunk(hb_ctx *c, SideData &S, unsigned int *too_long, Bu
             abs_feature(col, S.rec, W, G.word, c->stream);
         } else {
             S.grams[g] = as<uint32_t>(grams_buf) + gram_off[g];
+            S.gram_len[g] = (g + 1 < gram_off.size() ? gram_off[g + 1] : grams_buf.bytes / 4) - gram_off[g];
             jac_features_impl(col, G.q, S.rec, W, G.word, S.grams[g], c->w_jac.p, too_long, c->n_sm, c->stream);
         }
     }
@@ -493,6 +495,7 @@ extern "C" hb_status hb_block_stream(hb_ctx *c, int64_t n_rows_s, int32_t n_cols
     radix_sort_u64(as<uint64_t>(c->w_out), as<uint64_t>(c->w_alt), n_pairs, nullptr, kb, c->w_sort.p,
                    c->w_sort.bytes, c->stream, &sorted);
     hb_pair *out = nullptr;
+    HB_STRY(check_bounds(c, "hb_block_stream"));
     HB_STRY(deliver(c, sorted, n_pairs, kbs, true, &out));
     cleanup();
     Buf *tmp[] = {&tables, &cnt_r, &start_r, &chunk_rec, &chunk_hot, &chunk_grams, &flag};

@@ -130,7 +130,7 @@ __global__ void k_scatter_slots(const uint32_t *slot, int64_t n, const uint32_t 
     uint32_t base = 0;
     if (s != NO_SLOT && leader == lane) base = atomicAdd(&cursor[s], (uint32_t)__popc(peers));
     base = __shfl_sync(0xffffffffu, base, leader);
-    if (s != NO_SLOT) members[start[s] + base + __popc(peers & ((1u << lane) - 1u))] = (uint32_t)i;
+    if (s != NO_SLOT) members[HB_IDX(start[s] + base + __popc(peers & ((1u << lane) - 1u)), n, 30)] = (uint32_t)i;
 }
 
 __device__ __forceinline__ uint64_t tiles_of(uint32_t nr, uint32_t ns, int self_join, int tile) {
@@ -345,5 +345,7 @@ void clamp_blocks(uint32_t *n_blocks, uint32_t block_cap, cudaStream_t s) {
     HB_LAUNCHED(1);
     k_clamp_blocks<<<1, 1, 0, s>>>(n_blocks, block_cap);
 }
+
+HB_ERROR_READER(checked_error_block)
 
 }  // namespace hb

@@ -302,76 +302,96 @@ __device__ void write_gram_feature(uint32_t *r, uint32_t ucount, uint32_t start,
     r[FEAT_JAC_MASK + 1] = (uint32_t)(mask >> 32);
 }
 
-// One string's grams sorted by a group of G lanes (G = 4, 8, 16 or 32, two
-// grams per lane, up to 2G grams): a bitonic network over the 2G elements, the
-// element e = 2 * (lane in group) + j; partners at a distance of two or more
-// elements sit in another lane of the group (a shuffle), at distance one in the
-// same lane.  The unique grams are compacted with ballots and written in
-// order; their 32 bin counts (at most 64 grams, so no 8-bit count saturates)
-// and 64-bit presence mask are summed in the warp's shared words.  e is the
-// string's entry (id, byte offset, length, first gram slot), by the lane's
-// bytes 2gl .. 2gl+4 of it (zero past the end), both loaded beforehand.
-template <int G>
-__device__ __forceinline__ void grams_group(int q, bool has, uint4 e, const uint32_t (&by)[5], uint32_t *grams,
-                                            uint32_t *rec, int W, int feat, uint32_t *acc) {
+// One string's grams sorted by a group of G lanes holding E grams each (up to
+// E*G grams; E = 2 or 4): a bitonic network over the E*G elements, element
+// e = E * (lane in group) + j.  Partners at a distance below E sit in the same
+// lane (a compare-exchange in registers), farther ones in another lane of the
+// group (a shuffle).  The unique grams are compacted (per-lane counts summed
+// over the group with ballots of their bits) and written in order; their 32
+// bin counts (at most 64 grams, so no 8-bit count saturates) and 64-bit
+// presence mask are summed in the warp's shared words.  e is the string's entry
+// (id, byte offset, length, first gram slot), by the lane's bytes E*gl ..
+// E*gl+E+2 of it (zero past the end), both loaded beforehand.
+constexpr int QG_LANE_BYTES = 7;   // E + 3 bytes for E = 4 grams of up to 4 bytes
+
+template <int G, int E>
+__device__ __forceinline__ void grams_group(int q, bool has, uint4 e, const uint32_t (&by)[QG_LANE_BYTES],
+                                            uint32_t *grams, uint64_t gcap, uint32_t *rec, int W, int feat,
+                                            uint32_t *acc) {
     const int lane = threadIdx.x & 31;
     const int gl = lane & (G - 1), gi = lane / G;
     const uint32_t i = e.x, gs = e.w;
-    const uint32_t g = has ? e.z - (uint32_t)q + 1u : 0u;   // strings of this class have 1..2G grams
-    uint32_t v0 = 0, v1 = 0;
+    const uint32_t g = has ? e.z - (uint32_t)q + 1u : 0u;   // strings of this class have 1..E*G grams
+    const uint32_t k0 = (uint32_t)(E * gl);
+    uint32_t v[E];
 #pragma unroll
-    for (int t = 0; t < 4; t++) {
-        if (t < q) {
-            v0 = (v0 << 8) | by[t];
-            v1 = (v1 << 8) | by[t + 1];
-        }
+    for (int j = 0; j < E; j++) {
+        uint32_t x = 0;
+#pragma unroll
+        for (int t = 0; t < 4; t++)
+            if (t < q) x = (x << 8) | by[j + t];
+        v[j] = k0 + j < g ? x : 0xFFFFFFFFu;
     }
-    const uint32_t k0 = 2u * gl, k1 = k0 + 1u;
-    v0 = k0 < g ? v0 : 0xFFFFFFFFu;
-    v1 = k1 < g ? v1 : 0xFFFFFFFFu;
 #pragma unroll
-    for (int size = 2; size <= 2 * G; size <<= 1) {
-        const bool up = (k0 & (uint32_t)size) == 0u;   // the same for both elements once size >= 2
+    for (int size = 2; size <= E * G; size <<= 1) {
 #pragma unroll
         for (int stride = size / 2; stride > 0; stride >>= 1) {
-            if (stride == 1) {
-                const uint32_t lo = min(v0, v1), hi = max(v0, v1);
-                v0 = up ? lo : hi;
-                v1 = up ? hi : lo;
+            if (stride < E) {
+#pragma unroll
+                for (int j = 0; j < E; j++) {
+                    const int p = j ^ stride;
+                    if (p > j) {
+                        // direction from the element's bit `size`: within the lane below E, else the lane's
+                        const bool up = size < E ? ((j & size) == 0) : ((k0 & (uint32_t)size) == 0u);
+                        const uint32_t lo = min(v[j], v[p]), hi = max(v[j], v[p]);
+                        v[j] = up ? lo : hi;
+                        v[p] = up ? hi : lo;
+                    }
+                }
             } else {
-                const int ls = stride >> 1;
-                const uint32_t p0 = __shfl_xor_sync(0xffffffffu, v0, ls);
-                const uint32_t p1 = __shfl_xor_sync(0xffffffffu, v1, ls);
+                const int ls = stride / E;
+                const bool up = (k0 & (uint32_t)size) == 0u;
                 const bool keep_min = ((gl & ls) == 0) == up;
-                v0 = keep_min ? min(v0, p0) : max(v0, p0);
-                v1 = keep_min ? min(v1, p1) : max(v1, p1);
+#pragma unroll
+                for (int j = 0; j < E; j++) {
+                    const uint32_t p = __shfl_xor_sync(0xffffffffu, v[j], ls);
+                    v[j] = keep_min ? min(v[j], p) : max(v[j], p);
+                }
             }
         }
     }
-    // unique flags: an element differs from the one before it (lane gl-1's second)
-    const uint32_t prev = __shfl_up_sync(0xffffffffu, v1, 1);
-    const bool u0 = k0 < g && (gl == 0 || v0 != prev);
-    const bool u1 = k1 < g && v1 != v0;
-    const uint32_t b0 = __ballot_sync(0xffffffffu, u0), b1 = __ballot_sync(0xffffffffu, u1);
+    // unique flags: an element differs from the one before it (lane gl-1's last for j = 0)
+    const uint32_t prev = __shfl_up_sync(0xffffffffu, v[E - 1], 1);
+    bool u[E];
+    uint32_t cnt = 0;
+#pragma unroll
+    for (int j = 0; j < E; j++) {
+        u[j] = k0 + j < g && (j > 0 ? v[j] != v[j - 1] : (gl == 0 || v[0] != prev));
+        cnt += u[j] ? 1u : 0u;
+    }
+    // the group's exclusive prefix of the per-lane counts (0..E) from ballots of their bits
     const uint32_t gbits = (G == 32 ? 0xffffffffu : ((1u << G) - 1u)) << (gi * G);
     const uint32_t lower = gbits & ((1u << lane) - 1u);
-    const uint32_t pos0 = __popc(b0 & lower) + __popc(b1 & lower);
-    const uint32_t ucount = __popc(b0 & gbits) + __popc(b1 & gbits);
-    if (u0) grams[gs + pos0] = v0;
-    if (u1) grams[gs + pos0 + (u0 ? 1u : 0u)] = v1;
-    // feature words: 8 words of 32 8-bit bin counts, then the 64-bit mask
+    uint32_t pre = 0, ucount = 0;
+#pragma unroll
+    for (int b = 0; b < (E == 4 ? 3 : 2); b++) {
+        const uint32_t bal = __ballot_sync(0xffffffffu, (cnt >> b) & 1u);
+        pre += (uint32_t)__popc(bal & lower) << b;
+        ucount += (uint32_t)__popc(bal & gbits) << b;
+    }
     uint32_t *sh = acc + gi * 10;
     for (int w = gl; w < 10; w += G) sh[w] = 0u;
     __syncwarp();
-    if (u0) {
-        const uint32_t bin = gram_bin(v0), bit = gram_bit(v0);
-        atomicAdd(sh + (bin >> 2), 1u << ((bin & 3u) * 8u));
-        atomicOr(sh + 8 + (bit >> 5), 1u << (bit & 31u));
-    }
-    if (u1) {
-        const uint32_t bin = gram_bin(v1), bit = gram_bit(v1);
-        atomicAdd(sh + (bin >> 2), 1u << ((bin & 3u) * 8u));
-        atomicOr(sh + 8 + (bit >> 5), 1u << (bit & 31u));
+#pragma unroll
+    for (int j = 0; j < E; j++) {
+        if (u[j]) {
+            grams[HB_IDX((uint64_t)gs + pre, gcap, 20)] = v[j];
+            pre++;
+            // feature words: 8 words of 32 8-bit bin counts, then the 64-bit mask
+            const uint32_t bin = gram_bin(v[j]), bit = gram_bit(v[j]);
+            atomicAdd(sh + (bin >> 2), 1u << ((bin & 3u) * 8u));
+            atomicOr(sh + 8 + (bit >> 5), 1u << (bit & 31u));
+        }
     }
     __syncwarp();
     if (has) {
@@ -383,11 +403,12 @@ __device__ __forceinline__ void grams_group(int q, bool has, uint4 e, const uint
 
 // Strings in bucket order (by gram count), in six classes: no grams (null or
 // shorter than q; a thread each), 1-8, 9-16, 17-32 and 33-64 grams (a group of
-// 4, 8, 16 or 32 lanes each), and more than 64 grams (a thread each, handed to
-// the per-warp and per-block kernels).  bucket_end[b] is the end of bucket b in
-// the order.  Warps walk the classes' groups with a grid stride; the entries
-// of the group two steps ahead and the bytes of the next are loaded before a
-// group is sorted, so the two dependent loads of a string overlap the sorting.
+// 4, 4, 8 or 16 lanes each, 2, 4, 4 and 4 grams to a lane), and more than 64
+// grams (a thread each, handed to the per-warp and per-block kernels).
+// bucket_end[b] is the end of bucket b in the order.  Warps walk the classes'
+// groups with a grid stride; the entries of the group two steps ahead and the
+// bytes of the next are loaded before a group is sorted, so the two dependent
+// loads of a string overlap the sorting.
 constexpr int QG_COOP_THREADS = 256;
 
 struct CoopStep {
@@ -414,10 +435,9 @@ __device__ __forceinline__ CoopStep coop_step(uint32_t w, const uint32_t (&lo)[7
     const uint32_t wc = w - ws_c;
     uint32_t pos;
     if (c == 0 || c == 5) pos = lo_c + wc * 32u + (uint32_t)lane;
-    else if (c == 1) pos = lo_c + wc * 8u + (uint32_t)(lane >> 2);
-    else if (c == 2) pos = lo_c + wc * 4u + (uint32_t)(lane >> 3);
-    else if (c == 3) pos = lo_c + wc * 2u + (uint32_t)(lane >> 4);
-    else pos = lo_c + wc;
+    else if (c == 1 || c == 2) pos = lo_c + wc * 8u + (uint32_t)(lane >> 2);
+    else if (c == 3) pos = lo_c + wc * 4u + (uint32_t)(lane >> 3);
+    else pos = lo_c + wc * 2u + (uint32_t)(lane >> 4);
     st.c = c;
     st.pos = pos;
     st.has = pos < hi_c;
@@ -428,23 +448,27 @@ __device__ __forceinline__ uint4 coop_entry(const CoopStep &st, const uint4 *ent
     return st.has ? ent[st.pos] : make_uint4(0u, 0u, 0u, 0u);
 }
 
-// bytes 2gl .. 2gl+4 of the lane's string (group classes only)
+// bytes E*gl .. E*gl+E+q-2 of the lane's string (group classes only; class 1
+// has groups of 4 lanes with 2 grams each, classes 2-4 groups of 4, 8 and 16
+// lanes with 4 grams each)
 __device__ __forceinline__ void coop_bytes(const CoopStep &st, uint4 e, const uint8_t *bytes, int q,
-                                           uint32_t (&by)[5]) {
+                                           uint32_t (&by)[QG_LANE_BYTES]) {
     const int lane = threadIdx.x & 31;
-    const int gl = st.c >= 1 && st.c <= 4 ? (lane & ((4 << (st.c - 1)) - 1)) : 0;
     const bool grp = st.has && st.c >= 1 && st.c <= 4;
+    const int G = st.c <= 2 ? 4 : st.c == 3 ? 8 : 16;
+    const int E = st.c == 1 ? 2 : 4;
+    const uint32_t k0 = (uint32_t)(E * (lane & (G - 1)));
 #pragma unroll
-    for (int t = 0; t < 5; t++) {
-        const uint32_t k = 2u * gl + (uint32_t)t;
-        by[t] = (grp && t <= q && k < e.z) ? (uint32_t)bytes[e.y + k] : 0u;
+    for (int t = 0; t < QG_LANE_BYTES; t++) {
+        const uint32_t k = k0 + (uint32_t)t;
+        by[t] = (grp && t < E + q - 1 && k < e.z) ? (uint32_t)bytes[e.y + k] : 0u;
     }
 }
 
 __global__ void __launch_bounds__(QG_COOP_THREADS) k_grams_coop(const uint8_t *bytes, const uint8_t *valid, int64_t n,
                                                                 int q, const uint4 *ent, const uint32_t *bucket_end,
-                                                                uint32_t *grams, uint32_t *rec, int W, int feat,
-                                                                uint32_t *mid_list, unsigned int *n_mid,
+                                                                uint32_t *grams, uint64_t gcap, uint32_t *rec, int W,
+                                                                int feat, uint32_t *mid_list, unsigned int *n_mid,
                                                                 uint32_t *long_list, unsigned int *n_long) {
     __shared__ uint32_t acc_all[QG_COOP_THREADS / 32][80];
     uint32_t *acc = acc_all[threadIdx.x >> 5];
@@ -458,7 +482,7 @@ __global__ void __launch_bounds__(QG_COOP_THREADS) k_grams_coop(const uint8_t *b
     lo[4] = bucket_end[32];
     lo[5] = bucket_end[64];
     lo[6] = (uint32_t)n;
-    const uint32_t per[6] = {32, 8, 4, 2, 1, 32};
+    const uint32_t per[6] = {32, 8, 8, 4, 2, 32};
     uint32_t wstart[7];
     wstart[0] = 0;
 #pragma unroll
@@ -469,13 +493,13 @@ __global__ void __launch_bounds__(QG_COOP_THREADS) k_grams_coop(const uint8_t *b
     uint4 eA = coop_entry(A, ent);
     CoopStep B = coop_step(w + nw, lo, wstart, lane);
     uint4 eB = coop_entry(B, ent);
-    uint32_t bA[5];
+    uint32_t bA[QG_LANE_BYTES];
     coop_bytes(A, eA, bytes, q, bA);
     while (A.c >= 0) {
         w += nw;
         const CoopStep C = coop_step(w + nw, lo, wstart, lane);
         const uint4 eC = coop_entry(C, ent);
-        uint32_t bB[5];
+        uint32_t bB[QG_LANE_BYTES];
         coop_bytes(B, eB, bytes, q, bB);
         if (A.c == 0) {
             if (A.has) {
@@ -493,18 +517,18 @@ __global__ void __launch_bounds__(QG_COOP_THREADS) k_grams_coop(const uint8_t *b
                 else long_list[atomicAdd(n_long, 1u)] = eA.x;
             }
         } else if (A.c == 1) {
-            grams_group<4>(q, A.has, eA, bA, grams, rec, W, feat, acc);
+            grams_group<4, 2>(q, A.has, eA, bA, grams, gcap, rec, W, feat, acc);
         } else if (A.c == 2) {
-            grams_group<8>(q, A.has, eA, bA, grams, rec, W, feat, acc);
+            grams_group<4, 4>(q, A.has, eA, bA, grams, gcap, rec, W, feat, acc);
         } else if (A.c == 3) {
-            grams_group<16>(q, A.has, eA, bA, grams, rec, W, feat, acc);
+            grams_group<8, 4>(q, A.has, eA, bA, grams, gcap, rec, W, feat, acc);
         } else {
-            grams_group<32>(q, A.has, eA, bA, grams, rec, W, feat, acc);
+            grams_group<16, 4>(q, A.has, eA, bA, grams, gcap, rec, W, feat, acc);
         }
         A = B;
         eA = eB;
 #pragma unroll
-        for (int t = 0; t < 5; t++) bA[t] = bB[t];
+        for (int t = 0; t < QG_LANE_BYTES; t++) bA[t] = bB[t];
         B = C;
         eB = eC;
     }
@@ -514,7 +538,7 @@ __global__ void __launch_bounds__(QG_COOP_THREADS) k_grams_coop(const uint8_t *b
 // shared memory, the unique grams compacted with warp ballots and counted in
 // 32 bins with shared-memory atomics.
 __global__ void __launch_bounds__(256) k_grams_mid(const uint8_t *bytes, const uint32_t *off, int q,
-                                                  const uint32_t *gstart, uint32_t *grams, uint32_t *rec, int W,
+                                                  const uint32_t *gstart, uint32_t *grams, uint64_t gcap, uint32_t *rec, int W,
                                                   int feat, const uint32_t *mid_list, const unsigned int *n_mid) {
     __shared__ uint32_t sm[8][QG_MID];
     __shared__ uint32_t bins[8][32];
@@ -548,6 +572,7 @@ __global__ void __launch_bounds__(256) k_grams_mid(const uint8_t *bytes, const u
             }
         }
         uint32_t *dst = grams + gstart[i];
+        if (!HB_RANGE_OK(gstart[i], g, gcap, 21)) continue;
         uint32_t base = 0;
         uint64_t mask = 0;
         for (uint32_t c0 = 0; c0 < g; c0 += 32) {
@@ -583,7 +608,7 @@ __global__ void __launch_bounds__(256) k_grams_mid(const uint8_t *bytes, const u
 
 // Strings with more grams: one block per string, bitonic sort in shared memory.
 __global__ void __launch_bounds__(256) k_grams_long(const uint8_t *bytes, const uint32_t *off, int q,
-                                                   const uint32_t *gstart, uint32_t *grams, uint32_t *rec, int W,
+                                                   const uint32_t *gstart, uint32_t *grams, uint64_t gcap, uint32_t *rec, int W,
                                                    int feat, const uint32_t *long_list, const unsigned int *n_long,
                                                    unsigned int *too_long) {
     __shared__ uint32_t s[QG_LONG_MAX];
@@ -625,6 +650,7 @@ __global__ void __launch_bounds__(256) k_grams_long(const uint8_t *bytes, const 
         }
         // unique: a block-wide compaction in index order
         uint32_t *dst = grams + gstart[i];
+        if (!HB_RANGE_OK(gstart[i], g, gcap, 22)) continue;
         uint32_t base = 0;
         for (uint32_t c0 = 0; c0 < g; c0 += blockDim.x) {
             uint32_t k = c0 + threadIdx.x;
@@ -964,12 +990,16 @@ void jac_features_impl(const DevCol &c, int q, uint32_t *rec, int W, int feat, u
     k_bucket_scan<<<1, 32, 0, s>>>(bucket_count, bucket_cursor);
     k_bucket_scatter<<<blocks_for(n, ENC_THREADS), ENC_THREADS, 0, s>>>(cnt, c.off, gstart, n, bucket_cursor, ent);
     k_grams_coop<<<(unsigned)(n_sm * 8), QG_COOP_THREADS, 0, s>>>(c.bytes, c.valid, n, q, ent, bucket_cursor, grams,
-                                                                  rec, W, feat, mid_list, n_mid, long_list, n_long);
+                                                                  c.nbytes, rec, W, feat, mid_list, n_mid, long_list,
+                                                                  n_long);
     HB_LAUNCHED(1);
-    k_grams_mid<<<(unsigned)(n_sm * 8), 256, 0, s>>>(c.bytes, c.off, q, gstart, grams, rec, W, feat, mid_list, n_mid);
+    k_grams_mid<<<(unsigned)(n_sm * 8), 256, 0, s>>>(c.bytes, c.off, q, gstart, grams, c.nbytes, rec, W, feat,
+                                                     mid_list, n_mid);
     HB_LAUNCHED(1);
-    k_grams_long<<<(unsigned)(n_sm * 4), 256, 0, s>>>(c.bytes, c.off, q, gstart, grams, rec, W, feat, long_list,
-                                                      n_long, too_long);
+    k_grams_long<<<(unsigned)(n_sm * 4), 256, 0, s>>>(c.bytes, c.off, q, gstart, grams, c.nbytes, rec, W, feat,
+                                                      long_list, n_long, too_long);
 }
+
+HB_ERROR_READER(checked_error_encode)
 
 }  // namespace hb

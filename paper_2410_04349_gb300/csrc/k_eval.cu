@@ -220,8 +220,10 @@ __device__ __forceinline__ bool eval_op(const EvalParams &P, int k, const uint32
         }
         if (max(p1, p2) > op.k) return false;
         if (LOG) log_add(lg, k * LOG_FIELDS + 4, 1u);
-        const uint8_t *sa = static_cast<const uint8_t *>(P.ptr_r[k]) + __ldg(a + f + 1);
-        const uint8_t *sb = static_cast<const uint8_t *>(P.ptr_s[k]) + __ldg(b + f + 1);
+        const uint32_t oa = __ldg(a + f + 1), ob = __ldg(b + f + 1);
+        if (!HB_RANGE_OK(oa, la, P.len_r[k], 12) || !HB_RANGE_OK(ob, lb, P.len_s[k], 13)) return false;
+        const uint8_t *sa = static_cast<const uint8_t *>(P.ptr_r[k]) + oa;
+        const uint8_t *sb = static_cast<const uint8_t *>(P.ptr_s[k]) + ob;
         uint32_t rows = 0;
         const bool r = ed_le(sa, (int)la, sb, (int)lb, op.k, rows);
         if (LOG) log_add(lg, k * LOG_FIELDS + 5, rows * (2u * op.k + 1u));
@@ -255,8 +257,10 @@ __device__ __forceinline__ bool eval_op(const EvalParams &P, int k, const uint32
         if (LOG) log_add(lg, k * LOG_FIELDS + 4, 1u);
         const uint64_t imin = (need + den - 1) / den;
         if (imin == 0) return true;
-        const uint32_t *A = static_cast<const uint32_t *>(P.ptr_r[k]) + __ldg(a + f + 1);
-        const uint32_t *B = static_cast<const uint32_t *>(P.ptr_s[k]) + __ldg(b + f + 1);
+        const uint32_t ga = __ldg(a + f + 1), gb = __ldg(b + f + 1);
+        if (!HB_RANGE_OK(ga, na, P.len_r[k], 14) || !HB_RANGE_OK(gb, nb, P.len_s[k], 15)) return false;
+        const uint32_t *A = static_cast<const uint32_t *>(P.ptr_r[k]) + ga;
+        const uint32_t *B = static_cast<const uint32_t *>(P.ptr_s[k]) + gb;
         uint32_t i = 0, j = 0, I = 0;
         bool res = false;
         while (i < na && j < nb) {
@@ -294,8 +298,10 @@ __device__ __forceinline__ bool eval_op(const EvalParams &P, int k, const uint32
     if (LOG) log_add(lg, k * LOG_FIELDS + 4, 1u);
     const uint64_t imin = (need + dn - 1) / dn;
     if (imin == 0) return true;
-    const uint32_t *A = static_cast<const uint32_t *>(P.ptr_r[k]) + __ldg(a + f + 1);
-    const uint32_t *B = static_cast<const uint32_t *>(P.ptr_s[k]) + __ldg(b + f + 1);
+    const uint32_t ga = __ldg(a + f + 1), gb = __ldg(b + f + 1);
+    if (!HB_RANGE_OK(ga, na, P.len_r[k], 14) || !HB_RANGE_OK(gb, nb, P.len_s[k], 15)) return false;
+    const uint32_t *A = static_cast<const uint32_t *>(P.ptr_r[k]) + ga;
+    const uint32_t *B = static_cast<const uint32_t *>(P.ptr_s[k]) + gb;
     uint32_t i = 0, j = 0, I = 0;
     bool res = false;
     while (i < na && j < nb) {
@@ -645,7 +651,8 @@ __device__ __noinline__ void phase2(const EvalParams &P, const uint64_t *lut, bo
     bool hit = false;
     if (act) {
         const uint64_t alive = alive_of(P, lut, E);
-        hit = run_program<LOG>(P, alive, P.rec_r + (size_t)ra * W, rec_c + (size_t)cb * W, lg);
+        hit = run_program<LOG>(P, alive, P.rec_r + (size_t)HB_IDX(ra, P.n_r, 10) * W,
+                               rec_c + (size_t)HB_IDX(cb, P.self_join ? P.n_r : P.n_s, 11) * W, lg);
     }
     const unsigned hm = __ballot_sync(0xffffffffu, hit);
     if (hm) {
@@ -715,7 +722,7 @@ __global__ void __launch_bounds__(EV_THREADS, 4) k_eval(const __grid_constant__ 
         uint32_t bi = find_block(P.tile_prefix, nb, t0, lane);
         for (uint64_t t = t0; t < t1; t++) {
             while (P.tile_prefix[bi + 1] <= t) bi++;
-            const BlockDesc B = P.blocks[bi];
+            const BlockDesc B = P.blocks[HB_IDX(bi, nb, 1)];
             // pn > 0: a packed tile of self-join blocks of pn tuples, side by side
             const int pn = (int)B.packed;
             uint32_t ti = 0, tj = 0;
@@ -737,9 +744,12 @@ __global__ void __launch_bounds__(EV_THREADS, 4) k_eval(const __grid_constant__ 
             for (int rr = 0; rr < R; rr++) {
                 const int r = rr * 32 + lane;
                 uint32_t pid = 0;   // packed tile: row r = member r % pn of block r / pn; columns alike
-                if (pn && r < nr) pid = P.members_r[P.small[B.start_r + r / pn] + r % pn];
+                if (pn && r < nr)
+                    pid = P.members_r[HB_IDX(P.small[HB_IDX(B.start_r + r / pn, P.small_len, 3)] + r % pn,
+                                             P.members_r_len, 4)];
                 if (r < nr) {
-                    const uint32_t id = pn ? pid : P.members_r[B.start_r + r0 + r];
+                    const uint32_t id = HB_IDX(pn ? pid : P.members_r[HB_IDX(B.start_r + r0 + r, P.members_r_len, 2)],
+                                               P.n_r, 6);
                     rid_s[r] = id;
                     const uint4 *src = reinterpret_cast<const uint4 *>(P.hot_r + (size_t)id * HW);
                     uint32_t *dst = hrows + r * HWP;
@@ -752,7 +762,8 @@ __global__ void __launch_bounds__(EV_THREADS, 4) k_eval(const __grid_constant__ 
                     }
                 }
                 if (r < nc) {
-                    const uint32_t id = pn ? pid : P.members_s[B.start_s + c0 + r];
+                    const uint32_t id = HB_IDX(pn ? pid : P.members_s[HB_IDX(B.start_s + c0 + r, P.members_s_len, 5)],
+                                               P.self_join ? P.n_r : P.n_s, 7);
                     cid_s[r] = id;
                     const uint4 *src = reinterpret_cast<const uint4 *>(hot_c + (size_t)id * HW);
                     uint32_t *dst = hcols + r;   // word-major: word w of column c at w * T + c
@@ -940,7 +951,8 @@ __global__ void __launch_bounds__(EV_THREADS, 4) k_eval(const __grid_constant__ 
                     while (mk && pos < SURV_CAP) {
                         const int c = first_bit(mk);
                         mk &= mk - 1;
-                        surv[pos++] = (uint16_t)(rb | (uint32_t)c);
+                        surv[HB_IDX(pos, SURV_CAP, 8)] = (uint16_t)(rb | (uint32_t)c);
+                        pos++;
                     }
                     kmask[rr] = mk;
                 }
@@ -1004,9 +1016,10 @@ __global__ void __launch_bounds__(EV_THREADS, 4) k_eval(const __grid_constant__ 
                 const unsigned km = __ballot_sync(0xffffffffu, keep);
                 if (keep) {
                     const int q = pend + __popc(km & lt);
-                    ring_ra[q] = ra;
-                    ring_cb[q] = cb;
-                    ring_e[q] = E;
+                    const int qc = (int)HB_IDX(q, RING_SLOTS, 9);
+                    ring_ra[qc] = ra;
+                    ring_cb[qc] = cb;
+                    ring_e[qc] = E;
                 }
                 pend += __popc(km);
                 if (pend >= 32) {
@@ -1182,5 +1195,7 @@ void pack_pairs(const uint64_t *keys, int64_t n, int key_bits_s, hb_pair *out, c
     HB_LAUNCHED(1);
     k_pack_pairs<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(keys, n, key_bits_s, out);
 }
+
+HB_ERROR_READER(checked_error_eval)
 
 }  // namespace hb

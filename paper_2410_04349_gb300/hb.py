@@ -23,7 +23,8 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libhb.so")
+# HB_CHECKED=1 in the environment loads the bounds-checked build (libhb_checked.so)
+LIB_PATH = os.path.join(_HERE, "libhb_checked.so" if os.environ.get("HB_CHECKED") == "1" else "libhb.so")
 
 HB_OK, HB_ERR_ARG, HB_ERR_OOM, HB_ERR_CUDA, HB_ERR_STATE, HB_ERR_OVERFLOW, HB_ERR_DEVICE_TIMEOUT = 0, -1, -2, -3, -4, -5, -6
 KINDS = {"eq": 0, "eq_prefix": 1, "ed": 2, "jaccard": 3, "absdiff": 4, "const_eq": 5, "contain": 6, "tjaccard": 7}

@@ -77,3 +77,16 @@ def test_create_without_gpu_fails_cleanly():
         hb.Context(device=0)
     assert e.value.status in (hb.HB_ERR_CUDA, hb.HB_ERR_ARG)
     assert "cuda" in str(e.value).lower()
+
+
+def test_checked_library_exports_the_same_symbols():
+    import ctypes
+    path = os.path.join(ROOT, "paper_2410_04349_gb300", "libhb_checked.so")
+    if not os.path.exists(path):
+        pytest.skip("libhb_checked.so not built")
+    L = ctypes.CDLL(path)
+    for n in declared_symbols():
+        assert hasattr(L, n), n
+    L.hb_version.restype = ctypes.c_char_p
+    assert b"checked" in L.hb_version()
+    assert b"checked" not in hb.lib().hb_version()
