@@ -309,7 +309,7 @@ extern "C" void hb_destroy(hb_ctx *c) {
     for (hb_ctx::MdLane &L : c->md_lanes) {
         if (L.stream) cudaStreamSynchronize(L.stream);
         Buf *lb[] = {&L.table, &L.slot_r, &L.count_r, &L.start_r, &L.cursor, &L.slot_s, &L.count_s, &L.start_s,
-                     &L.scan, &L.meta};
+                     &L.scan, &L.meta, &L.jac};
         for (Buf *b : lb) free_buf(c, *b);
         if (L.done) cudaEventDestroy(L.done);
         if (L.stream) cudaStreamDestroy(L.stream);
@@ -1153,6 +1153,20 @@ __global__ void k_job_codes(const int64_t *job_rows, int n_jobs, int64_t n, uint
     rec[i * W + word] = (uint32_t)lo;
 }
 
+// Side streams of the context (created on first use): the encoder and the
+// block builder run independent work on them, forked from and joined to the
+// context's stream with events.
+static hb_status ensure_lanes(hb_ctx *c, int lanes) {
+    if ((int)c->md_lanes.size() < lanes) c->md_lanes.resize(lanes);
+    if (!c->md_fork) HB_CUDA(cudaEventCreateWithFlags(&c->md_fork, cudaEventDisableTiming));
+    for (int l = 0; l < lanes; l++) {
+        hb_ctx::MdLane &L = c->md_lanes[l];
+        if (!L.stream) HB_CUDA(cudaStreamCreateWithFlags(&L.stream, cudaStreamNonBlocking));
+        if (!L.done) HB_CUDA(cudaEventCreateWithFlags(&L.done, cudaEventDisableTiming));
+    }
+    return HB_OK;
+}
+
 hb_status encode_side(hb_ctx *c, int side) {
     SideData &S = c->side[side];
     if (S.encoded && S.hot_map == c->hot_map) return HB_OK;
@@ -1184,6 +1198,17 @@ hb_status encode_side(hb_ctx *c, int side) {
         c->dict.assign(c->eqkeys.size(), nullptr);
         c->dict_cap.assign(c->eqkeys.size(), 0);
     }
+    // Independent encoding tasks (each equality key's dictionary, each edit-distance,
+    // |a-b| and q-gram feature group) write disjoint words of the records; they
+    // run below on up to MD_LANES side streams at once.  Their buffers are
+    // allocated here on the context's stream, before the fork.
+    struct EncTask {
+        int kind;   // 0: equality key, 1: feature group
+        size_t idx;
+        double cost;
+        int lane;
+    };
+    std::vector<EncTask> tasks;
     for (size_t e = 0; e < c->eqkeys.size(); e++) {
         const EqKey &k = c->eqkeys[e];
         if (side == 0) {
@@ -1191,14 +1216,9 @@ hb_status encode_side(hb_ctx *c, int side) {
             HB_TRY(dmalloc(c, &p, sizeof(uint64_t) * cap));
             c->dict[e] = static_cast<uint64_t *>(p);
             c->dict_cap[e] = cap;
-            dict_build(S.cols[k.col_t], k.prefix, c->dict[e], cap, S.rec + e, W, c->stream);
-        } else {
-            dict_probe(S.cols[k.col_s], k.prefix, c->side[0].cols[k.col_t], k.prefix, c->dict[e], c->dict_cap[e],
-                       S.rec + e, W, c->stream);
         }
-        if (c->part_m)
-            part_feature(S.cols[side == 0 ? k.col_t : k.col_s], k.prefix, c->part_m, S.rec, W,
-                         (int)(c->eqkeys.size() + e), c->stream);
+        const DevCol &col = S.cols[side == 0 ? k.col_t : k.col_s];
+        tasks.push_back({0, e, (double)n + (col.type == HB_COL_STRING ? (double)col.nbytes : 0.0), 0});
     }
     // feature groups
     S.grams.assign(c->groups.size(), nullptr);
@@ -1274,16 +1294,72 @@ hb_status encode_side(hb_ctx *c, int side) {
             continue;
         }
         if (G.kind == OP_ED) {
-            ed_features(col, S.rec, W, G.word, c->stream);
+            tasks.push_back({1, g, (double)col.nbytes, 0});
         } else if (G.kind == OP_ABS) {
-            abs_feature(col, S.rec, W, G.word, c->stream);
+            tasks.push_back({1, g, 0.5 * (double)n, 0});
         } else {
             HB_TRY(dmalloc(c, &p, sizeof(uint32_t) * (col.nbytes + 4)));
             S.grams[g] = static_cast<uint32_t *>(p);
             S.gram_len[g] = col.nbytes + 4;
-            HB_TRY(grow(c, c->w_jac, jac_scratch_bytes(n)));
-            jac_features_impl(col, G.q, S.rec, W, G.word, S.grams[g], c->w_jac.p, as<unsigned int>(flag), c->n_sm,
-                              c->stream);
+            tasks.push_back({1, g, 4.0 * (double)col.nbytes + (double)n, 0});
+        }
+    }
+    // longest first, each onto the least loaded lane
+    const int lanes = std::min((int)tasks.size(), MD_LANES);
+    std::sort(tasks.begin(), tasks.end(), [](const EncTask &a, const EncTask &b) { return a.cost > b.cost; });
+    {
+        double load[MD_LANES] = {0, 0, 0, 0};
+        for (EncTask &t : tasks) {
+            int best = 0;
+            for (int l = 1; l < lanes; l++)
+                if (load[l] < load[best]) best = l;
+            t.lane = best;
+            load[best] += t.cost;
+        }
+    }
+    const bool forked = lanes >= 2;
+    if (forked) {
+        HB_TRY(ensure_lanes(c, lanes));
+        for (const EncTask &t : tasks)
+            if (t.kind == 1 && c->groups[t.idx].kind == OP_JAC)
+                HB_TRY(grow(c, c->md_lanes[t.lane].jac, jac_scratch_bytes(n)));
+        HB_CUDA(cudaEventRecord(c->md_fork, c->stream));
+        for (int l = 0; l < lanes; l++) HB_CUDA(cudaStreamWaitEvent(c->md_lanes[l].stream, c->md_fork, 0));
+    } else {
+        for (const EncTask &t : tasks)
+            if (t.kind == 1 && c->groups[t.idx].kind == OP_JAC) HB_TRY(grow(c, c->w_jac, jac_scratch_bytes(n)));
+    }
+    for (const EncTask &t : tasks) {
+        cudaStream_t st = forked ? c->md_lanes[t.lane].stream : c->stream;
+        if (t.kind == 0) {
+            const size_t e = t.idx;
+            const EqKey &k = c->eqkeys[e];
+            if (side == 0)
+                dict_build(S.cols[k.col_t], k.prefix, c->dict[e], c->dict_cap[e], S.rec + e, W, st);
+            else
+                dict_probe(S.cols[k.col_s], k.prefix, c->side[0].cols[k.col_t], k.prefix, c->dict[e],
+                           c->dict_cap[e], S.rec + e, W, st);
+            if (c->part_m)
+                part_feature(S.cols[side == 0 ? k.col_t : k.col_s], k.prefix, c->part_m, S.rec, W,
+                             (int)(c->eqkeys.size() + e), st);
+            continue;
+        }
+        const size_t g = t.idx;
+        const FeatGroup &G = c->groups[g];
+        const DevCol &col = S.cols[side == 0 ? G.col_t : G.col_s];
+        if (G.kind == OP_ED) {
+            ed_features(col, S.rec, W, G.word, st);
+        } else if (G.kind == OP_ABS) {
+            abs_feature(col, S.rec, W, G.word, st);
+        } else {
+            void *scratch = forked ? c->md_lanes[t.lane].jac.p : c->w_jac.p;
+            jac_features_impl(col, G.q, S.rec, W, G.word, S.grams[g], scratch, as<unsigned int>(flag), c->n_sm, st);
+        }
+    }
+    if (forked) {
+        for (int l = 0; l < lanes; l++) {
+            HB_CUDA(cudaEventRecord(c->md_lanes[l].done, c->md_lanes[l].stream));
+            HB_CUDA(cudaStreamWaitEvent(c->stream, c->md_lanes[l].done, 0));
         }
     }
     unsigned int too_long = 0;
@@ -1353,12 +1429,9 @@ hb_status build_blocks(hb_ctx *c, const uint32_t *rec_r, int64_t n_r, const uint
     // block descriptors, tile counts and small-block ranges are claimed with
     // atomics.  MD a runs on lane a % lanes.
     const int lanes = std::min(std::max(na, 1), MD_LANES);
-    if ((int)c->md_lanes.size() < lanes) c->md_lanes.resize(lanes);
-    if (!c->md_fork) HB_CUDA(cudaEventCreateWithFlags(&c->md_fork, cudaEventDisableTiming));
+    HB_TRY(ensure_lanes(c, lanes));
     for (int l = 0; l < lanes; l++) {
         hb_ctx::MdLane &L = c->md_lanes[l];
-        if (!L.stream) HB_CUDA(cudaStreamCreateWithFlags(&L.stream, cudaStreamNonBlocking));
-        if (!L.done) HB_CUDA(cudaEventCreateWithFlags(&L.done, cudaEventDisableTiming));
         HB_TRY(grow(c, L.table, sizeof(uint64_t) * H));
         HB_TRY(grow(c, L.slot_r, sizeof(uint32_t) * (size_t)(n_r + 1)));
         HB_TRY(grow(c, L.count_r, sizeof(uint32_t) * (H + 1)));
@@ -1699,7 +1772,7 @@ extern "C" hb_status hb_get_stats(const hb_ctx *c, hb_stats *out) {
     for (const Buf *b : bufs) tot += b->bytes;
     for (const hb_ctx::MdLane &L : c->md_lanes) {
         const Buf *lb[] = {&L.table, &L.slot_r, &L.count_r, &L.start_r, &L.cursor, &L.slot_s, &L.count_s,
-                           &L.start_s, &L.scan, &L.meta};
+                           &L.start_s, &L.scan, &L.meta, &L.jac};
         for (const Buf *b : lb) tot += b->bytes;
     }
     out->device_bytes = (int64_t)tot;

@@ -171,6 +171,7 @@ struct hb_ctx {
     // block building of several MDs at once: per-lane scratch, side streams, events
     struct MdLane {
         Buf table, slot_r, count_r, start_r, cursor, slot_s, count_s, start_s, scan, meta;
+        Buf jac;   // q-gram encoder scratch when the lane encodes a Jaccard column
         cudaStream_t stream = nullptr;
         cudaEvent_t done = nullptr;
     };
