@@ -531,11 +531,12 @@ __device__ __forceinline__ Mask p1_filter(const uint32_t *__restrict__ hr, const
 // combination cb of other-key matches, own8 bit cb = the pair is owned, kf8
 // bit cb = it is kept even when every base filter fails (an owned pair is kept
 // when one passes: fm).  Returns the row's surviving columns; owned = its
-// owned (candidate) pairs.
+// owned (candidate) pairs; extra = the survivors of kf8 combinations (more MDs
+// alive than the block's base set; the others have exactly the base set).
 template <int KO, typename Mask>
 __device__ __forceinline__ Mask p1_combine(const Mask *em, Mask fm, uint32_t own8, uint32_t kf8, Mask vm,
-                                           unsigned &owned) {
-    Mask keep = 0;
+                                           unsigned &owned, Mask &extra) {
+    Mask keep = 0, ext = 0;
     owned = 0;
 #pragma unroll
     for (int cb = 0; cb < (1 << KO); cb++) {
@@ -544,19 +545,22 @@ __device__ __forceinline__ Mask p1_combine(const Mask *em, Mask fm, uint32_t own
 #pragma unroll
         for (int i = 0; i < KO; i++) mt &= ((cb >> i) & 1) ? em[i] : ~em[i];
         owned += (unsigned)pop(mt);
-        keep |= ((kf8 >> cb) & 1u) ? mt : (mt & fm);
+        const bool kf = (kf8 >> cb) & 1u;
+        keep |= kf ? mt : (mt & fm);
+        ext |= kf ? mt : (Mask)0;
     }
+    extra = ext;
     return keep;
 }
 
 // p1_row: the same for one row with at most one base filter (FK), in a single
 // pass over the columns (keys and filter together), then the decisions of
-// p1_combine applied inline; keep_out = surviving columns, owned_out = owned
-// (candidate) pairs.
+// p1_combine applied inline; keep_out = surviving columns, extra_out = those
+// of kf8 combinations, owned_out = owned (candidate) pairs.
 template <int KO, int FK, int T, typename Mask>
 __device__ __forceinline__ void p1_row(const uint32_t *__restrict__ hr, const uint32_t *__restrict__ hcols, int nc,
                                        const int *okey, const Op &op0, uint32_t own8, uint32_t kf8, Mask vm,
-                                       Mask &keep_out, unsigned &owned_out) {
+                                       Mask &keep_out, Mask &extra_out, unsigned &owned_out) {
     uint32_t rk[KO > 0 ? KO : 1];
     const uint32_t *ck[KO > 0 ? KO : 1];
 #pragma unroll
@@ -601,7 +605,7 @@ __device__ __forceinline__ void p1_row(const uint32_t *__restrict__ hr, const ui
     }
     if (FK == F_NONE) fm = ~(Mask)0;
     if (FK == F_RANGE && rnull) fm = 0;
-    Mask keep = 0;
+    Mask keep = 0, ext = 0;
     unsigned owned = 0;
 #pragma unroll
     for (int cb = 0; cb < (1 << KO); cb++) {
@@ -610,9 +614,12 @@ __device__ __forceinline__ void p1_row(const uint32_t *__restrict__ hr, const ui
 #pragma unroll
         for (int i = 0; i < KO; i++) mt &= ((cb >> i) & 1) ? em[i] : ~em[i];
         owned += (unsigned)pop(mt);
-        keep |= ((kf8 >> cb) & 1u) ? mt : (mt & fm);
+        const bool kf = (kf8 >> cb) & 1u;
+        keep |= kf ? mt : (mt & fm);
+        ext |= kf ? mt : (Mask)0;
     }
     keep_out = keep;
+    extra_out = ext;
     owned_out = owned;
 }
 
@@ -712,6 +719,9 @@ __global__ void __launch_bounds__(EV_THREADS, 4) k_eval(const __grid_constant__ 
     const uint32_t *rec_c = P.self_join ? P.rec_r : P.rec_s;
     const uint32_t *hot_c = P.self_join ? P.hot_r : P.hot_s;
     unsigned long long cand = 0, exam = 0;
+    // the row band whose hot records are staged (warp-uniform): consecutive
+    // tiles of one block share their rows, which are then not staged again
+    uint32_t rows_bi = 0xFFFFFFFFu, rows_ti = 0;
 
     for (;;) {
         unsigned long long t0 = 0;
@@ -720,13 +730,51 @@ __global__ void __launch_bounds__(EV_THREADS, 4) k_eval(const __grid_constant__ 
         if (t0 >= total) break;
         const uint64_t t1 = min((uint64_t)t0 + (uint64_t)P.claim, total);
         uint32_t bi = find_block(P.tile_prefix, nb, t0, lane);
+        // the next tile of the claim, located one tile ahead (warp-uniform), and
+        // its member ids (per lane), loaded while this tile is evaluated
+        bool nx_ok = false;
+        uint32_t nx_ti = 0, nx_tj = 0, nx_r[R], nx_c[R];
+#pragma unroll
+        for (int rr = 0; rr < R; rr++) nx_r[rr] = nx_c[rr] = 0;
         for (uint64_t t = t0; t < t1; t++) {
             while (P.tile_prefix[bi + 1] <= t) bi++;
             const BlockDesc B = P.blocks[HB_IDX(bi, nb, 1)];
             // pn > 0: a packed tile of self-join blocks of pn tuples, side by side
             const int pn = (int)B.packed;
             uint32_t ti = 0, tj = 0;
-            if (!pn) decode_tile(t - P.tile_prefix[bi], B.n_r, B.n_s, P.self_join, T, ti, tj);
+            const bool pre = nx_ok;   // this tile was located, and its member ids loaded, one tile ago
+            uint32_t pre_r[R], pre_c[R];
+#pragma unroll
+            for (int rr = 0; rr < R; rr++) {
+                pre_r[rr] = nx_r[rr];
+                pre_c[rr] = nx_c[rr];
+            }
+            if (pre) {
+                ti = nx_ti;
+                tj = nx_tj;
+            } else if (!pn) {
+                decode_tile(t - P.tile_prefix[bi], B.n_r, B.n_s, P.self_join, T, ti, tj);
+            }
+            const bool rows_kept = !pn && bi == rows_bi && ti == rows_ti;
+            nx_ok = false;
+            if (t + 1 < t1) {
+                uint32_t bj = bi;
+                while (P.tile_prefix[bj + 1] <= t + 1) bj++;
+                const BlockDesc B1 = P.blocks[HB_IDX(bj, nb, 1)];
+                if (!B1.packed) {
+                    decode_tile(t + 1 - P.tile_prefix[bj], B1.n_r, B1.n_s, P.self_join, T, nx_ti, nx_tj);
+                    const uint32_t nr1 = min((uint32_t)T, B1.n_r - nx_ti * T), nc1 = min((uint32_t)T, B1.n_s - nx_tj * T);
+                    const bool same_rows = bj == bi && nx_ti == ti;
+#pragma unroll
+                    for (int rr = 0; rr < R; rr++) {
+                        const uint32_t r = (uint32_t)(rr * 32 + lane);
+                        nx_r[rr] = (!same_rows && r < nr1)
+                                       ? P.members_r[HB_IDX(B1.start_r + nx_ti * T + r, P.members_r_len, 2)] : 0u;
+                        nx_c[rr] = r < nc1 ? P.members_s[HB_IDX(B1.start_s + nx_tj * T + r, P.members_s_len, 5)] : 0u;
+                    }
+                    nx_ok = true;
+                }
+            }
             const uint32_t r0 = ti * T, c0 = tj * T;
             const int nr = (int)min((uint32_t)T, B.n_r - r0);
             const int nc = (int)min((uint32_t)T, B.n_s - c0);
@@ -747,9 +795,10 @@ __global__ void __launch_bounds__(EV_THREADS, 4) k_eval(const __grid_constant__ 
                 if (pn && r < nr)
                     pid = P.members_r[HB_IDX(P.small[HB_IDX(B.start_r + r / pn, P.small_len, 3)] + r % pn,
                                              P.members_r_len, 4)];
-                if (r < nr) {
-                    const uint32_t id = HB_IDX(pn ? pid : P.members_r[HB_IDX(B.start_r + r0 + r, P.members_r_len, 2)],
-                                               P.n_r, 6);
+                if (r < nr && !rows_kept) {
+                    const uint32_t id =
+                        HB_IDX(pn ? pid : pre ? pre_r[rr] : P.members_r[HB_IDX(B.start_r + r0 + r, P.members_r_len, 2)],
+                               P.n_r, 6);
                     rid_s[r] = id;
                     const uint4 *src = reinterpret_cast<const uint4 *>(P.hot_r + (size_t)id * HW);
                     uint32_t *dst = hrows + r * HWP;
@@ -762,8 +811,9 @@ __global__ void __launch_bounds__(EV_THREADS, 4) k_eval(const __grid_constant__ 
                     }
                 }
                 if (r < nc) {
-                    const uint32_t id = HB_IDX(pn ? pid : P.members_s[HB_IDX(B.start_s + c0 + r, P.members_s_len, 5)],
-                                               P.self_join ? P.n_r : P.n_s, 7);
+                    const uint32_t id =
+                        HB_IDX(pn ? pid : pre ? pre_c[rr] : P.members_s[HB_IDX(B.start_s + c0 + r, P.members_s_len, 5)],
+                               P.self_join ? P.n_r : P.n_s, 7);
                     cid_s[r] = id;
                     const uint4 *src = reinterpret_cast<const uint4 *>(hot_c + (size_t)id * HW);
                     uint32_t *dst = hcols + r;   // word-major: word w of column c at w * T + c
@@ -777,6 +827,8 @@ __global__ void __launch_bounds__(EV_THREADS, 4) k_eval(const __grid_constant__ 
                 }
             }
             __syncwarp();
+            rows_bi = pn ? 0xFFFFFFFFu : bi;
+            rows_ti = ti;
             // ---- phase 1: every pair of the tile; lane = row, loop over the
             // columns; each lane collects the kept columns of its rows in a bit mask
             exam += pn ? (unsigned long long)(nr / pn) * (pn * (pn - 1) / 2)
@@ -814,7 +866,9 @@ __global__ void __launch_bounds__(EV_THREADS, 4) k_eval(const __grid_constant__ 
             // rejected if the first predicate of each of them fails its necessary
             // condition; any other owned pair goes on as it is
             const bool filt = !LOG && nbase != 255;
-            Mask kmask[R];
+            // kmask: surviving columns of each row; xmask: those whose alive set
+            // is more than the block's base set (the rest have exactly the base set)
+            Mask kmask[R], xmask[R];
             // fast path: at most 4 varying keys, and at most one base filter unless MULTI
             const bool fast = ko <= (MULTI ? 4 : 3) && (MULTI || !filt || nbase == 1);
             if (fast) {
@@ -826,7 +880,7 @@ __global__ void __launch_bounds__(EV_THREADS, 4) k_eval(const __grid_constant__ 
                     const int r = rr * 32 + lane;
                     const uint32_t *hr = hrows + r * HWP;
                     const Mask vm = valid_cols<Mask>(r, nr, nc, diag, pn);
-                    Mask km = 0;
+                    Mask km = 0, xm = 0;
                     unsigned ow = 0;
                     bool done = false;
                     if constexpr (MULTI) {
@@ -846,37 +900,38 @@ __global__ void __launch_bounds__(EV_THREADS, 4) k_eval(const __grid_constant__ 
                                                         : p1_filter<F_RANGE, T, Mask>(hr, hcols, nc, op);
                             }
                             switch (ko) {
-                            case 0: km = p1_combine<0, Mask>(em, fm, own8, kf8, vm, ow); break;
-                            case 1: km = p1_combine<1, Mask>(em, fm, own8, kf8, vm, ow); break;
-                            case 2: km = p1_combine<2, Mask>(em, fm, own8, kf8, vm, ow); break;
-                            case 3: km = p1_combine<3, Mask>(em, fm, own8, kf8, vm, ow); break;
-                            default: km = p1_combine<4, Mask>(em, fm, own8, kf8, vm, ow); break;
+                            case 0: km = p1_combine<0, Mask>(em, fm, own8, kf8, vm, ow, xm); break;
+                            case 1: km = p1_combine<1, Mask>(em, fm, own8, kf8, vm, ow, xm); break;
+                            case 2: km = p1_combine<2, Mask>(em, fm, own8, kf8, vm, ow, xm); break;
+                            case 3: km = p1_combine<3, Mask>(em, fm, own8, kf8, vm, ow, xm); break;
+                            default: km = p1_combine<4, Mask>(em, fm, own8, kf8, vm, ow, xm); break;
                             }
                             done = true;
                         } else if (ko == 4) {
                             switch (fk) {
-                            case F_NONE: p1_row<4, F_NONE, T>(hr, hcols, nc, okey, op0, own8, kf8, vm, km, ow); break;
-                            case F_RANGE: p1_row<4, F_RANGE, T>(hr, hcols, nc, okey, op0, own8, kf8, vm, km, ow); break;
-                            default: p1_row<4, F_ABS, T>(hr, hcols, nc, okey, op0, own8, kf8, vm, km, ow); break;
+                            case F_NONE: p1_row<4, F_NONE, T>(hr, hcols, nc, okey, op0, own8, kf8, vm, km, xm, ow); break;
+                            case F_RANGE: p1_row<4, F_RANGE, T>(hr, hcols, nc, okey, op0, own8, kf8, vm, km, xm, ow); break;
+                            default: p1_row<4, F_ABS, T>(hr, hcols, nc, okey, op0, own8, kf8, vm, km, xm, ow); break;
                             }
                             done = true;
                         }
                     }
                     if (!done) switch (ko * 3 + fk) {
-                    case 0: p1_row<0, F_NONE, T>(hr, hcols, nc, okey, op0, own8, kf8, vm, km, ow); break;
-                    case 1: p1_row<0, F_RANGE, T>(hr, hcols, nc, okey, op0, own8, kf8, vm, km, ow); break;
-                    case 2: p1_row<0, F_ABS, T>(hr, hcols, nc, okey, op0, own8, kf8, vm, km, ow); break;
-                    case 3: p1_row<1, F_NONE, T>(hr, hcols, nc, okey, op0, own8, kf8, vm, km, ow); break;
-                    case 4: p1_row<1, F_RANGE, T>(hr, hcols, nc, okey, op0, own8, kf8, vm, km, ow); break;
-                    case 5: p1_row<1, F_ABS, T>(hr, hcols, nc, okey, op0, own8, kf8, vm, km, ow); break;
-                    case 6: p1_row<2, F_NONE, T>(hr, hcols, nc, okey, op0, own8, kf8, vm, km, ow); break;
-                    case 7: p1_row<2, F_RANGE, T>(hr, hcols, nc, okey, op0, own8, kf8, vm, km, ow); break;
-                    case 8: p1_row<2, F_ABS, T>(hr, hcols, nc, okey, op0, own8, kf8, vm, km, ow); break;
-                    case 9: p1_row<3, F_NONE, T>(hr, hcols, nc, okey, op0, own8, kf8, vm, km, ow); break;
-                    case 10: p1_row<3, F_RANGE, T>(hr, hcols, nc, okey, op0, own8, kf8, vm, km, ow); break;
-                    default: p1_row<3, F_ABS, T>(hr, hcols, nc, okey, op0, own8, kf8, vm, km, ow); break;
+                    case 0: p1_row<0, F_NONE, T>(hr, hcols, nc, okey, op0, own8, kf8, vm, km, xm, ow); break;
+                    case 1: p1_row<0, F_RANGE, T>(hr, hcols, nc, okey, op0, own8, kf8, vm, km, xm, ow); break;
+                    case 2: p1_row<0, F_ABS, T>(hr, hcols, nc, okey, op0, own8, kf8, vm, km, xm, ow); break;
+                    case 3: p1_row<1, F_NONE, T>(hr, hcols, nc, okey, op0, own8, kf8, vm, km, xm, ow); break;
+                    case 4: p1_row<1, F_RANGE, T>(hr, hcols, nc, okey, op0, own8, kf8, vm, km, xm, ow); break;
+                    case 5: p1_row<1, F_ABS, T>(hr, hcols, nc, okey, op0, own8, kf8, vm, km, xm, ow); break;
+                    case 6: p1_row<2, F_NONE, T>(hr, hcols, nc, okey, op0, own8, kf8, vm, km, xm, ow); break;
+                    case 7: p1_row<2, F_RANGE, T>(hr, hcols, nc, okey, op0, own8, kf8, vm, km, xm, ow); break;
+                    case 8: p1_row<2, F_ABS, T>(hr, hcols, nc, okey, op0, own8, kf8, vm, km, xm, ow); break;
+                    case 9: p1_row<3, F_NONE, T>(hr, hcols, nc, okey, op0, own8, kf8, vm, km, xm, ow); break;
+                    case 10: p1_row<3, F_RANGE, T>(hr, hcols, nc, okey, op0, own8, kf8, vm, km, xm, ow); break;
+                    default: p1_row<3, F_ABS, T>(hr, hcols, nc, okey, op0, own8, kf8, vm, km, xm, ow); break;
                     }
                     kmask[rr] = km;
+                    xmask[rr] = xm;
                     cand += ow;
                 }
             } else {
@@ -885,7 +940,7 @@ __global__ void __launch_bounds__(EV_THREADS, 4) k_eval(const __grid_constant__ 
                     const int r = rr * 32 + lane;
                     const uint32_t *hr = hrows + r * HWP;
                     const Mask vm = valid_cols<Mask>(r, nr, nc, diag, pn);
-                    Mask km = 0;
+                    Mask km = 0, xm = 0;
                     for (int c = 0; c < nc; c++) {
                         const uint32_t *hc = hcols + c;
                         bool own, isbase;
@@ -917,22 +972,29 @@ __global__ void __launch_bounds__(EV_THREADS, 4) k_eval(const __grid_constant__ 
                         }
                         const Mask bit = (Mask)1 << c;
                         if (keep) km |= bit;
+                        if (own && !(filt && isbase)) xm |= bit;
                         if (own && (vm & bit)) cand++;
                     }
                     kmask[rr] = km & vm;
+                    xmask[rr] = xm & vm;
                 }
             }
-            // survivors, in rounds of at most SURV_CAP: a warp prefix sum of the
-            // per-lane counts places each lane's kept pairs in the warp's survivor
-            // list (a round takes the first SURV_CAP in lane order; the rest stay
-            // in the masks for the next round)
+            // survivors, by class (cls 0: alive set = the block's base set, the
+            // same for every pair of the class, so its screens are warp-uniform;
+            // cls 1: the others), each in rounds of at most SURV_CAP: a warp
+            // prefix sum of the per-lane counts places each lane's kept pairs in
+            // the warp's survivor list (a round takes the first SURV_CAP in lane
+            // order; the rest stay in the masks for the next round)
+#pragma unroll
+            for (int rr = 0; rr < R; rr++) kmask[rr] &= ~xmask[rr];
+            for (int cls = 0; cls < 2; cls++)
             for (;;) {
             int cnt;
             bool more;
             {
                 int my = 0;
 #pragma unroll
-                for (int rr = 0; rr < R; rr++) my += pop(kmask[rr]);
+                for (int rr = 0; rr < R; rr++) my += pop(cls ? xmask[rr] : kmask[rr]);
                 int incl = my;
 #pragma unroll
                 for (int o = 1; o < 32; o <<= 1) {
@@ -946,7 +1008,7 @@ __global__ void __launch_bounds__(EV_THREADS, 4) k_eval(const __grid_constant__ 
                 int pos = incl - my;
 #pragma unroll
                 for (int rr = 0; rr < R; rr++) {
-                    Mask mk = kmask[rr];
+                    Mask mk = cls ? xmask[rr] : kmask[rr];
                     const uint32_t rb = (uint32_t)(rr * 32 + lane) << 6;
                     while (mk && pos < SURV_CAP) {
                         const int c = first_bit(mk);
@@ -954,7 +1016,8 @@ __global__ void __launch_bounds__(EV_THREADS, 4) k_eval(const __grid_constant__ 
                         surv[HB_IDX(pos, SURV_CAP, 8)] = (uint16_t)(rb | (uint32_t)c);
                         pos++;
                     }
-                    kmask[rr] = mk;
+                    if (cls) xmask[rr] = mk;
+                    else kmask[rr] = mk;
                 }
             }
             __syncwarp();
@@ -967,12 +1030,13 @@ __global__ void __launch_bounds__(EV_THREADS, 4) k_eval(const __grid_constant__ 
                         const uint32_t e16 = surv[s];
                         const int r = (int)(e16 >> 6), c = (int)(e16 & 63u);
                         const uint32_t *hr = hrows + r * HWP, *hc = hcols + c;
-                        E = P.eqset[m];
-                        for (uint32_t ok = okeys; ok; ok &= ok - 1) {
-                            const int e = __ffs(ok) - 1;
-                            const uint32_t x = hr[e];
-                            E |= (x == hc[e * T] && x < NOMATCH_CODE) ? (1u << e) : 0u;
-                        }
+                        E = P.eqset[m];   // class 0: its alive set is alive_of(eqset[m]) = the base set
+                        if (cls)
+                            for (uint32_t ok = okeys; ok; ok &= ok - 1) {
+                                const int e = __ffs(ok) - 1;
+                                const uint32_t x = hr[e];
+                                E |= (x == hc[e * T] && x < NOMATCH_CODE) ? (1u << e) : 0u;
+                            }
                         ra = rid_s[r];
                         cb = cid_s[c];
                     }
@@ -993,15 +1057,19 @@ __global__ void __launch_bounds__(EV_THREADS, 4) k_eval(const __grid_constant__ 
                     const uint32_t e16 = surv[s];
                     const int r = (int)(e16 >> 6), c = (int)(e16 & 63u);
                     const uint32_t *hr = hrows + r * HWP, *hc = hcols + c;
+                    // class 0: the base set, whatever other keys match (its MDs all
+                    // have filters, so none is equality-only); class 1: from the keys
                     E = P.eqset[m];
-                    for (uint32_t ok = okeys; ok; ok &= ok - 1) {
-                        const int e = __ffs(ok) - 1;
-                        const uint32_t x = hr[e];
-                        E |= (x == hc[e * T] && x < NOMATCH_CODE) ? (1u << e) : 0u;
+                    uint64_t alive = base;
+                    if (cls) {
+                        for (uint32_t ok = okeys; ok; ok &= ok - 1) {
+                            const int e = __ffs(ok) - 1;
+                            const uint32_t x = hr[e];
+                            E |= (x == hc[e * T] && x < NOMATCH_CODE) ? (1u << e) : 0u;
+                        }
+                        alive = alive_of(P, lut, E);
                     }
-                    keep = true;
                     {
-                        const uint64_t alive = alive_of(P, lut, E);
                         keep = (alive & P.eqonly) != 0;
                         for (uint64_t a = alive & ~P.group_mds; a && !keep; a &= a - 1) {
                             const int j = __ffsll((long long)a) - 1;
