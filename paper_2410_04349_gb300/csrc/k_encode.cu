@@ -303,21 +303,23 @@ __device__ void write_gram_feature(uint32_t *r, uint32_t ucount, uint32_t start,
 }
 
 // One string's grams sorted by a group of G lanes holding E grams each (up to
-// E*G grams; E = 2 or 4): a bitonic network over the E*G elements, element
+// E*G grams; E = 4 or 8): a bitonic network over the E*G elements, element
 // e = E * (lane in group) + j.  Partners at a distance below E sit in the same
 // lane (a compare-exchange in registers), farther ones in another lane of the
 // group (a shuffle).  The unique grams are compacted (per-lane counts summed
 // over the group with ballots of their bits) and written in order; their 32
 // bin counts (at most 64 grams, so no 8-bit count saturates) and 64-bit
 // presence mask are summed in the warp's shared words.  e is the string's entry
-// (id, byte offset, length, first gram slot), by the lane's bytes E*gl ..
-// E*gl+E+2 of it (zero past the end), both loaded beforehand.
-constexpr int QG_LANE_BYTES = 7;   // E + 3 bytes for E = 4 grams of up to 4 bytes
-
+// (id, byte offset, length, first gram slot); a[0..2] are the lane's bytes
+// E*gl .. E*gl+11 of the string, byte t of the window in byte t % 4 of a[t / 4]
+// (loaded beforehand; bytes past the string's end are never part of a gram
+// that is kept).  Gram j is bytes j .. j+q-1 of the window, the first byte
+// most significant: one byte permutation (selector sel[j % 4]) of the word
+// pair that holds it, masked to q bytes.
 template <int G, int E>
-__device__ __forceinline__ void grams_group(int q, bool has, uint4 e, const uint32_t (&by)[QG_LANE_BYTES],
-                                            uint32_t *grams, uint64_t gcap, uint32_t *rec, int W, int feat,
-                                            uint32_t *acc) {
+__device__ __forceinline__ void grams_group(int q, uint32_t qmask, const uint32_t (&sel)[4], bool has, uint4 e,
+                                            const uint32_t (&a)[3], uint32_t *grams, uint64_t gcap, uint32_t *rec,
+                                            int W, int feat, uint32_t *acc) {
     const int lane = threadIdx.x & 31;
     const int gl = lane & (G - 1), gi = lane / G;
     const uint32_t i = e.x, gs = e.w;
@@ -326,10 +328,7 @@ __device__ __forceinline__ void grams_group(int q, bool has, uint4 e, const uint
     uint32_t v[E];
 #pragma unroll
     for (int j = 0; j < E; j++) {
-        uint32_t x = 0;
-#pragma unroll
-        for (int t = 0; t < 4; t++)
-            if (t < q) x = (x << 8) | by[j + t];
+        const uint32_t x = __byte_perm(a[j >> 2], a[(j >> 2) + 1], sel[j & 3]) & qmask;
         v[j] = k0 + j < g ? x : 0xFFFFFFFFu;
     }
 #pragma unroll
@@ -373,8 +372,9 @@ __device__ __forceinline__ void grams_group(int q, bool has, uint4 e, const uint
     const uint32_t gbits = (G == 32 ? 0xffffffffu : ((1u << G) - 1u)) << (gi * G);
     const uint32_t lower = gbits & ((1u << lane) - 1u);
     uint32_t pre = 0, ucount = 0;
+    constexpr int CNT_BITS = E == 8 ? 4 : E == 4 ? 3 : 2;
 #pragma unroll
-    for (int b = 0; b < (E == 4 ? 3 : 2); b++) {
+    for (int b = 0; b < CNT_BITS; b++) {
         const uint32_t bal = __ballot_sync(0xffffffffu, (cnt >> b) & 1u);
         pre += (uint32_t)__popc(bal & lower) << b;
         ucount += (uint32_t)__popc(bal & gbits) << b;
@@ -402,13 +402,13 @@ __device__ __forceinline__ void grams_group(int q, bool has, uint4 e, const uint
 }
 
 // Strings in bucket order (by gram count), in six classes: no grams (null or
-// shorter than q; a thread each), 1-8, 9-16, 17-32 and 33-64 grams (a group of
-// 4, 4, 8 or 16 lanes each, 2, 4, 4 and 4 grams to a lane), and more than 64
-// grams (a thread each, handed to the per-warp and per-block kernels).
-// bucket_end[b] is the end of bucket b in the order.  Warps walk the classes'
-// groups with a grid stride; the entries of the group two steps ahead and the
-// bytes of the next are loaded before a group is sorted, so the two dependent
-// loads of a string overlap the sorting.
+// shorter than q; a thread each), 1-8, 9-16, 17-32 and 33-64 grams (groups of
+// 2, 2, 4 and 8 lanes with 4, 8, 8 and 8 grams to a lane: 16, 16, 8 and 4
+// strings per warp), and more than 64 grams (a thread each, handed to the
+// per-warp and per-block kernels).  bucket_end[b] is the end of bucket b in the
+// order.  Warps walk the classes' groups with a grid stride; the entries of the
+// group two steps ahead and the bytes of the next are loaded before a group is
+// sorted, so the two dependent loads of a string overlap the sorting.
 constexpr int QG_COOP_THREADS = 256;
 
 struct CoopStep {
@@ -435,9 +435,9 @@ __device__ __forceinline__ CoopStep coop_step(uint32_t w, const uint32_t (&lo)[7
     const uint32_t wc = w - ws_c;
     uint32_t pos;
     if (c == 0 || c == 5) pos = lo_c + wc * 32u + (uint32_t)lane;
-    else if (c == 1 || c == 2) pos = lo_c + wc * 8u + (uint32_t)(lane >> 2);
-    else if (c == 3) pos = lo_c + wc * 4u + (uint32_t)(lane >> 3);
-    else pos = lo_c + wc * 2u + (uint32_t)(lane >> 4);
+    else if (c == 1 || c == 2) pos = lo_c + wc * 16u + (uint32_t)(lane >> 1);
+    else if (c == 3) pos = lo_c + wc * 8u + (uint32_t)(lane >> 2);
+    else pos = lo_c + wc * 4u + (uint32_t)(lane >> 3);
     st.c = c;
     st.pos = pos;
     st.has = pos < hi_c;
@@ -448,20 +448,25 @@ __device__ __forceinline__ uint4 coop_entry(const CoopStep &st, const uint4 *ent
     return st.has ? ent[st.pos] : make_uint4(0u, 0u, 0u, 0u);
 }
 
-// bytes E*gl .. E*gl+E+q-2 of the lane's string (group classes only; class 1
-// has groups of 4 lanes with 2 grams each, classes 2-4 groups of 4, 8 and 16
-// lanes with 4 grams each)
-__device__ __forceinline__ void coop_bytes(const CoopStep &st, uint4 e, const uint8_t *bytes, int q,
-                                           uint32_t (&by)[QG_LANE_BYTES]) {
+// the lane's 12-byte window E*gl .. E*gl+11 of its string (group classes only,
+// lanes holding at least one gram): four aligned words from the column's byte
+// array, shifted into place (byte arrays start 4-byte aligned and are padded
+// by 16 bytes, so the words past a string's end stay in bounds)
+__device__ __forceinline__ void coop_words(const CoopStep &st, uint4 e, const uint8_t *bytes, int q,
+                                           uint32_t (&a)[3]) {
     const int lane = threadIdx.x & 31;
-    const bool grp = st.has && st.c >= 1 && st.c <= 4;
-    const int G = st.c <= 2 ? 4 : st.c == 3 ? 8 : 16;
-    const int E = st.c == 1 ? 2 : 4;
+    const int G = st.c <= 2 ? 2 : st.c == 3 ? 4 : 8;
+    const int E = st.c == 1 ? 4 : 8;
     const uint32_t k0 = (uint32_t)(E * (lane & (G - 1)));
-#pragma unroll
-    for (int t = 0; t < QG_LANE_BYTES; t++) {
-        const uint32_t k = k0 + (uint32_t)t;
-        by[t] = (grp && t < E + q - 1 && k < e.z) ? (uint32_t)bytes[e.y + k] : 0u;
+    a[0] = a[1] = a[2] = 0u;
+    if (st.has && st.c >= 1 && st.c <= 4 && k0 + (uint32_t)q <= e.z) {
+        const uint32_t at = e.y + k0;
+        const uint32_t *wp = reinterpret_cast<const uint32_t *>(bytes) + (at >> 2);
+        const uint32_t w0 = __ldg(wp), w1 = __ldg(wp + 1), w2 = __ldg(wp + 2), w3 = __ldg(wp + 3);
+        const uint32_t s = 8u * (at & 3u);
+        a[0] = __funnelshift_r(w0, w1, s);
+        a[1] = __funnelshift_r(w1, w2, s);
+        a[2] = __funnelshift_r(w2, w3, s);
     }
 }
 
@@ -470,9 +475,19 @@ __global__ void __launch_bounds__(QG_COOP_THREADS) k_grams_coop(const uint8_t *b
                                                                 uint32_t *grams, uint64_t gcap, uint32_t *rec, int W,
                                                                 int feat, uint32_t *mid_list, unsigned int *n_mid,
                                                                 uint32_t *long_list, unsigned int *n_long) {
-    __shared__ uint32_t acc_all[QG_COOP_THREADS / 32][80];
+    __shared__ uint32_t acc_all[QG_COOP_THREADS / 32][160];
     uint32_t *acc = acc_all[threadIdx.x >> 5];
     const int lane = threadIdx.x & 31;
+    // byte selectors of a gram starting at window byte p (mod 4): result byte m
+    // (m < q) = window byte p + q - 1 - m; the bytes from q up are masked off
+    uint32_t sel[4];
+#pragma unroll
+    for (int p = 0; p < 4; p++) {
+        uint32_t x = 0;
+        for (int m = 0; m < q; m++) x |= (uint32_t)((p + q - 1 - m) & 7) << (4 * m);
+        sel[p] = x;
+    }
+    const uint32_t qmask = q >= 4 ? 0xFFFFFFFFu : ((1u << (8 * q)) - 1u);
     // class c covers order positions [lo[c], lo[c+1]) and takes per[c] strings per warp
     uint32_t lo[7];
     lo[0] = 0;
@@ -482,7 +497,7 @@ __global__ void __launch_bounds__(QG_COOP_THREADS) k_grams_coop(const uint8_t *b
     lo[4] = bucket_end[32];
     lo[5] = bucket_end[64];
     lo[6] = (uint32_t)n;
-    const uint32_t per[6] = {32, 8, 8, 4, 2, 32};
+    const uint32_t per[6] = {32, 16, 16, 8, 4, 32};
     uint32_t wstart[7];
     wstart[0] = 0;
 #pragma unroll
@@ -493,14 +508,14 @@ __global__ void __launch_bounds__(QG_COOP_THREADS) k_grams_coop(const uint8_t *b
     uint4 eA = coop_entry(A, ent);
     CoopStep B = coop_step(w + nw, lo, wstart, lane);
     uint4 eB = coop_entry(B, ent);
-    uint32_t bA[QG_LANE_BYTES];
-    coop_bytes(A, eA, bytes, q, bA);
+    uint32_t bA[3];
+    coop_words(A, eA, bytes, q, bA);
     while (A.c >= 0) {
         w += nw;
         const CoopStep C = coop_step(w + nw, lo, wstart, lane);
         const uint4 eC = coop_entry(C, ent);
-        uint32_t bB[QG_LANE_BYTES];
-        coop_bytes(B, eB, bytes, q, bB);
+        uint32_t bB[3];
+        coop_words(B, eB, bytes, q, bB);
         if (A.c == 0) {
             if (A.has) {
                 const uint32_t i = eA.x;
@@ -517,18 +532,18 @@ __global__ void __launch_bounds__(QG_COOP_THREADS) k_grams_coop(const uint8_t *b
                 else long_list[atomicAdd(n_long, 1u)] = eA.x;
             }
         } else if (A.c == 1) {
-            grams_group<4, 2>(q, A.has, eA, bA, grams, gcap, rec, W, feat, acc);
+            grams_group<2, 4>(q, qmask, sel, A.has, eA, bA, grams, gcap, rec, W, feat, acc);
         } else if (A.c == 2) {
-            grams_group<4, 4>(q, A.has, eA, bA, grams, gcap, rec, W, feat, acc);
+            grams_group<2, 8>(q, qmask, sel, A.has, eA, bA, grams, gcap, rec, W, feat, acc);
         } else if (A.c == 3) {
-            grams_group<8, 4>(q, A.has, eA, bA, grams, gcap, rec, W, feat, acc);
+            grams_group<4, 8>(q, qmask, sel, A.has, eA, bA, grams, gcap, rec, W, feat, acc);
         } else {
-            grams_group<16, 4>(q, A.has, eA, bA, grams, gcap, rec, W, feat, acc);
+            grams_group<8, 8>(q, qmask, sel, A.has, eA, bA, grams, gcap, rec, W, feat, acc);
         }
         A = B;
         eA = eB;
 #pragma unroll
-        for (int t = 0; t < QG_LANE_BYTES; t++) bA[t] = bB[t];
+        for (int t = 0; t < 3; t++) bA[t] = bB[t];
         B = C;
         eB = eC;
     }
