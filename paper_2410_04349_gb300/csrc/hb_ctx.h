@@ -179,7 +179,7 @@ struct hb_ctx {
     cudaEvent_t md_fork = nullptr;
     // autotuner cache: job-size signature -> (tile, claim)
     std::vector<std::pair<std::vector<int64_t>, std::pair<int, int>>> tune_cache;
-    int claim = 8;
+    int claim = 16;
     // planner statistics kept for the learned model: per predicate [len mean, len std, p10, p50, p90, max,
     // gram mean, gram std, null fraction, LSH bucket stddev], summarised on demand (ensure_pred_stats)
     // from the sampled lengths / gram counts ([predicate][stat_keep]) and bucket deviations
