@@ -723,6 +723,10 @@ __global__ void __launch_bounds__(EV_THREADS, 4) k_eval(const __grid_constant__ 
     // the row band whose hot records are staged (warp-uniform): consecutive
     // tiles of one block share their rows, which are then not staged again
     uint32_t rows_bi = 0xFFFFFFFFu, rows_ti = 0;
+    // the tile-level decision tables of the last MD seen (warp-uniform): its
+    // varying keys (4 x 8 bits), their count and the owned / base-set masks
+    uint32_t c_m = 0xFFFFFFFFu, c_okey = 0, c_own = 0, c_basem = 0;
+    int c_ko = 0;
 
     for (;;) {
         unsigned long long t0 = 0;
@@ -761,9 +765,18 @@ __global__ void __launch_bounds__(EV_THREADS, 4) k_eval(const __grid_constant__ 
             if (t + 1 < t1) {
                 uint32_t bj = bi;
                 while (P.tile_prefix[bj + 1] <= t + 1) bj++;
-                const BlockDesc B1 = P.blocks[HB_IDX(bj, nb, 1)];
+                const bool same_block = bj == bi;
+                const BlockDesc B1 = same_block ? B : P.blocks[HB_IDX(bj, nb, 1)];
                 if (!B1.packed) {
-                    decode_tile(t + 1 - P.tile_prefix[bj], B1.n_r, B1.n_s, P.self_join, T, nx_ti, nx_tj);
+                    if (same_block) {
+                        // the tile after (ti, tj) in the block's order: along the row band, then
+                        // the next band from its diagonal (self-join) or first column band
+                        const uint32_t ntc = (B.n_s + T - 1) / T;
+                        nx_ti = tj + 1 < ntc ? ti : ti + 1;
+                        nx_tj = tj + 1 < ntc ? tj + 1 : (P.self_join ? ti + 1 : 0u);
+                    } else {
+                        decode_tile(t + 1 - P.tile_prefix[bj], B1.n_r, B1.n_s, P.self_join, T, nx_ti, nx_tj);
+                    }
                     const uint32_t nr1 = min((uint32_t)T, B1.n_r - nx_ti * T), nc1 = min((uint32_t)T, B1.n_s - nx_tj * T);
                     const bool same_rows = bj == bi && nx_ti == ti;
 #pragma unroll
@@ -839,29 +852,37 @@ __global__ void __launch_bounds__(EV_THREADS, 4) k_eval(const __grid_constant__ 
             // works out, for the l-th combination of other-key matches, whether
             // the owner check passes and whether exactly the block's base MDs are
             // alive; each pair then reads its answer from two bit masks.
-            const int ko = __popc(okeys);
-            int okey[4] = {0, 0, 0, 0};
-            {
+            // (depend on the MD alone: worked out again only when it changes)
+            if (m != c_m) {
+                c_m = m;
+                c_ko = __popc(okeys);
+                int ok4[4] = {0, 0, 0, 0};
                 uint32_t ok = okeys;
 #pragma unroll
                 for (int i = 0; i < 4; i++) {
                     if (ok) {
-                        okey[i] = __ffs(ok) - 1;
+                        ok4[i] = __ffs(ok) - 1;
                         ok &= ok - 1;
                     }
                 }
-            }
-            uint32_t ownmask = 0, basemask = 0;
-            if (ko <= 4) {
-                uint32_t E = P.eqset[m];
+                c_okey = (uint32_t)ok4[0] | ((uint32_t)ok4[1] << 8) | ((uint32_t)ok4[2] << 16) | ((uint32_t)ok4[3] << 24);
+                c_own = c_basem = 0;
+                if (c_ko <= 4) {
+                    uint32_t E = P.eqset[m];
 #pragma unroll
-                for (int i = 0; i < 4; i++)
-                    if (i < ko && ((lane >> i) & 1)) E |= 1u << okey[i];
-                const bool in = lane < (1 << ko);
-                const uint64_t al = in ? alive_of(P, lut, E) : 0ull;
-                ownmask = __ballot_sync(0xffffffffu, in && (al & mbit) && !(al & below));
-                basemask = __ballot_sync(0xffffffffu, in && al == base);
+                    for (int i = 0; i < 4; i++)
+                        if (i < c_ko && ((lane >> i) & 1)) E |= 1u << ok4[i];
+                    const bool in = lane < (1 << c_ko);
+                    const uint64_t al = in ? alive_of(P, lut, E) : 0ull;
+                    c_own = __ballot_sync(0xffffffffu, in && (al & mbit) && !(al & below));
+                    c_basem = __ballot_sync(0xffffffffu, in && al == base);
+                }
             }
+            const int ko = c_ko;
+            int okey[4];
+#pragma unroll
+            for (int i = 0; i < 4; i++) okey[i] = (int)((c_okey >> (8 * i)) & 255u);
+            const uint32_t ownmask = c_own, basemask = c_basem;
             // the MDs alive for every pair of this block (the owner and those whose
             // keys are a subset of its keys): when no other MD is alive, a pair is
             // rejected if the first predicate of each of them fails its necessary
