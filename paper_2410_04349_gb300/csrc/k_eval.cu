@@ -715,6 +715,15 @@ __global__ void __launch_bounds__(EV_THREADS, 4) k_eval(const __grid_constant__ 
 
     const uint32_t nb = *P.n_blocks;
     const uint64_t total = P.tile_prefix[nb];
+    // tiles per claim: at most P.claim, and few enough that every warp gets about
+    // 8 claims (small launches would otherwise end on a few warps' last claims);
+    // kept in shared memory, read once per claim
+    __shared__ unsigned s_claim;
+    if (threadIdx.x == 0) {
+        const uint64_t per = total / ((uint64_t)gridDim.x * (blockDim.x >> 5) * 8);
+        s_claim = (unsigned)max((uint64_t)1, min((uint64_t)P.claim, per));
+    }
+    __syncthreads();
     const unsigned lt = (1u << lane) - 1u;
     const uint32_t allkeys = P.keymask;
     const uint32_t *rec_c = P.self_join ? P.rec_r : P.rec_s;
@@ -724,16 +733,18 @@ __global__ void __launch_bounds__(EV_THREADS, 4) k_eval(const __grid_constant__ 
     // tiles of one block share their rows, which are then not staged again
     uint32_t rows_bi = 0xFFFFFFFFu, rows_ti = 0;
     // the tile-level decision tables of the last MD seen (warp-uniform): its
-    // varying keys (4 x 8 bits), their count and the owned / base-set masks
+    // varying keys (4 x 8 bits), their count, the owned / base-set masks, its
+    // base filter count and the program index of its first base filter
     uint32_t c_m = 0xFFFFFFFFu, c_okey = 0, c_own = 0, c_basem = 0;
-    int c_ko = 0;
+    int c_ko = 0, c_nbase = 0, c_op0 = 0;
 
     for (;;) {
         unsigned long long t0 = 0;
-        if (lane == 0) t0 = atomicAdd(P.tile_counter, (unsigned long long)P.claim);
+        const unsigned claim = s_claim;
+        if (lane == 0) t0 = atomicAdd(P.tile_counter, (unsigned long long)claim);
         t0 = __shfl_sync(0xffffffffu, t0, 0);
         if (t0 >= total) break;
-        const uint64_t t1 = min((uint64_t)t0 + (uint64_t)P.claim, total);
+        const uint64_t t1 = min((uint64_t)t0 + (uint64_t)claim, total);
         uint32_t bi = find_block(P.tile_prefix, nb, t0, lane);
         // the next tile of the claim, located one tile ahead (warp-uniform), and
         // its member ids (per lane), loaded while this tile is evaluated
@@ -798,8 +809,46 @@ __global__ void __launch_bounds__(EV_THREADS, 4) k_eval(const __grid_constant__ 
             const uint64_t below = (mbit - 1ull) & P.owner_mds;
             const uint32_t okeys = allkeys & ~(uint32_t)P.eqset[m];
             const uint64_t base = P.base_alive[m];
-            const int nbase = P.base_nops[m];
-            const Op op0 = P.ops[(nbase != 255 && nbase > 0) ? P.base_op[m][0] : 0];
+            // The equality keys of the owner MD hold for every pair of its block;
+            // only the other keys (okeys) vary.  With at most 4 of them, lane l
+            // works out, for the l-th combination of other-key matches, whether
+            // the owner check passes and whether exactly the block's base MDs are
+            // alive; each pair then reads its answer from two bit masks.
+            // (depend on the MD alone: worked out again only when it changes)
+            if (m != c_m) {
+                c_m = m;
+                c_nbase = P.base_nops[m];
+                c_op0 = (c_nbase != 255 && c_nbase > 0) ? P.base_op[m][0] : 0;
+                c_ko = __popc(okeys);
+                int ok4[4] = {0, 0, 0, 0};
+                uint32_t ok = okeys;
+#pragma unroll
+                for (int i = 0; i < 4; i++) {
+                    if (ok) {
+                        ok4[i] = __ffs(ok) - 1;
+                        ok &= ok - 1;
+                    }
+                }
+                c_okey = (uint32_t)ok4[0] | ((uint32_t)ok4[1] << 8) | ((uint32_t)ok4[2] << 16) | ((uint32_t)ok4[3] << 24);
+                c_own = c_basem = 0;
+                if (c_ko <= 4) {
+                    uint32_t E = P.eqset[m];
+#pragma unroll
+                    for (int i = 0; i < 4; i++)
+                        if (i < c_ko && ((lane >> i) & 1)) E |= 1u << ok4[i];
+                    const bool in = lane < (1 << c_ko);
+                    const uint64_t al = in ? alive_of(P, lut, E) : 0ull;
+                    c_own = __ballot_sync(0xffffffffu, in && (al & mbit) && !(al & below));
+                    c_basem = __ballot_sync(0xffffffffu, in && al == base);
+                }
+            }
+            const int ko = c_ko;
+            int okey[4];
+#pragma unroll
+            for (int i = 0; i < 4; i++) okey[i] = (int)((c_okey >> (8 * i)) & 255u);
+            const uint32_t ownmask = c_own, basemask = c_basem;
+            const int nbase = c_nbase;
+            const Op op0 = P.ops[c_op0];
             // ---- stage the hot records of the tile's rows and columns
             __syncwarp();
 #pragma unroll
@@ -847,42 +896,6 @@ __global__ void __launch_bounds__(EV_THREADS, 4) k_eval(const __grid_constant__ 
             // columns; each lane collects the kept columns of its rows in a bit mask
             exam += pn ? (unsigned long long)(nr / pn) * (pn * (pn - 1) / 2)
                        : diag ? (unsigned long long)nr * (nr - 1) / 2 : (unsigned long long)nr * nc;
-            // The equality keys of the owner MD hold for every pair of its block;
-            // only the other keys (okeys) vary.  With at most 4 of them, lane l
-            // works out, for the l-th combination of other-key matches, whether
-            // the owner check passes and whether exactly the block's base MDs are
-            // alive; each pair then reads its answer from two bit masks.
-            // (depend on the MD alone: worked out again only when it changes)
-            if (m != c_m) {
-                c_m = m;
-                c_ko = __popc(okeys);
-                int ok4[4] = {0, 0, 0, 0};
-                uint32_t ok = okeys;
-#pragma unroll
-                for (int i = 0; i < 4; i++) {
-                    if (ok) {
-                        ok4[i] = __ffs(ok) - 1;
-                        ok &= ok - 1;
-                    }
-                }
-                c_okey = (uint32_t)ok4[0] | ((uint32_t)ok4[1] << 8) | ((uint32_t)ok4[2] << 16) | ((uint32_t)ok4[3] << 24);
-                c_own = c_basem = 0;
-                if (c_ko <= 4) {
-                    uint32_t E = P.eqset[m];
-#pragma unroll
-                    for (int i = 0; i < 4; i++)
-                        if (i < c_ko && ((lane >> i) & 1)) E |= 1u << ok4[i];
-                    const bool in = lane < (1 << c_ko);
-                    const uint64_t al = in ? alive_of(P, lut, E) : 0ull;
-                    c_own = __ballot_sync(0xffffffffu, in && (al & mbit) && !(al & below));
-                    c_basem = __ballot_sync(0xffffffffu, in && al == base);
-                }
-            }
-            const int ko = c_ko;
-            int okey[4];
-#pragma unroll
-            for (int i = 0; i < 4; i++) okey[i] = (int)((c_okey >> (8 * i)) & 255u);
-            const uint32_t ownmask = c_own, basemask = c_basem;
             // the MDs alive for every pair of this block (the owner and those whose
             // keys are a subset of its keys): when no other MD is alive, a pair is
             // rejected if the first predicate of each of them fails its necessary
