@@ -755,24 +755,24 @@ static hb_status plan_stats(hb_ctx *c, std::vector<double> &sp, std::vector<doub
         specs[p] = s;
     }
     Buf tmp;
-    size_t bytes = sizeof(SampleSpec) * P + sizeof(uint32_t) * ((size_t)P * K + P + 2 * (size_t)P * n_keep) + 1024;
+    size_t bytes = sizeof(SampleSpec) * P + sizeof(uint32_t) * ((size_t)P * K + 2 * (size_t)P * n_keep) + 1024;
     HB_TRY(grow(c, tmp, bytes));
     char *base = static_cast<char *>(tmp.p);
     SampleSpec *d_specs = reinterpret_cast<SampleSpec *>(base);
     uint32_t *hist = reinterpret_cast<uint32_t *>(base + ((sizeof(SampleSpec) * P + 255) & ~size_t(255)));
-    uint32_t *present = hist + (size_t)P * K;
-    uint32_t *lens = present + P;
+    uint32_t *lens = hist + (size_t)P * K;
     uint32_t *grams = lens + (size_t)P * n_keep;
     HB_CUDA(cudaMemcpyAsync(d_specs, specs.data(), sizeof(SampleSpec) * P, cudaMemcpyHostToDevice, c->stream));
-    HB_CUDA(cudaMemsetAsync(hist, 0, sizeof(uint32_t) * ((size_t)P * K + P), c->stream));
-    lsh_hist(d_specs, P, R.n, n_samples, K, hist, present, lens, grams, n_keep, c->stream);
-    std::vector<uint32_t> h((size_t)P * K + P + 2 * (size_t)P * n_keep);
+    HB_CUDA(cudaMemsetAsync(hist, 0, sizeof(uint32_t) * (size_t)P * K, c->stream));
+    lsh_hist(d_specs, P, R.n, n_samples, K, hist, lens, grams, n_keep, c->stream);
+    std::vector<uint32_t> h((size_t)P * K + 2 * (size_t)P * n_keep);
     HB_CUDA(cudaMemcpyAsync(h.data(), hist, sizeof(uint32_t) * h.size(), cudaMemcpyDeviceToHost, c->stream));
     HB_CUDA(cudaStreamSynchronize(c->stream));
     free_buf(c, tmp);
     std::vector<double> sd(P, 0.0);
     for (int p = 0; p < P; p++) {
-        const double n = h[(size_t)P * K + p];
+        double n = 0;   // sampled values present: every one is in exactly one bucket
+        for (int b = 0; b < K; b++) n += h[(size_t)p * K + b];
         double acc = 0;
         for (int b = 0; b < K; b++) {
             double d = h[(size_t)p * K + b] - n / K;
@@ -784,8 +784,8 @@ static hb_status plan_stats(hb_ctx *c, std::vector<double> &sp, std::vector<doub
         double mlen = 0, mg = 0;
         int cnt = 0;
         for (int s = 0; s < n_keep; s++) {
-            uint32_t L = h[(size_t)P * K + P + (size_t)p * n_keep + s];
-            uint32_t G = h[(size_t)P * K + P + (size_t)P * n_keep + (size_t)p * n_keep + s];
+            uint32_t L = h[(size_t)P * K + (size_t)p * n_keep + s];
+            uint32_t G = h[(size_t)P * K + (size_t)P * n_keep + (size_t)p * n_keep + s];
             if (L == NULL_LEN) continue;
             mlen += L;
             mg += G;

@@ -285,7 +285,7 @@ struct SampleSpec {
     int32_t pad;
 };
 void lsh_hist(const SampleSpec *specs_dev, int n_preds, int64_t n_rows, int n_samples, int k_buckets,
-              uint32_t *hist, uint32_t *present, uint32_t *lens, uint32_t *grams, int n_keep, cudaStream_t s);
+              uint32_t *hist, uint32_t *lens, uint32_t *grams, int n_keep, cudaStream_t s);
 
 // planner.cpp
 struct PlanResult {

@@ -227,13 +227,20 @@ __global__ void k_small_plan(uint32_t *meta, int tile, uint32_t small_cap, unsig
     meta[SmallMeta::TILES + SMALL_MAX + 1] = tp;
 }
 
+// (lanes of a warp holding blocks of one size take their positions with one
+// atomic: the size classes' cursors are only 15 counters)
 __global__ void k_small_scatter(const uint32_t *count, const uint32_t *start, uint64_t cap, uint32_t member_base,
                                 uint32_t *meta, uint32_t *small, uint32_t small_cap) {
     const int64_t sl = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (sl >= (int64_t)cap) return;
-    const uint32_t n = count[sl];
-    if (n < 2 || n > (uint32_t)SMALL_MAX) return;
-    const uint32_t pos = meta[SmallMeta::OFF + n] + atomicAdd(&meta[SmallMeta::CURSOR + n], 1u);
+    const uint32_t n = sl < (int64_t)cap ? count[sl] : 0u;
+    const bool is_small = n >= 2 && n <= (uint32_t)SMALL_MAX;
+    const unsigned peers = __match_any_sync(0xffffffffu, is_small ? n : 0u);
+    if (!is_small) return;
+    const int lane = threadIdx.x & 31, leader = __ffs(peers) - 1;
+    uint32_t b = 0;
+    if (lane == leader) b = atomicAdd(&meta[SmallMeta::CURSOR + n], (uint32_t)__popc(peers));
+    b = __shfl_sync(peers, b, leader);
+    const uint32_t pos = meta[SmallMeta::OFF + n] + b + (uint32_t)__popc(peers & ((1u << lane) - 1u));
     if (pos < small_cap) small[pos] = member_base + start[sl];
 }
 

@@ -33,8 +33,11 @@ __device__ __forceinline__ uint64_t shash_bytes(const uint8_t *p, uint32_t n) {
     return smix(h);
 }
 
+// (the number of sampled values present is the sum of a predicate's bucket
+// counts: the host adds them up, instead of every sample adding one to a
+// single counter)
 __global__ void k_lsh_hist(const SampleSpec *specs, int n_preds, int64_t n_rows, int n_samples, int k_buckets,
-                           uint32_t *hist, uint32_t *present, uint32_t *lens, uint32_t *grams, int n_keep) {
+                           uint32_t *hist, uint32_t *lens, uint32_t *grams, int n_keep) {
     const int p = blockIdx.y;
     const SampleSpec sp = specs[p];
     for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n_samples; s += gridDim.x * blockDim.x) {
@@ -79,7 +82,6 @@ __global__ void k_lsh_hist(const SampleSpec *specs, int n_preds, int64_t n_rows,
             h = smix((uint64_t)(int64_t)cell);
         }
         atomicAdd(&hist[(int64_t)p * k_buckets + (h % (uint64_t)k_buckets)], 1u);
-        atomicAdd(&present[p], 1u);
         if (s < n_keep) {
             lens[(int64_t)p * n_keep + s] = len;
             grams[(int64_t)p * n_keep + s] = ng;
@@ -90,12 +92,11 @@ __global__ void k_lsh_hist(const SampleSpec *specs, int n_preds, int64_t n_rows,
 }  // namespace
 
 void lsh_hist(const SampleSpec *specs_dev, int n_preds, int64_t n_rows, int n_samples, int k_buckets,
-              uint32_t *hist, uint32_t *present, uint32_t *lens, uint32_t *grams, int n_keep, cudaStream_t s) {
+              uint32_t *hist, uint32_t *lens, uint32_t *grams, int n_keep, cudaStream_t s) {
     if (n_preds == 0 || n_rows == 0) return;
     dim3 grid((unsigned)((n_samples + 255) / 256), (unsigned)n_preds);
     HB_LAUNCHED(1);
-    k_lsh_hist<<<grid, 256, 0, s>>>(specs_dev, n_preds, n_rows, n_samples, k_buckets, hist, present, lens, grams,
-                                    n_keep);
+    k_lsh_hist<<<grid, 256, 0, s>>>(specs_dev, n_preds, n_rows, n_samples, k_buckets, hist, lens, grams, n_keep);
 }
 
 }  // namespace hb
