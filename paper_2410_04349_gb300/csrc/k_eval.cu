@@ -2,15 +2,17 @@
 //
 // Work items are tiles of a block's pair space (T x T tuples, the upper
 // triangle for a self-join), or packed tiles holding several small self-join
-// blocks side by side.  A persistent grid of warps claims tiles (8 per claim)
-// from one atomic counter (task stealing in the form of a shared queue,
-// Section 5.2).  Each warp works on one tile at a time:
+// blocks side by side.  A persistent grid of warps claims tiles (up to 16 per
+// claim) from one atomic counter (task stealing in the form of a shared queue,
+// Section 5.2).  Each warp works on one tile at a time; consecutive tiles of a
+// claim mostly share their row band, whose staged records are then kept, and
+// the next tile's member ids are loaded while the current one is evaluated:
 //
 //  phase 1 (every pair, branch-light): the warp stages the tile's "hot"
 //    records (equality codes, the filter operand of each MD's first predicate
 //    and, within a word budget, bins and second-predicate operands) in shared
 //    memory, rows tuple-major and columns word-major; lane = row, loop over
-//    the columns 8 at a time.  For every pair:
+//    the columns 4 at a time.  For every pair:
 //      - equality keys: bit e of E is set when both tuples hold the same
 //        present code of key e; the MDs whose keys are all in E are alive;
 //      - owner check: the pair is handled only in the block of the lowest
@@ -26,8 +28,9 @@
 //    per-warp survivor list.
 //  phase 1b (when the hot record holds more than phase 1 used): each survivor
 //    is screened with the staged necessary conditions of every alive MD's
-//    first two predicates (shared memory only) and the rest join a per-warp
-//    ring spanning tiles, so phase 2 always runs 32 pairs at a time.
+//    first two predicates (shared memory only; the survivors whose alive set
+//    is the block's base set first, with warp-uniform ops) and the rest join
+//    a per-warp ring spanning tiles, so phase 2 always runs 32 pairs at a time.
 //  phase 2 (survivors, 32 at a time, all lanes busy): the sequential execution
 //    path of Section 5.1 on the full records: non-equality predicates in plan
 //    order, each evaluated once per pair and its result applied to every MD
