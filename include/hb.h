@@ -245,6 +245,36 @@ HB_API hb_status hb_plan(hb_ctx *ctx, int32_t mode, hb_plan_info *info_out);
 HB_API hb_status hb_set_partitions(hb_ctx *ctx, uint32_t m);
 
 /*
+ * Sharded evaluation over `world` processes, each with a GPU of its own (a
+ * build addition: the paper spreads partitions over GPUs, Section 5.3
+ * "Multi-GPU scheduling"; here the unit of work is a block).  Every process
+ * loads the same tables and rules and encodes and groups them alike; a block
+ * (one MD's group of tuples that agree on its equality keys, with all the
+ * pairs the owner rule gives that MD) is evaluated by rank
+ *     (fmix32(r ^ (md * 0x9E3779B9)) mod world),
+ * r = the smallest row id of the group (of R in R x S) and fmix32 the 32-bit
+ * finaliser of MurmurHash3 (h ^= h >> 16; h *= 0x85EBCA6B; h ^= h >> 13;
+ * h *= 0xC2B2AE35; h ^= h >> 16), a function of the data alone.  hb_block and
+ * hb_block_device then return this rank's pairs, sorted; the ranks' outputs are
+ * disjoint and their union is the unsharded result (merge them with
+ * hb_merge_pairs).  Candidate counts in hb_get_stats are this rank's.
+ * 0 <= rank < world, else HB_ERR_ARG; world = 1 (the default) evaluates every
+ * block.  hb_block_stream and hb_block_batch return HB_ERR_STATE while
+ * world > 1.  Applies from the next hb_block.
+ */
+HB_API hb_status hb_set_shard(hb_ctx *ctx, int32_t rank, int32_t world);
+
+/*
+ * Host-side k-way merge (a build addition: the final gather step of a sharded
+ * evaluation): lists[l] holds counts[l] pairs sorted ascending by (tid1, tid2);
+ * out (caller-allocated, sum of counts entries) receives all of them sorted
+ * the same way (pairs equal across lists are all kept, list order among
+ * them).  Reads and writes host memory only; no GPU is needed.  HB_ERR_ARG on
+ * k < 0, a negative count, or a NULL array where a count is positive.
+ */
+HB_API hb_status hb_merge_pairs(const hb_pair *const *lists, const int64_t *counts, int32_t k, hb_pair *out);
+
+/*
  * Compute Ca for the loaded tables (self-join when only R is loaded).
  * *pairs_out receives a library-allocated host array of *n_out pairs sorted
  * ascending by (tid1, tid2), unique; free it with hb_free_pairs.  Plans with

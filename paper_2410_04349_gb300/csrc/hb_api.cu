@@ -309,7 +309,7 @@ extern "C" void hb_destroy(hb_ctx *c) {
     for (hb_ctx::MdLane &L : c->md_lanes) {
         if (L.stream) cudaStreamSynchronize(L.stream);
         Buf *lb[] = {&L.table, &L.slot_r, &L.count_r, &L.start_r, &L.cursor, &L.slot_s, &L.count_s, &L.start_s,
-                     &L.scan, &L.meta, &L.jac};
+                     &L.scan, &L.meta, &L.jac, &L.minrow};
         for (Buf *b : lb) free_buf(c, *b);
         if (L.done) cudaEventDestroy(L.done);
         if (L.stream) cudaStreamDestroy(L.stream);
@@ -1131,6 +1131,44 @@ extern "C" hb_status hb_set_partitions(hb_ctx *c, uint32_t m) {
     return HB_OK;
 }
 
+extern "C" hb_status hb_set_shard(hb_ctx *c, int32_t rank, int32_t world) {
+    if (!c) return fail(HB_ERR_ARG, "hb_set_shard: ctx is NULL");
+    if (world < 1 || rank < 0 || rank >= world) return fail(HB_ERR_ARG, "hb_set_shard: need 0 <= rank < world");
+    c->shard_rank = (uint32_t)rank;
+    c->shard_world = (uint32_t)world;
+    return HB_OK;
+}
+
+extern "C" hb_status hb_merge_pairs(const hb_pair *const *lists, const int64_t *counts, int32_t k, hb_pair *out) {
+    if (k < 0 || (k > 0 && (!lists || !counts))) return fail(HB_ERR_ARG, "hb_merge_pairs: lists or counts is NULL");
+    int64_t total = 0;
+    for (int32_t l = 0; l < k; l++) {
+        if (counts[l] < 0 || (counts[l] > 0 && !lists[l])) return fail(HB_ERR_ARG, "hb_merge_pairs: bad list");
+        total += counts[l];
+    }
+    if (total > 0 && !out) return fail(HB_ERR_ARG, "hb_merge_pairs: out is NULL");
+    // a binary heap of (next pair, list) ordered by (tid1, tid2, list)
+    auto key = [](const hb_pair &p) { return ((uint64_t)p.tid1 << 32) | (uint64_t)p.tid2; };
+    std::vector<std::pair<uint64_t, int32_t>> heap;
+    std::vector<int64_t> pos(k > 0 ? k : 1, 0);
+    for (int32_t l = 0; l < k; l++)
+        if (counts[l] > 0) heap.push_back({key(lists[l][0]), l});
+    auto greater = [](const std::pair<uint64_t, int32_t> &a, const std::pair<uint64_t, int32_t> &b) { return a > b; };
+    std::make_heap(heap.begin(), heap.end(), greater);
+    int64_t o = 0;
+    while (!heap.empty()) {
+        std::pop_heap(heap.begin(), heap.end(), greater);
+        const int32_t l = heap.back().second;
+        heap.pop_back();
+        out[o++] = lists[l][pos[l]++];
+        if (pos[l] < counts[l]) {
+            heap.push_back({key(lists[l][pos[l]]), l});
+            std::push_heap(heap.begin(), heap.end(), greater);
+        }
+    }
+    return HB_OK;
+}
+
 extern "C" hb_status hb_plan(hb_ctx *c, int32_t mode, hb_plan_info *info_out) {
     if (!c) return fail(HB_ERR_ARG, "hb_plan: ctx is NULL");
     HB_TRY(do_plan(c, mode, false));
@@ -1439,6 +1477,7 @@ hb_status build_blocks(hb_ctx *c, const uint32_t *rec_r, int64_t n_r, const uint
         HB_TRY(grow(c, L.cursor, sizeof(uint32_t) * (H + 1)));
         HB_TRY(grow(c, L.scan, scan_tmp_bytes((int64_t)H + 1)));
         if (self) HB_TRY(grow(c, L.meta, sizeof(uint32_t) * SMALL_META_WORDS));
+        if (c->shard_world > 1) HB_TRY(grow(c, L.minrow, sizeof(uint32_t) * (H + 1)));
         if (!self) {
             HB_TRY(grow(c, L.slot_s, sizeof(uint32_t) * (size_t)(n_s + 1)));
             HB_TRY(grow(c, L.count_s, sizeof(uint32_t) * (H + 1)));
@@ -1463,6 +1502,9 @@ hb_status build_blocks(hb_ctx *c, const uint32_t *rec_r, int64_t n_r, const uint
         HB_CUDA(cudaMemsetAsync(L.cursor.p, 0, sizeof(uint32_t) * (H + 1), st));
         uint32_t *mem_r = as<uint32_t>(c->w_members_r) + (size_t)a * (size_t)std::max<int64_t>(n_r, 1);
         scatter_slots(as<uint32_t>(L.slot_r), n_r, as<uint32_t>(L.start_r), as<uint32_t>(L.cursor), mem_r, st);
+        if (self && c->shard_world > 1)
+            shard_filter(as<uint32_t>(L.slot_r), n_r, as<uint32_t>(L.count_r), nullptr, as<uint32_t>(L.minrow), H,
+                         (uint32_t)m, c->shard_rank, c->shard_world, st);
         if (self) {
             emit_blocks_packed(as<uint32_t>(L.count_r), as<uint32_t>(L.start_r), H, (uint32_t)m,
                                (uint32_t)((size_t)a * (size_t)std::max<int64_t>(n_r, 1)), c->tile,
@@ -1478,6 +1520,9 @@ hb_status build_blocks(hb_ctx *c, const uint32_t *rec_r, int64_t n_r, const uint
             HB_CUDA(cudaMemsetAsync(L.cursor.p, 0, sizeof(uint32_t) * (H + 1), st));
             uint32_t *mem_s = as<uint32_t>(c->w_members_s) + (size_t)a * (size_t)std::max<int64_t>(n_s, 1);
             scatter_slots(as<uint32_t>(L.slot_s), n_s, as<uint32_t>(L.start_s), as<uint32_t>(L.cursor), mem_s, st);
+            if (c->shard_world > 1)
+                shard_filter(as<uint32_t>(L.slot_r), n_r, as<uint32_t>(L.count_r), as<uint32_t>(L.count_s),
+                             as<uint32_t>(L.minrow), H, (uint32_t)m, c->shard_rank, c->shard_world, st);
             emit_blocks(as<uint32_t>(L.count_r), as<uint32_t>(L.start_r), as<uint32_t>(L.count_s),
                         as<uint32_t>(L.start_s), H, (uint32_t)m, 0,
                         (uint32_t)((size_t)a * (size_t)std::max<int64_t>(n_r, 1)),
@@ -1772,7 +1817,7 @@ extern "C" hb_status hb_get_stats(const hb_ctx *c, hb_stats *out) {
     for (const Buf *b : bufs) tot += b->bytes;
     for (const hb_ctx::MdLane &L : c->md_lanes) {
         const Buf *lb[] = {&L.table, &L.slot_r, &L.count_r, &L.start_r, &L.cursor, &L.slot_s, &L.count_s,
-                           &L.start_s, &L.scan, &L.meta, &L.jac};
+                           &L.start_s, &L.scan, &L.meta, &L.jac, &L.minrow};
         for (const Buf *b : lb) tot += b->bytes;
     }
     out->device_bytes = (int64_t)tot;

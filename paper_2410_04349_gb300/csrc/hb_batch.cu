@@ -294,6 +294,7 @@ extern "C" hb_status hb_block_batch(hb_ctx *c, int32_t n_jobs, const int64_t *jo
     *pairs_out = nullptr;
     if (n_jobs < 1) return fail(HB_ERR_ARG, "hb_block_batch: n_jobs must be >= 1");
     if (!is_self(c)) return fail(HB_ERR_STATE, "hb_block_batch: jobs are stacked in R only (do not load S)");
+    if (c->shard_world > 1) return fail(HB_ERR_STATE, "hb_block_batch: sharded evaluation runs on hb_block only");
     const int64_t n = c->side[0].n;
     if (job_rows[0] != 0 || job_rows[n_jobs] != n)
         return fail(HB_ERR_ARG, "hb_block_batch: job_rows must start at 0 and end at the row count of R");

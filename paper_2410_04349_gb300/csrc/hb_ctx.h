@@ -100,6 +100,8 @@ struct hb_ctx {
     // one grouping MD per root branch follows the rules' MDs in eqset
     int64_t fail_alloc_after = -1;   // HB_FAIL_ALLOC_AFTER fault injection (-1: off)
     uint32_t part_m = 0;
+    // sharded evaluation (hb_set_shard): this process evaluates the blocks owned by rank
+    uint32_t shard_rank = 0, shard_world = 1;
     uint32_t layout_part_m = 0;       // part_m the layout was built for
     uint64_t group_mds = 0;           // bits of the grouping MDs
     std::vector<int> branch_key;      // per branch: equality key index (-1: one partition of all tuples)
@@ -172,6 +174,7 @@ struct hb_ctx {
     struct MdLane {
         Buf table, slot_r, count_r, start_r, cursor, slot_s, count_s, start_s, scan, meta;
         Buf jac;   // q-gram encoder scratch when the lane encodes a Jaccard column
+        Buf minrow;   // sharded evaluation: each group's smallest row
         cudaStream_t stream = nullptr;
         cudaEvent_t done = nullptr;
     };

@@ -246,6 +246,10 @@ void group_probe(const uint32_t *rec_probe, int64_t n, const uint32_t *rec_owner
 void count_slots(const uint32_t *slot, int64_t n, uint32_t *count, cudaStream_t s);
 void scatter_slots(const uint32_t *slot, int64_t n, const uint32_t *start, uint32_t *cursor, uint32_t *members,
                    cudaStream_t s);
+// sharded evaluation: the counts of groups (slots) owned by another rank are set
+// to 0, so their blocks are not emitted; minrow: cap words of scratch
+void shard_filter(const uint32_t *slot_r, int64_t n_r, uint32_t *count_r, uint32_t *count_s, uint32_t *minrow,
+                  uint64_t cap, uint32_t md, uint32_t rank, uint32_t world, cudaStream_t s);
 void emit_blocks(const uint32_t *count_r, const uint32_t *start_r, const uint32_t *count_s, const uint32_t *start_s,
                  uint64_t cap, uint32_t md, int self_join, uint32_t member_base_r, uint32_t member_base_s, int tile,
                  BlockDesc *blocks, uint64_t *tiles, uint32_t *n_blocks, uint32_t block_cap, unsigned int *overflow,

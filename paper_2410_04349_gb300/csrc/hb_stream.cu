@@ -149,6 +149,7 @@ extern "C" hb_status hb_block_stream(hb_ctx *c, int64_t n_rows_s, int32_t n_cols
     *n_out = 0;
     if (c->side[0].cols.empty() && c->side[0].n == 0) return fail(HB_ERR_STATE, "hb_block_stream: R not loaded");
     if (c->part_m) return fail(HB_ERR_STATE, "hb_block_stream: partitioned blocking runs on hb_block only");
+    if (c->shard_world > 1) return fail(HB_ERR_STATE, "hb_block_stream: sharded evaluation runs on hb_block only");
     if (n_rows_s < 0 || n_rows_s >= (1ll << 30)) return fail(HB_ERR_ARG, "hb_block_stream: n_rows_s out of range");
     for (int k = 0; k < n_cols; k++) {
         const hb_column &col = cols_s[k];

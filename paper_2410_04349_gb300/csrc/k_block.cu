@@ -133,6 +133,43 @@ __global__ void k_scatter_slots(const uint32_t *slot, int64_t n, const uint32_t 
     if (s != NO_SLOT) members[HB_IDX(start[s] + base + __popc(peers & ((1u << lane) - 1u)), n, 30)] = (uint32_t)i;
 }
 
+// ---- sharding the evaluation over several processes (one GPU each) ----
+// A block (one MD's group of tuples that agree on its equality keys) belongs to
+// one rank: shard_owner(md, the group's smallest row id), a function of the
+// data alone, so every process assigns every block alike however its own
+// dictionary and group slots were numbered.  The smallest row of each group:
+// the lowest lane among a warp's lanes of one slot holds the smallest row
+// (rows increase with the lane), which takes an atomic minimum.
+__global__ void k_group_min(const uint32_t *slot, int64_t n, uint32_t *minrow) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t s = i < n ? slot[i] : NO_SLOT;
+    const unsigned peers = __match_any_sync(0xffffffffu, s);
+    if (s != NO_SLOT && (__ffs(peers) - 1) == (int)(threadIdx.x & 31)) atomicMin(&minrow[s], (uint32_t)i);
+}
+
+// owner rank: the 32-bit finaliser of MurmurHash3 (Appleby) of the row id
+// mixed with the MD index, modulo the number of ranks
+__device__ __forceinline__ uint32_t shard_owner(uint32_t md, uint32_t row, uint32_t world) {
+    uint32_t h = row ^ (md * 0x9E3779B9u);
+    h ^= h >> 16;
+    h *= 0x85EBCA6Bu;
+    h ^= h >> 13;
+    h *= 0xC2B2AE35u;
+    h ^= h >> 16;
+    return h % world;
+}
+
+// groups owned by another rank get no members: their blocks are not emitted
+__global__ void k_shard_filter(uint32_t *count_r, uint32_t *count_s, const uint32_t *minrow, uint64_t cap,
+                               uint32_t md, uint32_t rank, uint32_t world) {
+    const int64_t sl = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (sl >= (int64_t)cap || count_r[sl] == 0) return;
+    if (shard_owner(md, minrow[sl], world) != rank) {
+        count_r[sl] = 0;
+        if (count_s) count_s[sl] = 0;
+    }
+}
+
 __device__ __forceinline__ uint64_t tiles_of(uint32_t nr, uint32_t ns, int self_join, int tile) {
     uint64_t a = (nr + tile - 1) / tile;
     if (self_join) return a * (a + 1) / 2;
@@ -319,6 +356,14 @@ void scatter_slots(const uint32_t *slot, int64_t n, const uint32_t *start, uint3
     if (n == 0) return;
     HB_LAUNCHED(1);
     k_scatter_slots<<<nblk(n), BT, 0, s>>>(slot, n, start, cursor, members);
+}
+
+void shard_filter(const uint32_t *slot_r, int64_t n_r, uint32_t *count_r, uint32_t *count_s, uint32_t *minrow,
+                  uint64_t cap, uint32_t md, uint32_t rank, uint32_t world, cudaStream_t s) {
+    cudaMemsetAsync(minrow, 0xFF, sizeof(uint32_t) * (size_t)cap, s);
+    HB_LAUNCHED(2);
+    if (n_r > 0) k_group_min<<<nblk(n_r), BT, 0, s>>>(slot_r, n_r, minrow);
+    k_shard_filter<<<nblk((int64_t)cap), BT, 0, s>>>(count_r, count_s, minrow, cap, md, rank, world);
 }
 
 void emit_blocks(const uint32_t *count_r, const uint32_t *start_r, const uint32_t *count_s, const uint32_t *start_s,

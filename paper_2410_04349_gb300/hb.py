@@ -106,7 +106,8 @@ EXPORTS = ["hb_create", "hb_destroy", "hb_last_error", "hb_version", "hb_load_ta
            "hb_get_cost_model", "hb_set_cost_model", "hb_mlp_forward", "hb_mlp_forward_bf16", "hb_mlp_backward",
            "hb_mlp_backward_noalloc", "hb_adam_step", "hb_probe_int_issue", "hb_time_pairs",
            "hb_pair_model_forward", "hb_pair_model_backward", "hb_train_pair_model", "hb_tile_log",
-           "hb_train_tile_model", "hb_set_tile_model", "hb_get_tile_model", "hb_batch_tile", "hb_set_partitions"]
+           "hb_train_tile_model", "hb_set_tile_model", "hb_get_tile_model", "hb_batch_tile", "hb_set_partitions",
+           "hb_set_shard", "hb_merge_pairs"]
 
 _lib = None
 
@@ -145,6 +146,8 @@ def lib():
         "hb_set_tile_model": (st, [P, P]), "hb_get_tile_model": (st, [P, P]),
         "hb_batch_tile": (st, [P, P, P, P]),
         "hb_set_partitions": (st, [P, ctypes.c_uint32]),
+        "hb_set_shard": (st, [P, i32, i32]),
+        "hb_merge_pairs": (st, [P, P, i32, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -309,6 +312,12 @@ class Context:
                "hb_plan")
         return info
 
+    def set_shard(self, rank, world):
+        """Sharded evaluation: later blocking calls return the pairs of the
+        blocks owned by `rank` of `world` (a function of each block's MD and
+        smallest row); world = 1 evaluates everything."""
+        _check(lib().hb_set_shard(self._h, int(rank), int(world)), "hb_set_shard")
+
     def set_partitions(self, m):
         """Root-edge hash partitioning (Section 5.3) with m partitions per hash
         function; 0 restores exact equality groups.  Applies from the next plan."""
@@ -440,6 +449,19 @@ class Context:
     def set_cost_model(self, params):
         params = np.ascontiguousarray(params, np.float32)
         _check(lib().hb_set_cost_model(self._h, params.ctypes.data), "hb_set_cost_model")
+
+
+def merge_pairs(lists):
+    """k-way merge of sorted (n, 2) uint32 pair arrays into one sorted array
+    (host code of the library)."""
+    arrs = [np.ascontiguousarray(a, dtype=np.uint32).reshape(-1, 2) for a in lists]
+    k = len(arrs)
+    counts = np.array([a.shape[0] for a in arrs], dtype=np.int64)
+    ptrs = (ctypes.c_void_p * max(k, 1))(*[a.ctypes.data for a in arrs])
+    out = np.empty((int(counts.sum()), 2), dtype=np.uint32)
+    _check(lib().hb_merge_pairs(ptrs, counts.ctypes.data if k else None, k, out.ctypes.data if out.size else None),
+           "hb_merge_pairs")
+    return out.astype(np.int64)
 
 
 def plan_order(sp, cost, mds, skip=None):
