@@ -406,6 +406,48 @@ def measure_all_pairs(args):
             "timing": "CUDA events around the evaluation kernel, median"}
 
 
+def measure_sharded(args, table, mds, world=4):
+    """Sharded evaluation (hb_set_shard) of the step's table and rules, the
+    ranks run one after the other on this GPU as separate processes would on
+    theirs: each rank's evaluation time and candidate share (how evenly the
+    owner function spreads the work), and whether the merged shards
+    (hb_merge_pairs) equal the unsharded result."""
+    import statistics as st_
+    from paper_2410_04349_gb300 import hb
+    runs, parts, whole = [], [], None
+    for rank in range(-1, world):
+        with hb.Context(device=0) as ctx:
+            ctx.load_table(0, table.n_rows, table.columns)
+            for md in mds:
+                ctx.add_md(md)
+            if rank >= 0:
+                ctx.set_shard(rank, world)
+            ctx.plan("rule_data")
+            pairs = ctx.block()
+            ev = []
+            for _ in range(max(1, min(args.steps, 3))):
+                pairs = ctx.block()
+                ev.append(ctx.stats()["ms_eval"])
+            stt = ctx.stats()
+        if rank < 0:
+            whole = pairs
+            whole_ms = st_.median(ev)
+            whole_cand = stt["candidate_pairs"]
+            continue
+        parts.append(pairs)
+        runs.append({"rank": rank, "eval_ms": st_.median(ev), "candidate_pairs": stt["candidate_pairs"],
+                     "emitted_pairs": int(len(pairs))})
+    merged = hb.merge_pairs(parts)
+    cand = [r["candidate_pairs"] for r in runs]
+    return {"workload": f"the step's table and rules ({table.n_rows} tuples, {len(mds)} MDs) in {world} shards, "
+                        "the ranks run in turn on one GPU", "world": world, "unsharded_eval_ms": whole_ms,
+            "runs": runs, "max_rank_eval_ms": max(r["eval_ms"] for r in runs),
+            "candidate_share_max_over_mean": max(cand) / (sum(cand) / world),
+            "candidates_add_up": sum(cand) == whole_cand,
+            "merged_equals_unsharded": bool(np.array_equal(merged, whole)),
+            "timing": "CUDA events around the evaluation kernel, median"}
+
+
 def measure_partitions(args, table, mds):
     """Root-edge hash partitioning (Section 5.3) on the step's own table and
     rules: m partitions per root-edge hash function instead of exact equality
@@ -672,6 +714,7 @@ def main():
         line["batched_vs_per_job"] = compare_c4(args)
         line["all_pairs"] = measure_all_pairs(args)
         line["partitions"] = measure_partitions(args, table, mds)
+        line["sharded"] = measure_sharded(args, table, mds)
     if rank == 0 and world == 1 and not args.no_cpu:
         rate, dt, cand, threads = cpu_oracle_rate(table, mds, args.cpu_sample_rows)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
